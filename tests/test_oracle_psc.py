@@ -1,0 +1,375 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: printed values, closed
+forms, quadrature, conservation identities or symmetry.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ lattices (Sec. 2.1)
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_lattice_isotropy(lattice):
+    """Weights and velocities satisfy the moment identities that recover Navier-Stokes:
+    sum w = 1, sum w e = 0, sum w e e = I/3, odd third moment 0, fourth moment
+    sum w e_a e_b e_c e_d = (d_ab d_cd + d_ac d_bd + d_ad d_bc)/9."""
+    e, w, opp = O.lattice_tables(lattice)
+    dim = 2 if lattice == 9 else 3
+    e = e[:, :dim].astype(np.float64)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose((w[:, None] * e).sum(0), 0.0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, e, e), np.eye(dim) / 3.0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", w, e, e, e), 0.0, atol=1e-15)
+    I = np.eye(dim)
+    iso = (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+           + np.einsum("ad,bc->abcd", I, I)) / 9.0
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, e, e, e, e), iso, atol=1e-15)
+    # opposite table and the D3Q19 weights printed after Eq. 3
+    assert np.all(e[opp] == -e)
+    if lattice == 19:
+        assert w[0] == pytest.approx(1 / 3) and np.allclose(w[1:7], 1 / 18)
+        assert np.allclose(w[7:], 1 / 36)
+
+
+# ------------------------------------------------------- linear approximation (Sec. 2.4)
+@pytest.mark.parametrize("r", [0.9, 1.5, 3.0, 6.5, 12.0, 40.0])
+def test_va_closed_form_matches_quadrature(r):
+    """Eq. 17 and Eq. 19 (integrand read as the sphere/disc height) against adaptive
+    quadrature of the height over the unit square / segment."""
+    q3, _ = integrate.dblquad(lambda y, x: math.sqrt(r * r - x * x - y * y), -0.5, 0.5,
+                              -0.5, 0.5, epsabs=1e-13, epsrel=1e-13)
+    q2, _ = integrate.quad(lambda x: math.sqrt(r * r - x * x), -0.5, 0.5, epsabs=1e-13,
+                           epsrel=1e-13)
+    assert O.va(3, r) == pytest.approx(q3, rel=1e-12, abs=1e-12)
+    assert O.va(2, r) == pytest.approx(q2, rel=1e-12, abs=1e-12)
+    # Eq. 18 and its large-r expansion f = 1/2 - 1/(12 r) (3D), 1/2 - 1/(24 r) (2D) + O(r^-3)
+    if r >= 6:
+        assert O.f_of_r(3, r) == pytest.approx(0.5 - 1 / (12 * r), abs=0.01 / r ** 3)
+        assert O.f_of_r(2, r) == pytest.approx(0.5 - 1 / (24 * r), abs=0.01 / r ** 3)
+
+
+def _exact_overlap_axis_cell(r, yc, dim):
+    """True covered volume of a unit cell centred at (0, yc[, 0]) by a sphere/disc of
+    radius r at the origin (quadrature of the clipped height)."""
+    def h(*xs):
+        s = r * r - sum(x * x for x in xs)
+        top = math.sqrt(s) if s > 0 else -1e300
+        return min(max(top - (yc - 0.5), 0.0), 1.0)
+    if dim == 2:
+        return integrate.quad(lambda x: h(x), -0.5, 0.5, epsabs=1e-12, limit=200)[0]
+    return integrate.dblquad(lambda z, x: h(x, z), -0.5, 0.5, -0.5, 0.5, epsabs=1e-11)[0]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("D", [-0.3, -0.05, 0.0, 0.2, 0.4])
+def test_linear_approximation_exact_under_its_assumptions(dim, D):
+    """Under assumptions (i)-(iii) of Sec. 2.4 (cell centre on an axis through the
+    particle centre, surface crossing only the side faces) Eq. 15-18 is exact. A cell at
+    distance r + D on the y axis of a large particle satisfies them, so the oracle's
+    fraction must equal the quadrature of the true overlap."""
+    r = 15.0
+    n = 48
+    p = O.make_params(9 if dim == 2 else 19, n, n, 1 if dim == 2 else n, tau=0.8)
+    c = np.array([20.0, 20.0 - (r + D) + 0.0, 0.0 if dim == 2 else 20.0])
+    # cell (20, 20[, 20]) sits at distance r + D above the particle centre along +y
+    eps_sum, nrec, pid, eps = O.solid_fraction(p, c[None, :], [r])
+    cell = (20 * n + 20) if dim == 2 else ((20 * n + 20) * n + 20)
+    exact = _exact_overlap_axis_cell(r, r + D, dim)
+    assert eps_sum[cell] == pytest.approx(exact, abs=2e-9)
+
+
+def _supersampled(p, X, r, dim, m):
+    """Covered fraction of every cell by deterministic m^dim midpoint supersampling."""
+    n = (p.nx, p.ny, p.nz)
+    out = np.zeros(p.nx * p.ny * p.nz)
+    offs = (np.arange(m) + 0.5) / m - 0.5
+    lo = [int(math.floor(X[a] - r - 1)) for a in range(dim)]
+    hi = [int(math.ceil(X[a] + r + 1)) for a in range(dim)]
+    if dim == 2:
+        ox, oy = np.meshgrid(offs, offs, indexing="ij")
+        for ix in range(lo[0], hi[0] + 1):
+            for iy in range(lo[1], hi[1] + 1):
+                d2 = (ix + ox - X[0]) ** 2 + (iy + oy - X[1]) ** 2
+                out[(iy % n[1]) * n[0] + ix % n[0]] += (d2 < r * r).mean()
+    else:
+        ox, oy, oz = np.meshgrid(offs, offs, offs, indexing="ij")
+        for ix in range(lo[0], hi[0] + 1):
+            for iy in range(lo[1], hi[1] + 1):
+                for iz in range(lo[2], hi[2] + 1):
+                    d2 = (ix + ox - X[0]) ** 2 + (iy + oy - X[1]) ** 2 + (iz + oz - X[2]) ** 2
+                    out[((iz % n[2]) * n[1] + iy % n[1]) * n[0] + ix % n[0]] += (d2 < r * r).mean()
+    return out
+
+
+@pytest.mark.parametrize("dim,r,m", [(2, 3.0, 96), (2, 6.5, 96), (2, 8.0, 64), (3, 3.0, 24),
+                                     (3, 6.0, 20)])
+def test_solid_fraction_against_supersampling_and_volume(dim, r, m):
+    """Table 1 per cell against the true overlap (supersampling), and the total against
+    the exact area/volume as in Eq. 20. Bounds: 0.06 per cell (the linear approximation's
+    corner-cell error), total relative error below 5e-3 (measured at most 3e-3 for r = 3..8)."""
+    rng = np.random.default_rng(7)
+    n = 32 if dim == 2 else 24
+    p = O.make_params(9 if dim == 2 else 19, n, n, 1 if dim == 2 else n, tau=0.8)
+    X = np.array([n / 2, n / 2, 0.0 if dim == 2 else n / 2]) + np.append(
+        rng.uniform(-0.5, 0.5, dim), [0.0] * (3 - dim))
+    eps_sum, *_ = O.solid_fraction(p, X[None, :], [r])
+    ss = _supersampled(p, X, r, dim, m)
+    assert np.max(np.abs(eps_sum - ss)) < 0.06
+    exact = math.pi * r * r if dim == 2 else 4.0 / 3.0 * math.pi * r ** 3
+    assert abs(eps_sum.sum() - exact) / exact < 5e-3
+
+
+def test_shell_cells_only_where_paper_says():
+    """Cells farther than r + h are untouched; cells within r - h are fully solid."""
+    p = O.make_params(19, 24, 24, 24, tau=0.8)
+    X = np.array([[11.3, 12.1, 11.7]])
+    r = 5.0
+    eps_sum, *_ = O.solid_fraction(p, X, [r])
+    z, y, x = np.meshgrid(np.arange(24), np.arange(24), np.arange(24), indexing="ij")
+    d = np.sqrt((x - X[0, 0]) ** 2 + (y - X[0, 1]) ** 2 + (z - X[0, 2]) ** 2).ravel()
+    assert np.all(eps_sum[d >= r + 1.0] == 0.0)
+    assert np.all(eps_sum[d <= r - 1.0] == 1.0)
+    mid = (d > r - 1.0) & (d < r + 1.0)
+    assert np.all((eps_sum[mid] >= 0.0) & (eps_sum[mid] <= 1.0))
+
+
+# ------------------------------------------------------------- weights (Eq. 9, Eq. 13)
+def test_worked_example_eq9_golden():
+    rows = np.loadtxt(os.path.join(GOLDEN, "eq9_worked_example.txt"))
+    for tau, b_orig, b_mod in rows:
+        Bn, Bs = O.cell_weights([0.4, 0.6], tau, mode=1)
+        assert round(Bn, 2) == pytest.approx(b_orig, abs=1e-12)
+        Bn_m, Bs_m = O.cell_weights([0.4, 0.6], tau, mode=0)
+        assert Bn_m == pytest.approx(b_mod, abs=1e-15)
+        assert Bs_m.sum() == pytest.approx(b_mod, abs=1e-15)
+
+
+def test_eq9_limits_and_single_particle_equivalence():
+    for tau in (0.55, 0.8, 2.0):
+        assert O.B(0.0, tau) == 0.0 and O.B(1.0, tau) == pytest.approx(1.0, abs=1e-15)
+        # with one particle the modified weight equals the original (text after Eq. 13)
+        for e in (0.1, 0.5, 0.93):
+            assert O.cell_weights([e], tau, 0)[0] == pytest.approx(O.cell_weights([e], tau, 1)[0],
+                                                                   rel=1e-15)
+    # Fig. 3(b): the original total always underestimates the modified one
+    for en in (0.6, 0.8, 1.0):
+        for e1 in np.linspace(0.05, en - 0.05, 7):
+            orig = O.cell_weights([e1, en - e1], 0.8, 1)[0]
+            mod = O.cell_weights([e1, en - e1], 0.8, 0)[0]
+            assert orig < mod
+
+
+def test_modified_weights_bounded_by_one_when_fractions_overlap():
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        k = rng.integers(2, 5)
+        eps = rng.uniform(0.2, 1.0, size=k)
+        Bn, Bs = O.cell_weights(eps, rng.uniform(0.51, 2.0), 0)
+        assert Bn == pytest.approx(1.0, abs=1e-12) if eps.sum() >= 1 else Bn <= 1.0
+        assert Bs.sum() == pytest.approx(Bn, rel=1e-12)
+        assert np.all(Bs >= 0)
+
+
+# --------------------------------------------------------- fluid solver (Sec. 2.1-2.2)
+def test_poiseuille_exact_at_the_bounce_back_magic_tau():
+    """Halfway bounce-back with BGK places the wall exactly half a spacing beyond the last
+    node when tau = 1/2 + sqrt(3/16); the body-force-driven channel then reaches the
+    parabola F/(2 rho nu) (y + 1/2)(H - 1/2 - y) with nu = (tau - 1/2)/3 (Eq. 5) to
+    round-off."""
+    tau = 0.5 + math.sqrt(3.0 / 16.0)
+    H, F = 16, 1e-6
+    p = O.make_params(9, 4, H, 1, bc=(0, 1, 0), tau=tau, body_force=(F, 0, 0))
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    O.run(p, f, 20000)
+    rho, u = O.macro(p, f)
+    y = np.arange(H)
+    nu = (tau - 0.5) / 3.0
+    ana = F / (2 * nu) * (y + 0.5) * (H - 0.5 - y)
+    assert np.max(np.abs(u[0, :, 0, 0] - ana)) / ana.max() < 1e-9
+    assert np.allclose(u[0, :, :, 1], 0.0, atol=1e-13)
+
+
+def _duct_series(y, z, lh, lw, G, mu, M=60):
+    s = G / (2 * mu) * y * (lh - y)
+    for m in range(1, M):
+        b = (2 * m - 1) * math.pi / lh
+        s = s - 4 * G * lh ** 2 / (mu * math.pi ** 3) / (2 * m - 1) ** 3 * (
+            np.sinh(b * z) + np.sinh(b * (lw - z))) / np.sinh(b * lw) * np.sin(b * y)
+    return s
+
+
+def test_duct_flow_within_paper_error():
+    """Sec. 3.1: body-force-driven D3Q19 duct, tau = 0.65, walls on both transverse
+    axes; the steady profile matches the series of Eq. 30 within the paper's 0.5 %
+    (here on a 21 x 21 cross-section, periodic along the flow)."""
+    tau, F, H = 0.65, 3.2e-6, 21
+    nu = (tau - 0.5) / 3.0
+    p = O.make_params(19, 1, H, H, bc=(0, 1, 1), tau=tau, body_force=(F, 0, 0))
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    O.run(p, f, int(14 * H * H / (2 * math.pi ** 2 * nu)))
+    rho, u = O.macro(p, f)
+    ux = u[:, :, 0, 0].T  # [y][z]
+    yy, zz = np.meshgrid(np.arange(H) + 0.5, np.arange(H) + 0.5, indexing="ij")
+    U = _duct_series(yy, zz, H, H, F, nu)
+    c = H // 2
+    norm_err = np.max(np.abs(ux[:, c] / ux[:, c].max() - U[:, c] / U[:, c].max()))
+    assert norm_err < 5e-3
+    assert np.max(np.abs(ux - U)) / U.max() < 5e-3
+    # symmetric about both mid-planes
+    assert np.allclose(ux, ux[::-1, :], rtol=1e-10, atol=1e-16)
+    assert np.allclose(ux, ux.T, rtol=1e-10, atol=1e-16)
+
+
+def test_fluid_at_rest_between_walls_stays_at_rest():
+    p = O.make_params(19, 6, 7, 8, bc=(0, 1, 1), tau=0.8)
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    f0 = f.copy()
+    O.run(p, f, 10)
+    assert np.array_equal(f, f0) or np.max(np.abs(f - f0)) < 1e-16
+
+
+# ------------------------------------------------ PSC coupling (Eq. 10, 12, 14, 7, 11)
+def _moving_setup(lattice, psc, seed=5):
+    rng = np.random.default_rng(seed)
+    if lattice == 9:
+        n = (40, 36, 1)
+        X = np.array([[12.3, 17.2, 0.0], [19.1, 19.9, 0.0], [30.5, 8.25, 0.0]])
+        r = np.array([5.0, 3.5, 4.2])  # first two overlap: cells with sum eps > 1
+    else:
+        n = (24, 22, 20)
+        X = np.array([[8.3, 9.2, 10.1], [14.2, 11.0, 9.6], [18.0, 3.2, 15.5]])
+        r = np.array([4.1, 3.2, 3.3])
+    U = rng.normal(0, 2e-3, size=(3, 3))
+    Om = rng.normal(0, 1e-3, size=(3, 3))
+    if lattice == 9:
+        U[:, 2] = 0.0
+        Om[:, :2] = 0.0
+    p = O.make_params(lattice, *n, tau=0.73, body_force=(2e-5, -1e-5, 3e-6 if lattice == 19 else 0.0),
+                      psc=psc)
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    f += rng.uniform(-1e-3, 1e-3, size=f.shape) * np.asarray(O.lattice_tables(lattice)[1])[:, None, None, None]
+    return p, f, X, U, Om, r
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+@pytest.mark.parametrize("psc", [0, 1])
+def test_mass_conserved_exactly(lattice, psc):
+    """sum_i Omega^s_i = 0 (Eq. 10), sum_i F_i = 0 (Eq. 4), streaming permutes."""
+    p, f, X, U, Om, r = _moving_setup(lattice, psc)
+    m0 = f.sum()
+    for _ in range(5):
+        O.step(p, f, X, U, Om, r)
+    assert abs(f.sum() - m0) / m0 < 1e-14
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+@pytest.mark.parametrize("psc", [0, 1])
+def test_momentum_budget_exact(lattice, psc):
+    """Periodic box: the fluid's momentum changes per step by F sum_n (1 - B_n) minus the
+    particles' total hydrodynamic force. Modified scheme: exact identity (Eq. 12, 14).
+    Original scheme: the collision adds sum_s B(eps_s) Omega^s while Eq. 11 weights each
+    particle by the cell's B_n, so the identity holds only where one particle touches a
+    cell; the overlapping pair makes the two sides differ by the double counting."""
+    p, f, X, U, Om, r = _moving_setup(lattice, psc)
+    e = O.lattice_tables(lattice)[0].astype(np.float64)
+    Fb = np.array([p.body_force[0], p.body_force[1], p.body_force[2]])
+    for _ in range(3):
+        M0 = np.einsum("izyx,ia->a", f, e)
+        Fp, Tp, Bn = O.step(p, f, X, U, Om, r, want_Bn=True)
+        M1 = np.einsum("izyx,ia->a", f, e)
+        budget = Fb * (1.0 - Bn).sum() - Fp.sum(0)
+        if psc == 0:
+            assert np.allclose(M1 - M0, budget, rtol=1e-10, atol=1e-15)
+    if psc == 1:
+        assert not np.allclose(M1 - M0, budget, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_comoving_particle_feels_no_force(lattice):
+    """A particle translating with a uniform equilibrium flow (no body force) leaves the
+    fluid unchanged and feels zero force and torque (Eq. 10 at u_s = u)."""
+    n = (30, 28, 1) if lattice == 9 else (20, 18, 16)
+    V = np.array([3e-3, -2e-3, 0.0 if lattice == 9 else 1.5e-3])
+    p = O.make_params(lattice, *n, tau=0.9)
+    f = O.equilibrium(p, 1.0, V).copy()
+    f0 = f.copy()
+    X = np.array([[11.4, 12.7, 0.0 if lattice == 9 else 8.2]])
+    F, T = O.step(p, f, X, V[None, :], np.zeros((1, 3)), [4.5])
+    assert np.max(np.abs(f - f0)) < 1e-15
+    assert np.allclose(F, 0, atol=1e-13) and np.allclose(T, 0, atol=1e-12)
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_drag_opposes_translation_and_torque_opposes_spin(lattice):
+    """In quiescent fluid the first-step force is -sum_n B_{n,s} rho u_s (Eq. 10 and 14
+    with f = f^eq(1, 0)), i.e. opposite to the particle's velocity, and a spinning
+    particle gets a torque opposite to its spin."""
+    n = (40, 40, 1) if lattice == 9 else (24, 24, 24)
+    p = O.make_params(lattice, *n, tau=0.8)
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    X = np.array([[20.2, 19.6, 0.0 if lattice == 9 else 11.9]])
+    Uv = np.array([[1e-3, 0.0, 0.0]])
+    F, T, Bn = O.step(p, f, X, Uv, np.zeros((1, 3)), [5.0], want_Bn=True)
+    assert F[0, 0] == pytest.approx(-Bn.sum() * 1e-3, rel=1e-12)
+    assert abs(F[0, 1]) < 1e-9 * abs(F[0, 0])
+    # spin about z at a lattice-symmetric centre: T_z = -Omega_z sum_n B_n |arm|^2 < 0
+    # and, by the mirror symmetries of the covered cells, zero net force
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    Xs = np.array([[20.0, 20.0, 0.0 if lattice == 9 else 12.0]])
+    Om = np.array([[0.0, 0.0, 2e-3]])
+    F, T = O.step(p, f, Xs, np.zeros((1, 3)), Om, [5.0])
+    assert T[0, 2] < 0 and np.max(np.abs(F)) < 1e-12 * abs(T[0, 2])
+
+
+def test_mirror_symmetric_pair_gets_mirrored_forces():
+    """Two identical discs placed symmetrically about x = 20 in a flow driven along y,
+    moving toward each other: forces mirror (F_x odd, F_y even, torque odd)."""
+    p = O.make_params(9, 40, 32, 1, tau=0.7, body_force=(0.0, 1e-5, 0.0))
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    X = np.array([[20.0 - 5.6, 15.3, 0.0], [20.0 + 5.6, 15.3, 0.0]])
+    U = np.array([[1e-3, 0.0, 0.0], [-1e-3, 0.0, 0.0]])
+    for _ in range(20):
+        F, T = O.step(p, f, X, U, np.zeros((2, 3)), [5.0, 5.0])
+    assert F[0, 0] == pytest.approx(-F[1, 0], rel=1e-9)
+    assert F[0, 1] == pytest.approx(F[1, 1], rel=1e-9)
+    assert T[0, 2] == pytest.approx(-T[1, 2], rel=1e-9)
+
+
+def test_c1_workload_has_shared_cells():
+    """The c1 packing places pair B 0.25 lu apart so some cells are shared; a 1 lu gap
+    (pair A) can share no cell because f(6.5) < 1/2."""
+    w = synth.workload("c1")
+    p = O.make_params(9, 64, 64, 1, tau=0.8)
+    eps_sum, nrec, pid, eps = O.solid_fraction(p, w["X"], w["r"])
+    shared = np.nonzero(nrec >= 2)[0]
+    assert shared.size > 0
+    assert set(np.unique(pid[shared, :2])) <= {2, 3}
+    assert O.f_of_r(2, 6.5) < 0.5
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_periodic_translation_invariance(lattice):
+    """Shifting the fluid and the particles by whole cells with periodic wrap (so that the
+    particles straddle the box faces) changes neither the forces nor the shifted field:
+    pins the minimum-image arms and distances (reading R10)."""
+    p, f, X, U, Om, r = _moving_setup(lattice, 0, seed=11)
+    shift = np.array([-10, -9, -8 if lattice == 19 else 0])
+    n = np.array([p.nx, p.ny, p.nz])
+    f2 = np.ascontiguousarray(np.roll(f, shift=tuple(shift[::-1]), axis=(1, 2, 3)))
+    X2 = X + shift
+    for a in range(3):
+        X2[:, a] %= n[a]
+    F1, T1 = O.step(p, f, X, U, Om, r)
+    F2, T2 = O.step(p, f2, X2, U, Om, r)
+    assert np.allclose(F1, F2, rtol=1e-11, atol=1e-17)
+    assert np.allclose(T1, T2, rtol=1e-11, atol=1e-16)
+    assert np.allclose(np.roll(f, shift=tuple(shift[::-1]), axis=(1, 2, 3)), f2, rtol=0, atol=1e-15)
