@@ -77,17 +77,119 @@ def lib():
     return _lib
 
 
+class DemParams(C.Structure):
+    """Mirror of ``ora_dem_params`` in dem_oracle.c."""
+
+    _fields_ = [
+        ("E", C.c_double), ("poisson", C.c_double), ("gamma", C.c_double),
+        ("density", C.c_double), ("mu_f", C.c_double), ("theta_crit", C.c_double),
+        ("alpha_n", C.c_double), ("k_t_scale", C.c_double), ("eta_t_scale", C.c_double),
+        ("dt", C.c_double), ("gravity", C.c_double * 3), ("adhesive", C.c_int), ("dim", C.c_int),
+        ("n", C.c_int * 3), ("periodic", C.c_int * 3),
+    ]
+
+
+NH = 7  # history values per contact: sliding spring (3), twist (1), rolling spring (3)
+
+
+def make_dem_params(E=2.0, poisson=0.3, gamma=2e-4, density=3.0, mu_f=0.3, theta_crit=0.01,
+                    alpha_n=0.3, k_t_scale=1.0, eta_t_scale=1.0, dt=0.1, gravity=(0, 0, 0),
+                    adhesive=1, dim=3, n=(64, 64, 64), periodic=(1, 1, 1)):
+    p = DemParams()
+    p.E, p.poisson, p.gamma, p.density = E, poisson, gamma, density
+    p.mu_f, p.theta_crit, p.alpha_n = mu_f, theta_crit, alpha_n
+    p.k_t_scale, p.eta_t_scale, p.dt = k_t_scale, eta_t_scale, dt
+    for a in range(3):
+        p.gravity[a] = float(gravity[a])
+        p.n[a] = int(n[a])
+        p.periodic[a] = int(periodic[a])
+    p.adhesive, p.dim = int(adhesive), int(dim)
+    return p
+
+
 def _extra_signatures(L):
-    """Signatures of the DEM and adjoint oracle entry points, when built."""
+    """Signatures of the DEM and adjoint oracle entry points."""
     dp = C.POINTER(C.c_double)
     ip = C.POINTER(C.c_int)
-    if hasattr(L, "ora_jkr_delta"):
-        L.ora_jkr_delta.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.ora_jkr_delta.restype = C.c_double
-        L.ora_jkr_contact_radius.argtypes = [C.c_double, C.c_double, C.c_double, ip]
-        L.ora_jkr_contact_radius.restype = C.c_double
-        L.ora_jkr_force.argtypes = [C.c_double, C.c_double, C.c_double]
-        L.ora_jkr_force.restype = C.c_double
+    pp = C.POINTER(DemParams)
+    L.ora_jkr_delta.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.ora_jkr_delta.restype = C.c_double
+    L.ora_jkr_contact_radius.argtypes = [C.c_double, C.c_double, C.c_double, ip]
+    L.ora_jkr_contact_radius.restype = C.c_double
+    L.ora_jkr_force.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.ora_jkr_force.restype = C.c_double
+    L.ora_dem_step.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, ip, ip, dp, C.c_int]
+    L.ora_dem_step.restype = C.c_int
+    L.ora_pairs_within.argtypes = [pp, C.c_int, dp, dp, C.c_double, ip, C.c_int]
+    L.ora_pairs_within.restype = C.c_int
+    L.ora_dem_pair_force.argtypes = [pp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+    L.ora_dem_pair_force.restype = C.c_int
+
+
+def jkr_delta(a, a0, R):
+    return lib().ora_jkr_delta(float(a), float(a0), float(R))
+
+
+def jkr_force(a, a0, FC):
+    return lib().ora_jkr_force(float(a), float(a0), float(FC))
+
+
+def jkr_contact_radius(delta, a0, R):
+    ok = C.c_int()
+    a = lib().ora_jkr_contact_radius(float(delta), float(a0), float(R), C.byref(ok))
+    return a, bool(ok.value)
+
+
+class DemState:
+    """Particle state plus the contact list (sorted canonical pairs and spring history)."""
+
+    def __init__(self, X, U, Om, r, cap=None):
+        self.X = _f64(X).reshape(-1, 3).copy()
+        self.U = _f64(U).reshape(-1, 3).copy()
+        self.Om = _f64(Om).reshape(-1, 3).copy()
+        self.r = _f64(r).reshape(-1).copy()
+        n = self.r.size
+        self.cap = cap if cap is not None else max(64, 8 * n)
+        self.pairs = np.zeros((self.cap, 2), dtype=np.int32)
+        self.hist = np.zeros((self.cap, NH))
+        self.ncontact = 0
+
+    def contacts(self):
+        return self.pairs[: self.ncontact].copy(), self.hist[: self.ncontact].copy()
+
+
+def dem_step(p, st, Ff=None, Tf=None, substeps=1):
+    n = st.r.size
+    Ff = np.zeros((n, 3)) if Ff is None else _f64(Ff).reshape(n, 3)
+    Tf = np.zeros((n, 3)) if Tf is None else _f64(Tf).reshape(n, 3)
+    nc = C.c_int(st.ncontact)
+    rc = lib().ora_dem_step(C.byref(p), n, _d(st.X), _d(st.U), _d(st.Om), _d(st.r), _d(Ff), _d(Tf),
+                            int(substeps), C.byref(nc), _i(st.pairs), _d(st.hist), st.cap)
+    st.ncontact = nc.value
+    _check(rc, "dem_step")
+    return st
+
+
+def pairs_within(p, X, r, thresh=0.0, cap=100000):
+    X = _f64(X).reshape(-1, 3)
+    r = _f64(r).reshape(-1)
+    out = np.zeros((cap, 2), dtype=np.int32)
+    k = lib().ora_pairs_within(C.byref(p), r.size, _d(X), _d(r), float(thresh), _i(out), cap)
+    if k < 0:
+        raise RuntimeError("pair capacity exceeded")
+    return out[:k].copy()
+
+
+def dem_pair_force(p, X, U, Om, r, i, j, hist=None):
+    X, U, Om = (_f64(a).reshape(-1, 3) for a in (X, U, Om))
+    r = _f64(r).reshape(-1)
+    h = np.zeros(NH) if hist is None else hist
+    assert h.dtype == np.float64 and h.flags.c_contiguous
+    fi, ti, fj, tj = (np.zeros(3) for _ in range(4))
+    rc = lib().ora_dem_pair_force(C.byref(p), r.size, _d(X), _d(U), _d(Om), _d(r), int(i), int(j),
+                                  _d(h), _d(fi), _d(ti), _d(fj), _d(tj))
+    _check(rc, "dem_pair_force")
+    return fi, ti, fj, tj, h
 
 
 def _d(a):
@@ -148,7 +250,7 @@ def _particles(X, U=None, Om=None, rad=None):
     return np.ascontiguousarray(X), np.ascontiguousarray(U), np.ascontiguousarray(Om), rad
 
 
-def solid_fraction(p, X, rad, maxk=16):
+def solid_fraction(p, X, rad, maxk=8):
     X = _f64(X).reshape(-1, 3)
     rad = _f64(rad).reshape(-1)
     ncell = p.nx * p.ny * p.nz
