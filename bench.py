@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the PSC lattice-Boltzmann + JKR-DEM step on GB300.
+
+A step is one pass of the whole hot path over the workload: bin the particles into lattice
+tiles, the fused PSC collide-stream kernel (solid fractions, weights, collision, streaming,
+force/torque reduction) and, when the DEM library is built, the DEM sub-steps. The default
+workload is the 2048 x 2048 D2Q9 channel with 5000 mobile discs (FP32, 10 DEM sub-steps per
+LBM step). The metric is million lattice updates per second (MLUPS), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on its own
+GPU (the method shards by domain, but one replica per GPU is what is measured here); the
+timed region is bracketed by a barrier and a device synchronisation, and the slowest rank's
+time is used. ``--impl reference`` times the FP64 CPU oracle on the host cores instead (rank
+0 only), each step a bounded sub-box of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_FILES = ["psc_kernels.cuh", "lattice.cuh", "psc_internal.h", "psc_f32.cu"]
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--storage", default=None)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dem", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------- distributed helpers
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_max(value, world, device=None):
+    """Max of a float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None and str(device).startswith("cuda"):
+            dist.barrier(device_ids=[device.index if hasattr(device, "index") else 0])
+        else:
+            dist.barrier()
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.25)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        return self.summary()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------- workload
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_FILES:
+        with open(os.path.join(ROOT, "paper_1901_09745_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, storage):
+    """DRAM bytes per collide-stream launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get("%s/%s" % (workload, storage))
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["bytes_per_launch"])
+
+
+WORKLOAD_TEXT = {
+    "c2": "D2Q9 2048x2048 channel (walls y), tau 0.7, 5000 mobile discs r~U(4,8) in a band of "
+          "solid fraction 0.40, velocities N(0,1e-3), JKR DEM 10 sub-steps per LBM step",
+    "c3": "D3Q19 256^3 periodic, tau 0.6, 2000 static spheres r=6, body force 1e-6",
+    "c3dense": "D3Q19 256^3 periodic, tau 0.6, 5563 static spheres r=6 (solid fraction 0.3)",
+    "c5": "D3Q19 512^3 channel (walls z), tau 0.55, 50000 spheres r~U(3,8)",
+}
+DEFAULT_STORAGE = {"c2": "f32", "c3": "f32", "c3dense": "f32", "c5": "f16", "c4": "f32", "c1": "f64"}
+BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+
+
+def dem_defaults(w):
+    """Contact-model parameters of the coupled workloads, in lattice units (see DESIGN)."""
+    return dict(E=2.0, poisson=0.3, gamma=2e-4, density=3.0, mu_f=0.3, theta_crit=0.01,
+                alpha_n=0.3, k_t_scale=1.0, eta_t_scale=1.0, dt_dem=1.0 / w["dem"]["substeps"],
+                gravity=(0.0, 0.0, 0.0), adhesive=1)
+
+
+# ---------------------------------------------------------------------------- ours
+def run_ours(args, rank, local_rank, world):
+    import torch
+    import paper_1901_09745_gb300 as P
+    import synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    P.lib()
+    w = synth.workload(args.workload)
+    storage = args.storage or DEFAULT_STORAGE.get(args.workload, "f32")
+    nx, ny, nz = w["n"]
+    ncell = nx * ny * nz
+    use_dem = (w.get("dem") is not None) and (not args.no_dem) and hasattr(P.lib(), "dem_create")
+    stream = torch.cuda.current_stream(dev)
+
+    ctx = P.lbm_create(w["lattice"], nx, ny, nz, bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                       storage=storage, stream=stream.cuda_stream)
+    P.lbm_set_particles(ctx, w["X"], w["U"], w["Om"], w["r"])
+    dem = None
+    if use_dem:
+        dem = P.dem_create(ctx, **dem_defaults(w))
+    substeps = w["dem"]["substeps"] if use_dem else 0
+
+    def one_step():
+        P.lbm_step(ctx, 1)
+        if dem is not None:
+            P.dem_step(dem, substeps)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    info0 = P.lbm_get_info(ctx)
+    launches0 = info0["launches"] + (P.dem_get_info(dem)["launches"] if dem is not None else 0)
+
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    P.lbm_kernel_timing(ctx, 1)
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clocks = sampler.stop() if sampler else None
+    ms = t0.elapsed_time(t1)
+    k_ms, k_n = P.lbm_kernel_timing(ctx, 0)
+    info1 = P.lbm_get_info(ctx)
+    launches1 = info1["launches"] + (P.dem_get_info(dem)["launches"] if dem is not None else 0)
+    ms_max = reduce_max(ms, world, dev)
+
+    # end to end through the C ABI with host (pinned) buffers, copies inside the timed region
+    n = len(w["r"])
+    hX = torch.from_numpy(np.ascontiguousarray(w["X"])).pin_memory()
+    hU = torch.from_numpy(np.ascontiguousarray(w["U"])).pin_memory()
+    hO = torch.from_numpy(np.ascontiguousarray(w["Om"])).pin_memory()
+    hR = torch.from_numpy(np.ascontiguousarray(w["r"])).pin_memory()
+    hF = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    hT = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    h0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.lbm_set_particles(ctx, hX, hU, hO, hR)
+        one_step()
+        P.lbm_get_forces(ctx, hF, hT)
+    torch.cuda.synchronize(dev)
+    e2e_s = reduce_max(time.perf_counter() - h0, world, dev)
+    P.lbm_destroy(ctx)
+
+    if rank != 0:
+        return None
+    q, sbytes = w["lattice"], BYTES[storage]
+    mlups = ncell * args.steps * world / (ms_max * 1e-3) / 1e6
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = 2.0 * q * sbytes * ncell
+    k_avg_s = (k_ms / max(k_n, 1)) * 1e-3
+    achieved = bytes_per_launch / k_avg_s / 1e9
+    traffic = recorded_traffic(args.workload, storage)
+    line = {
+        "metric": "PSC collide-stream + DEM step throughput (MLUPS)",
+        "value": round(mlups, 1),
+        "unit": "MLUPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": storage,
+        "data": "synthetic (seeded packings, see synth/)",
+        "config": {"workload": "%s: %s" % (args.workload, WORKLOAD_TEXT.get(args.workload, "")),
+                   "cells": ncell, "particles": n, "dem_substeps": substeps,
+                   "dem": "on" if use_dem else "not built",
+                   "l2": "inputs larger than L2: %.0f MB of populations read+written per step"
+                         % (bytes_per_launch / 1e6),
+                   "parallelism": "replicas (one independent domain per GPU)"},
+        "roofline": {"bound": "hbm", "kernel": "k_collide_stream", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_us": round(k_avg_s * 1e6, 2), "launches_timed": k_n},
+        "e2e": {"value": round(ncell * e2e_steps * world / e2e_s / 1e6, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": int(n * 10 * 8), "d2h_bytes_per_step": int(n * 6 * 8),
+                "steps": e2e_steps},
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clocks,
+    }
+    return line
+
+
+# ------------------------------------------------------------------------ CPU oracle
+def oracle_sample(workload, box):
+    """A bounded sub-box of the workload (same solid fraction and radius distribution)."""
+    import synth
+    w = synth.workload(workload)
+    scale = box / float(w["n"][0])
+    return synth.workload(workload, scale=scale)
+
+
+def run_oracle_steps(ws, steps):
+    import oracle as O
+    p = O.make_params(ws["lattice"], *ws["n"], bc=ws["bc"], tau=ws["tau"], body_force=ws["body_force"])
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    t = time.perf_counter()
+    O.run(p, f, steps, ws["X"], ws["U"], ws["Om"], ws["r"])
+    return time.perf_counter() - t
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    ws = oracle_sample(workload, 256 if workload in ("c2",) else 48)
+    ncell = int(np.prod(ws["n"]))
+    t1 = run_oracle_steps(ws, 2) / 2.0
+    steps = int(max(2, min(2000, budget_s / max(t1, 1e-6))))
+    t = run_oracle_steps(ws, steps)
+    return {"value": round(ncell * steps / t / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "%s sub-box %s (same solid fraction and radii), %d LBM steps, static particles, "
+                      "no DEM, FP64, single thread" % (workload, "x".join(map(str, ws["n"])), steps)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    ws = oracle_sample(args.workload, 512 if args.workload == "c2" else 64)
+    ncell = int(np.prod(ws["n"]))
+    for _ in range(min(args.warmup, 1)):
+        run_oracle_steps(ws, 1)
+    total, steps_run = 0.0, 0
+    for _ in range(args.steps):
+        total += run_oracle_steps(ws, 1)
+        steps_run += 1
+        if total > 150.0:   # keep the reference arm within a few minutes
+            break
+    mlups = ncell * steps_run / total / 1e6
+    cb = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+          "sample": "one LBM step of a %s sub-box of %s per step (static particles, FP64, 1 thread)"
+                    % ("x".join(map(str, ws["n"])), args.workload)}
+    return {"metric": "PSC collide-stream + DEM step throughput (MLUPS)", "value": round(mlups, 3),
+            "unit": "MLUPS", "impl": "reference", "n_gpus": world, "steps": steps_run,
+            "warmup": args.warmup, "ms_per_step": total / steps_run * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: %s" % (args.workload, WORKLOAD_TEXT.get(args.workload, ""))},
+            "cpu_baseline": cb,
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line))
+        return 0
+    import torch
+    init_dist(world, "nccl" if torch.cuda.is_available() else "gloo")
+    line = run_ours(args, rank, local_rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

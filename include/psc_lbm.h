@@ -1,0 +1,193 @@
+/*
+ * psc_lbm.h -- C ABI of the GB300 (sm_103a) library for the lattice-Boltzmann step with the
+ * modified partially-saturated-cell (PSC) immersed moving boundary and the adhesive (JKR)
+ * DEM contact update of Liu & Wu, "A hybrid LBM-DEM framework with an improved immersed
+ * moving boundary method for modelling complex particle-liquid flows involving adhesive
+ * particles" (arXiv 1901.09745).
+ *
+ * Conventions shared by every entry point
+ *  - Lattice units: spacing and time step are 1; cell n has its centre at the integer
+ *    coordinates (x, y, z), 0 <= x < nx etc. Positions, velocities (lattice units per
+ *    step), spins and radii are in these units.
+ *  - A wall axis (LBM_BC_BOUNCEBACK) has halfway bounce-back walls (Eq. 6) half a spacing
+ *    beyond the first and the last node, at -1/2 and n - 1/2.
+ *  - Population arrays exchanged with the caller are full f_i, FP64 (the device state
+ *    itself stores deviations f_i - w_i in every precision),
+ *    layout [Q][nz][ny][nx] (x fastest), in the velocity order below; they hold the
+ *    pre-collision populations f_i(x, t) of Eq. 1.
+ *      D2Q9 : 0 rest; 1 +x; 2 -x; 3 +y; 4 -y; 5 (+1,+1); 6 (-1,-1); 7 (+1,-1); 8 (-1,+1)
+ *      D3Q19: 0 rest; 1 +x; 2 -x; 3 +y; 4 -y; 5 +z; 6 -z; 7 (1,1,0); 8 (-1,-1,0);
+ *             9 (1,-1,0); 10 (-1,1,0); 11 (1,0,1); 12 (-1,0,-1); 13 (1,0,-1); 14 (-1,0,1);
+ *             15 (0,1,1); 16 (0,-1,-1); 17 (0,1,-1); 18 (0,-1,1)
+ *  - Particle vectors are arrays of n x 3 doubles (x, y, z per particle; z = 0 in 2D;
+ *    in 2D only the z component of a spin or a torque is used).
+ *  - Ownership: the caller owns every array it passes; the library copies what it needs
+ *    and owns all device state held by a context. `on_device` = 1 means the pointer is a
+ *    CUDA device pointer on the context's device, 0 means host memory.
+ *  - Ordering: work is queued on the context's stream (lbm_params.stream, or a stream the
+ *    library creates). Calls that return data in host memory synchronise that stream.
+ *  - Errors: every call returns an lbm_status and never aborts; a device-side error
+ *    (unstable density, contact solver failure) is recorded in a flag word on the device
+ *    and reported by the next call that synchronises. lbm_last_error() gives a message.
+ */
+#ifndef PSC_LBM_H
+#define PSC_LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;   /* opaque, library-owned fluid + particle state */
+typedef struct dem_ctx dem_ctx;   /* opaque, library-owned contact state */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,            /* invalid argument (message in lbm_last_error) */
+    LBM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    LBM_ERR_OOM = 3,            /* device allocation failed */
+    LBM_ERR_UNSUPPORTED = 4,    /* valid request this build does not provide */
+    LBM_ERR_UNSTABLE = 5,       /* a cell reached a non-positive or NaN density */
+    LBM_ERR_OVERFLOW = 6,       /* a fixed-capacity list overflowed */
+    LBM_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
+    DEM_ERR_NO_CONVERGENCE = 8  /* the JKR contact-radius solve did not converge */
+} lbm_status;
+
+enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+/* Population storage. Compute is FP64 for LBM_F64 and FP32 for the others. Every form
+ * stores deviations f_i - w_i from the lattice weights. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_DEV = 2, LBM_BF16_DEV = 3 };
+/* LBM_PSC_MODIFIED: Eq. 12-14 (per-particle weights, Eq. 13); LBM_PSC_ORIGINAL: Eq. 7-9, 11. */
+enum { LBM_PSC_MODIFIED = 0, LBM_PSC_ORIGINAL = 1 };
+
+typedef struct {
+    int lattice;            /* LBM_D2Q9 | LBM_D3Q19 (Sec. 2.1) */
+    int nx, ny, nz;         /* lattice extent; nz = 1 for D2Q9 */
+    int bc[3];              /* per axis: LBM_BC_PERIODIC | LBM_BC_BOUNCEBACK (Sec. 2.2) */
+    double tau;             /* relaxation parameter tau > 1/2 (Eq. 2); nu = (tau - 1/2)/3 */
+    double body_force[3];   /* macroscopic body force F of Eq. 4 */
+    int storage;            /* LBM_F64 | LBM_F32 | LBM_F16_DEV | LBM_BF16_DEV */
+    int psc;                /* LBM_PSC_MODIFIED (default) | LBM_PSC_ORIGINAL */
+    double shell_h;         /* h of Table 1 (<= 0 selects 1.0) */
+    double dev_scale;       /* FP16/BF16 deviation scale s: stored value = s (f_i - w_i);
+                               <= 0 selects 4096 for FP16 and 1 for BF16 */
+    int tile_cap;           /* candidate particles kept per lattice tile (<= 0: 64) */
+    void *stream;           /* cudaStream_t to queue work on; NULL: the library makes one */
+} lbm_params;
+
+/* Create a fluid at rest, f_i = f_i^eq(rho = 1, u = 0) = w_i (Eq. 3), with no particles.
+ * Validates the parameters (LBM_ERR_ARG with a message on failure) and allocates the two
+ * population buffers on the current CUDA device. *out receives the new context. */
+lbm_status lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Release every device and host resource of the context (NULL is accepted). */
+lbm_status lbm_destroy(lbm_ctx *ctx);
+
+/* Replace the particle set: n particles with centres X, velocities U, spins Omega (each
+ * n x 3) and radii (n), used by Eq. 10 (u_s = U + Omega x (x_n - X), Eq. 12) and by the
+ * solid fractions of Table 1. Radii must satisfy r^2 > 1/2 in 3D (Eq. 17 is defined) and
+ * r^2 > 1/4 in 2D (Eq. 19), and
+ * a periodic axis must be longer than 2 (r + h) + 1. The data is copied. n = 0 removes all
+ * particles. */
+lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
+                             const double *Omega, const double *radius, int on_device);
+
+/* Advance nsteps lattice-Boltzmann steps. Each step bins the particles into lattice tiles,
+ * computes every cell's solid fractions (Eq. 15-18, Table 1), weights (Eq. 9, 13),
+ * collision (Eq. 2-5, 10, 12), streaming (Eq. 1, 6, periodic wrap) and the per-particle
+ * force and torque (Eq. 14). Asynchronous on the context's stream. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Force F and torque T (n x 3 each) on every particle from the last step's collision
+ * (Eq. 14; Eq. 11 in original mode). Zero before the first step. Synchronises when the
+ * destination is host memory. */
+lbm_status lbm_get_forces(lbm_ctx *ctx, double *F, double *T, int on_device);
+
+/* Density rho (ncell) and force-shifted velocity u (ncell x 3) of Eq. 5 at the current
+ * time, layout [nz][ny][nx] (u: [nz][ny][nx][3]). */
+lbm_status lbm_get_macro(lbm_ctx *ctx, double *rho, double *u, int on_device);
+
+/* Read or overwrite the pre-collision populations f_i(x, t) (layout above). Setting
+ * converts to the context's storage format (rounding to nearest). */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
+
+/* Checkpoint: raw copy of the populations, particles and step counter into a caller
+ * buffer (host). With buf = NULL, *used receives the size needed. lbm_load_state
+ * restores a buffer written by lbm_save_state of a context with identical parameters. */
+lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t *used);
+lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size);
+
+/* Counters (the first n of): out[0] = steps taken, out[1] = tiles whose candidate list
+ * overflowed tile_cap in the last binning (handled by a slower exact path, never an
+ * error), out[2] = largest candidate count of a tile in the last binning, out[3] =
+ * particles, out[4] = kernels launched by this context, out[5] = of which fused
+ * collide-stream launches. Synchronises the stream. */
+lbm_status lbm_get_info(lbm_ctx *ctx, long long *out, int n);
+
+/* Optional CUDA-event timing of every fused collide-stream launch (used by the benchmark
+ * to measure the kernel's own duration inside a timed run). A call returns, in *ms_total
+ * and *launches (either may be NULL), the summed device time and the number of launches
+ * timed since the previous call, synchronising the stream, then enables (enable = 1) or
+ * disables timing for the launches that follow. */
+lbm_status lbm_kernel_timing(lbm_ctx *ctx, int enable, double *ms_total, long long *launches);
+
+/* ------------------------------------------------------------------ DEM (Sec. 2.5) --- */
+/* Contact-model parameters, lattice units. One material for all particles (Eq. 25 then
+ * gives 1/E* = 2 (1 - poisson^2) / E and 1/R = 1/r_i + 1/r_j). */
+typedef struct {
+    double E;            /* Young's modulus E_p */
+    double poisson;      /* Poisson ratio sigma, in (-1, 1/2) */
+    double gamma;        /* surface energy (JKR: F_C = 3 pi gamma R, Eq. 27 a0) */
+    double density;      /* particle mass density: spheres m = rho 4/3 pi r^3, discs m = rho pi r^2 */
+    double mu_f;         /* friction coefficient of Eq. 29 */
+    double theta_crit;   /* critical rolling angle of Eq. 29 */
+    double alpha_n;      /* normal damping: eta_N = alpha_n sqrt(m* k_N), k_N = 2 E* a */
+    double k_t_scale;    /* tangential stiffness k_T = k_t_scale 8 G* a */
+    double eta_t_scale;  /* tangential damping eta_T = eta_t_scale eta_N */
+    double dt_dem;       /* DEM time step (LBM steps); lambda = 1 / dt_dem sub-steps per LBM step */
+    double gravity[3];   /* G = m g of Eq. 21 */
+    int adhesive;        /* 1: JKR normal force (Eq. 26); 0: Hertz (non-adhesive comparison) */
+    double skin;         /* neighbour-list skin (<= 0: 0.5); particles may move skin/2 per call */
+} dem_params;
+
+/* Attach a DEM contact model to a fluid context (one per fluid). The DEM moves the fluid
+ * context's particles. */
+lbm_status dem_create(const dem_params *p, lbm_ctx *fluid, dem_ctx **out);
+lbm_status dem_destroy(dem_ctx *dem);
+
+/* Advance `substeps` DEM sub-steps of dt_dem (Eq. 21-29): contact detection (a pair enters
+ * contact at delta_N >= 0 and stays while delta_N > -delta_C), JKR / Hertz normal force,
+ * sliding, twisting and rolling resistance, semi-implicit Euler motion. The hydrodynamic
+ * force and torque of the last lbm_step stay fixed over the sub-steps (Sec. 2.5). The new
+ * positions, velocities and spins replace the fluid context's particle state. */
+lbm_status dem_step(dem_ctx *dem, int substeps);
+
+/* Particle state after the last DEM sub-step (n x 3 each; NULL pointers are skipped). */
+lbm_status dem_get_particles(dem_ctx *dem, double *X, double *U, double *Omega, int on_device);
+
+/* Contacts of the last sub-step as canonical pairs i < j sorted by (i, j), and their
+ * history seen from i (7 doubles each: sliding spring xyz, twist angle, rolling spring
+ * xyz; hist may be NULL). Host memory. LBM_ERR_OVERFLOW if more than cap pairs (*n still
+ * receives the count). */
+lbm_status dem_get_contacts(dem_ctx *dem, int *pairs, double *hist, int cap, int *n);
+
+/* Counters: out[0] DEM kernels launched, out[1] contact solves that did not converge,
+ * out[2] bin/neighbour-list overflows, out[3] skin violations, out[4] particles. */
+lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
+
+/* Lattice tables: e (Q x 3), w (Q), opposite index (Q). Returns Q, or -1 for an unknown
+ * lattice. Pure host function. */
+int lbm_lattice_tables(int lattice, int *e, double *w, int *opp);
+
+/* Message of the last failed call on this context (or of the last failed lbm_create when
+ * ctx is NULL). Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSC_LBM_H */

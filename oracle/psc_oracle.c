@@ -53,7 +53,7 @@
 #define ORA_ERR_OOM 2
 #define ORA_ERR_CAP 3
 
-#define ORA_MAXK 16 /* most particles that may touch one cell */
+#define ORA_MAXK 8 /* most particles that may touch one cell */
 
 typedef struct {
     int lattice;           /* 9 = D2Q9, 19 = D3Q19 */

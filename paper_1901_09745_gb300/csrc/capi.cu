@@ -1,0 +1,566 @@
+// capi.cu -- host side of the C ABI declared in include/psc_lbm.h: context management,
+// argument checking, device buffers, and the per-step launch sequence (bin particles ->
+// fused PSC collide-stream). Every entry point returns an lbm_status and never aborts.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/psc_lbm.h"
+#include "capi_internal.h"
+#include "lattice.cuh"
+#include "psc_internal.h"
+
+namespace psc {
+cudaError_t launch_collide_stream_f64(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
+cudaError_t launch_collide_stream_f32(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
+cudaError_t launch_collide_stream_f16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
+cudaError_t launch_collide_stream_bf16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
+cudaError_t launch_gather_f64(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_gather_f32(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_gather_f16(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_gather_bf16(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_set_f64(int, const double *, void *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_set_f32(int, const double *, void *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_set_f16(int, const double *, void *, const Geom &, const Phys &, cudaStream_t);
+cudaError_t launch_set_bf16(int, const double *, void *, const Geom &, const Phys &, cudaStream_t);
+
+cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout, const Geom &g,
+                                  const Phys &ph, const Tiles &tl, const Parts &pd, int *flags,
+                                  cudaStream_t s) {
+    switch (storage) {
+    case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s);
+    case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s);
+    case ST_F16: return launch_collide_stream_f16(lattice, fin, fout, g, ph, tl, pd, flags, s);
+    default: return launch_collide_stream_bf16(lattice, fin, fout, g, ph, tl, pd, flags, s);
+    }
+}
+cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out, double *rho, double *u,
+                          const Geom &g, const Phys &ph, cudaStream_t s) {
+    switch (storage) {
+    case ST_F64: return launch_gather_f64(lattice, fin, f_out, rho, u, g, ph, s);
+    case ST_F32: return launch_gather_f32(lattice, fin, f_out, rho, u, g, ph, s);
+    case ST_F16: return launch_gather_f16(lattice, fin, f_out, rho, u, g, ph, s);
+    default: return launch_gather_bf16(lattice, fin, f_out, rho, u, g, ph, s);
+    }
+}
+cudaError_t launch_set(int storage, int lattice, const double *f, void *fout, const Geom &g, const Phys &ph,
+                       cudaStream_t s) {
+    switch (storage) {
+    case ST_F64: return launch_set_f64(lattice, f, fout, g, ph, s);
+    case ST_F32: return launch_set_f32(lattice, f, fout, g, ph, s);
+    case ST_F16: return launch_set_f16(lattice, f, fout, g, ph, s);
+    default: return launch_set_bf16(lattice, f, fout, g, ph, s);
+    }
+}
+}  // namespace psc
+
+using namespace psc;
+
+static char g_create_error[512] = "no error";
+
+void ctx_error(lbm_ctx *ctx, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx ? ctx->err : g_create_error, sizeof(g_create_error), fmt, ap);
+    va_end(ap);
+}
+
+lbm_status ctx_cuda(lbm_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return LBM_OK;
+    ctx_error(ctx, "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+#define CK(call, what)                                         \
+    do {                                                       \
+        lbm_status st_ = ctx_cuda(ctx, (call), (what));        \
+        if (st_ != LBM_OK) return st_;                         \
+    } while (0)
+
+static size_t elem_bytes(int storage) {
+    switch (storage) {
+    case LBM_F64: return 8;
+    case LBM_F32: return 4;
+    default: return 2;
+    }
+}
+
+static void free_dev(void **p) {
+    if (*p) cudaFree(*p);
+    *p = NULL;
+}
+
+static void free_particles(lbm_ctx *ctx) {
+    free_dev((void **)&ctx->dX); free_dev((void **)&ctx->dU); free_dev((void **)&ctx->dOm);
+    free_dev((void **)&ctx->dR); free_dev((void **)&ctx->dFr); free_dev((void **)&ctx->dF);
+    free_dev((void **)&ctx->dT);
+    ctx->np_cap = 0;
+}
+
+extern "C" int lbm_lattice_tables(int lattice, int *e, double *w, int *opp_out) {
+    int q;
+    if (lattice == LBM_D2Q9) q = 9;
+    else if (lattice == LBM_D3Q19) q = 19;
+    else return -1;
+    for (int i = 0; i < q; ++i) {
+        int ex, ey, ez;
+        if (q == 9) { ex = D2Q9::ex(i); ey = D2Q9::ey(i); ez = 0; }
+        else { ex = D3Q19::ex(i); ey = D3Q19::ey(i); ez = D3Q19::ez(i); }
+        if (e) { e[3 * i] = ex; e[3 * i + 1] = ey; e[3 * i + 2] = ez; }
+        if (w) w[i] = (q == 9) ? weight<D2Q9>(i) : weight<D3Q19>(i);
+        if (opp_out) opp_out[i] = (q == 9) ? opp<D2Q9>(i) : opp<D3Q19>(i);
+    }
+    return q;
+}
+
+extern "C" const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err : g_create_error; }
+
+static lbm_status validate(const lbm_params *p) {
+    if (!p) { ctx_error(NULL, "params is NULL"); return LBM_ERR_ARG; }
+    if (p->lattice != LBM_D2Q9 && p->lattice != LBM_D3Q19) {
+        ctx_error(NULL, "lattice must be LBM_D2Q9 (9) or LBM_D3Q19 (19), got %d", p->lattice);
+        return LBM_ERR_ARG;
+    }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) {
+        ctx_error(NULL, "lattice extent must be positive, got %d x %d x %d", p->nx, p->ny, p->nz);
+        return LBM_ERR_ARG;
+    }
+    if (p->lattice == LBM_D2Q9 && p->nz != 1) { ctx_error(NULL, "D2Q9 needs nz = 1, got %d", p->nz); return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (p->bc[a] != LBM_BC_PERIODIC && p->bc[a] != LBM_BC_BOUNCEBACK) {
+            ctx_error(NULL, "bc[%d] must be LBM_BC_PERIODIC or LBM_BC_BOUNCEBACK, got %d", a, p->bc[a]);
+            return LBM_ERR_ARG;
+        }
+    if (!(p->tau > 0.5) || !isfinite(p->tau)) { ctx_error(NULL, "tau must exceed 1/2 (nu = (tau - 1/2)/3 > 0), got %g", p->tau); return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->body_force[a])) { ctx_error(NULL, "body force must be finite"); return LBM_ERR_ARG; }
+    if (p->storage < LBM_F64 || p->storage > LBM_BF16_DEV) { ctx_error(NULL, "unknown storage %d", p->storage); return LBM_ERR_ARG; }
+    if (p->psc != LBM_PSC_MODIFIED && p->psc != LBM_PSC_ORIGINAL) { ctx_error(NULL, "unknown psc mode %d", p->psc); return LBM_ERR_ARG; }
+    if (!isfinite(p->shell_h) || p->shell_h > 1e6) { ctx_error(NULL, "shell_h must be finite"); return LBM_ERR_ARG; }
+    if (p->tile_cap > 64) { ctx_error(NULL, "tile_cap must be at most 64, got %d", p->tile_cap); return LBM_ERR_ARG; }
+    if (!isfinite(p->dev_scale)) { ctx_error(NULL, "dev_scale must be finite"); return LBM_ERR_ARG; }
+    double ncell = (double)p->nx * p->ny * p->nz;
+    if (ncell * p->lattice > 4.0e12) { ctx_error(NULL, "lattice too large"); return LBM_ERR_ARG; }
+    const int ty = (p->lattice == LBM_D2Q9) ? D2Q9::TY : D3Q19::TY, tz = (p->lattice == LBM_D2Q9) ? 1 : D3Q19::TZ;
+    if ((p->ny + ty - 1) / ty > 65535 || (p->nz + tz - 1) / tz > 65535) {
+        ctx_error(NULL, "ny or nz too large for the tile grid (at most 65535 tiles per axis)");
+        return LBM_ERR_ARG;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
+    if (!out) { ctx_error(NULL, "out is NULL"); return LBM_ERR_ARG; }
+    *out = NULL;
+    lbm_status st = validate(p);
+    if (st != LBM_OK) return st;
+    lbm_ctx *ctx = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
+    if (!ctx) { ctx_error(NULL, "host allocation failed"); return LBM_ERR_OOM; }
+    ctx->p = *p;
+    if (ctx->p.shell_h <= 0.0) ctx->p.shell_h = 1.0;
+    if (ctx->p.tile_cap <= 0) ctx->p.tile_cap = 64;
+    if (ctx->p.dev_scale <= 0.0) ctx->p.dev_scale = (p->storage == LBM_F16_DEV) ? 4096.0 : 1.0;
+    if (p->storage == LBM_F64 || p->storage == LBM_F32) ctx->p.dev_scale = 1.0;
+    snprintf(ctx->err, sizeof(ctx->err), "no error");
+    ctx->q = p->lattice;
+    ctx->dim = (p->lattice == LBM_D2Q9) ? 2 : 3;
+    ctx->elem = elem_bytes(p->storage);
+    Geom &g = ctx->g;
+    g.n[0] = p->nx; g.n[1] = p->ny; g.n[2] = p->nz;
+    g.ncell = (long long)p->nx * p->ny * p->nz;
+    for (int a = 0; a < 3; ++a) { g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC); g.wrap_img[a] = 0; }
+    if (ctx->dim == 2) { g.t[0] = D2Q9::TX; g.t[1] = D2Q9::TY; g.t[2] = D2Q9::TZ; }
+    else { g.t[0] = D3Q19::TX; g.t[1] = D3Q19::TY; g.t[2] = D3Q19::TZ; }
+    for (int a = 0; a < 3; ++a) g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
+    ctx->ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
+    Phys &ph = ctx->ph;
+    ph.tau = p->tau;
+    for (int a = 0; a < 3; ++a) ph.body_force[a] = p->body_force[a];
+    ph.shell_h = ctx->p.shell_h;
+    ph.scale = ctx->p.dev_scale;
+    ph.psc = p->psc;
+
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess && p->stream) {
+        ctx->stream = (cudaStream_t)p->stream;
+        ctx->own_stream = 0;
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+        ctx->own_stream = 1;
+    }
+    size_t bytes = (size_t)g.ncell * ctx->q * ctx->elem;
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->f[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->f[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->flags, 4 * sizeof(int));
+    // rest state f_i = w_i: every stored deviation is zero (all-zero bits in every format)
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f[0], 0, bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f[1], 0, bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags, 0, 4 * sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx_error(NULL, "lbm_create: %s", cudaGetErrorString(e));
+        lbm_status s2 = (e == cudaErrorMemoryAllocation) ? LBM_ERR_OOM : LBM_ERR_CUDA;
+        lbm_destroy(ctx);
+        return s2;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
+    if (!ctx) return LBM_OK;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->dem) dem_release(ctx->dem);
+    free_dev(&ctx->f[0]); free_dev(&ctx->f[1]);
+    free_dev((void **)&ctx->flags);
+    free_particles(ctx);
+    free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
+    free_dev((void **)&ctx->diag);
+    for (int i = 0; i < ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
+    free(ctx->ev);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    free(ctx);
+    return LBM_OK;
+}
+
+Parts ctx_parts(lbm_ctx *ctx) {
+    Parts pd;
+    pd.n = ctx->np; pd.X = ctx->dX; pd.U = ctx->dU; pd.Om = ctx->dOm; pd.R = ctx->dR; pd.Fr = ctx->dFr;
+    pd.F = ctx->dF; pd.T = ctx->dT;
+    return pd;
+}
+
+static Tiles ctx_tiles(lbm_ctx *ctx) {
+    Tiles tl;
+    tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap; tl.stats = ctx->tile_stats;
+    return tl;
+}
+
+// Minimum-image flags: a periodic axis needs the per-cell minimum image when the tile plus
+// the widest particle shell does not fit well inside half the box.
+void ctx_update_wrap(lbm_ctx *ctx) {
+    for (int a = 0; a < 3; ++a) {
+        double need = ctx->g.t[a] + 2.0 * (ctx->rmax + ctx->p.shell_h) + 2.0;
+        ctx->g.wrap_img[a] = (a < ctx->dim && ctx->g.periodic[a] && ctx->g.n[a] < need) ? 1 : 0;
+    }
+}
+
+lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n) {
+    double rmax = 0.0;
+    const double rmin2 = (ctx->dim == 2) ? 0.25 : 0.5;
+    for (int i = 0; i < n; ++i) {
+        if (!(R[i] * R[i] > rmin2) || !isfinite(R[i])) {
+            ctx_error(ctx, "radius %d = %g: the linear approximation (Eq. 17/19) needs r^2 > %g", i, R[i], rmin2);
+            return LBM_ERR_ARG;
+        }
+        if (R[i] > rmax) rmax = R[i];
+    }
+    for (int a = 0; a < ctx->dim; ++a) {
+        if (ctx->g.periodic[a] && n > 0 && ctx->g.n[a] <= (int)floor(2.0 * (rmax + ctx->p.shell_h)) + 1) {
+            ctx_error(ctx, "periodic axis %d of length %d is too short for radius %g and h %g", a, ctx->g.n[a], rmax,
+                      ctx->p.shell_h);
+            return LBM_ERR_ARG;
+        }
+    }
+    ctx->rmax = rmax;
+    return LBM_OK;
+}
+
+lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n) {
+    if (n <= ctx->np_cap) return LBM_OK;
+    free_particles(ctx);
+    size_t v = (size_t)n * 3 * sizeof(double), s = (size_t)n * sizeof(double);
+    CK(cudaMalloc(&ctx->dX, v), "cudaMalloc(X)");
+    CK(cudaMalloc(&ctx->dU, v), "cudaMalloc(U)");
+    CK(cudaMalloc(&ctx->dOm, v), "cudaMalloc(Omega)");
+    CK(cudaMalloc(&ctx->dR, s), "cudaMalloc(radius)");
+    CK(cudaMalloc(&ctx->dFr, s), "cudaMalloc(f(r))");
+    CK(cudaMalloc(&ctx->dF, v), "cudaMalloc(F)");
+    CK(cudaMalloc(&ctx->dT, v), "cudaMalloc(T)");
+    CK(cudaMemsetAsync(ctx->dF, 0, v, ctx->stream), "memset F");
+    CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
+    ctx->np_cap = n;
+    return LBM_OK;
+}
+
+static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
+    if (ctx->tile_count) return LBM_OK;
+    CK(cudaMalloc(&ctx->tile_count, (size_t)ctx->ntiles * sizeof(int)), "cudaMalloc(tile counts)");
+    CK(cudaMalloc(&ctx->tile_list, (size_t)ctx->ntiles * ctx->p.tile_cap * sizeof(int)), "cudaMalloc(tile lists)");
+    CK(cudaMalloc(&ctx->tile_stats, 4 * sizeof(int)), "cudaMalloc(tile stats)");
+    CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
+                                        const double *Omega, const double *radius, int on_device) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (n < 0) { ctx_error(ctx, "particle count must be >= 0, got %d", n); return LBM_ERR_ARG; }
+    if (n > 0 && (!X || !U || !Omega || !radius)) { ctx_error(ctx, "particle arrays must not be NULL"); return LBM_ERR_ARG; }
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // validate radii on the host (device radii are copied back once)
+    double *hr = NULL;
+    if (n > 0) {
+        if (on_device) {
+            hr = (double *)malloc((size_t)n * sizeof(double));
+            if (!hr) { ctx_error(ctx, "host allocation failed"); return LBM_ERR_OOM; }
+            cudaError_t e = cudaMemcpyAsync(hr, radius, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) { free(hr); return ctx_cuda(ctx, e, "copy radii"); }
+        }
+        lbm_status st = ctx_check_radii(ctx, on_device ? hr : radius, n);
+        free(hr);
+        if (st != LBM_OK) return st;
+        if (!on_device) {
+            for (int i = 0; i < 3 * n; ++i)
+                if (!isfinite(X[i]) || !isfinite(U[i]) || !isfinite(Omega[i])) {
+                    ctx_error(ctx, "particle %d has a non-finite position, velocity or spin", i / 3);
+                    return LBM_ERR_ARG;
+                }
+        }
+    }
+    lbm_status st = ctx_reserve_particles(ctx, n);
+    if (st != LBM_OK) return st;
+    if (n > 0) {
+        size_t v = (size_t)n * 3 * sizeof(double), s = (size_t)n * sizeof(double);
+        CK(cudaMemcpyAsync(ctx->dX, X, v, kind, ctx->stream), "copy X");
+        CK(cudaMemcpyAsync(ctx->dU, U, v, kind, ctx->stream), "copy U");
+        CK(cudaMemcpyAsync(ctx->dOm, Omega, v, kind, ctx->stream), "copy Omega");
+        CK(cudaMemcpyAsync(ctx->dR, radius, s, kind, ctx->stream), "copy radius");
+        CK(cudaMemsetAsync(ctx->dF, 0, v, ctx->stream), "memset F");
+        CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
+        CK(launch_f_of_r(ctx->dim, ctx->dR, ctx->dFr, n, ctx->stream), "f(r) kernel");
+        st = ctx_reserve_tiles(ctx);
+        if (st != LBM_OK) return st;
+        if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "set_particles sync");
+    }
+    ctx->np = n;
+    ctx->bins_valid = 0;
+    ctx_update_wrap(ctx);
+    return LBM_OK;
+}
+
+lbm_status ctx_bin(lbm_ctx *ctx) {
+    if (ctx->np <= 0) return LBM_OK;
+    Tiles tl = ctx_tiles(ctx);
+    CK(cudaMemsetAsync(ctx->tile_count, 0, (size_t)ctx->ntiles * sizeof(int), ctx->stream), "memset tile counts");
+    CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
+    CK(launch_bin(ctx->dim, ctx->g, ctx->ph, tl, ctx_parts(ctx), ctx->stream), "bin kernel");
+    ctx->launches += 1;
+    ctx->bins_valid = 1;
+    return LBM_OK;
+}
+
+lbm_status ctx_step_once(lbm_ctx *ctx) {
+    if (ctx->np > 0) {
+        if (!ctx->bins_valid) {
+            lbm_status st = ctx_bin(ctx);
+            if (st != LBM_OK) return st;
+        } else {
+            size_t v = (size_t)ctx->np * 3 * sizeof(double);
+            CK(cudaMemsetAsync(ctx->dF, 0, v, ctx->stream), "memset F");
+            CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
+        }
+    }
+    cudaEvent_t *ev = NULL;
+    if (ctx->timing) {
+        if (ctx->ev_used + 2 > ctx->ev_cap) {
+            int cap = ctx->ev_cap ? 2 * ctx->ev_cap : 256;
+            cudaEvent_t *nev = (cudaEvent_t *)realloc(ctx->ev, sizeof(cudaEvent_t) * cap);
+            if (!nev) { ctx_error(ctx, "host allocation failed"); return LBM_ERR_OOM; }
+            ctx->ev = nev;
+            for (int i = ctx->ev_cap; i < cap; ++i) CK(cudaEventCreate(&ctx->ev[i]), "cudaEventCreate");
+            ctx->ev_cap = cap;
+        }
+        ev = &ctx->ev[ctx->ev_used];
+        ctx->ev_used += 2;
+        CK(cudaEventRecord(ev[0], ctx->stream), "cudaEventRecord");
+    }
+    CK(launch_collide_stream(ctx->p.storage, ctx->q, ctx->f[ctx->cur], ctx->f[ctx->cur ^ 1], ctx->g, ctx->ph,
+                             ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream),
+       "collide-stream kernel");
+    if (ev) CK(cudaEventRecord(ev[1], ctx->stream), "cudaEventRecord");
+    ctx->launches += 1;
+    ctx->cs_launches += 1;
+    ctx->cur ^= 1;
+    ctx->steps += 1;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 0) { ctx_error(ctx, "nsteps must be >= 0, got %d", nsteps); return LBM_ERR_ARG; }
+    for (int s = 0; s < nsteps; ++s) {
+        lbm_status st = ctx_step_once(ctx);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+// Read the device flag word after a synchronisation and turn it into a status.
+lbm_status ctx_check_flags(lbm_ctx *ctx) {
+    int h[4];
+    CK(cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "read flags");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    if (h[0] & 1) { ctx_error(ctx, "a cell reached a non-positive or NaN density (unstable run)"); return LBM_ERR_UNSTABLE; }
+    if (h[1]) { ctx_error(ctx, "JKR contact-radius solve did not converge for %d contacts", h[1]); return DEM_ERR_NO_CONVERGENCE; }
+    if (h[2]) { ctx_error(ctx, "%d DEM bin or neighbour-list overflows (more neighbours than slots)", h[2]); return LBM_ERR_OVERFLOW; }
+    if (h[3]) { ctx_error(ctx, "%d particle moves exceeded half the DEM neighbour-list skin in one call; raise dem_params.skin", h[3]); return LBM_ERR_OVERFLOW; }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_forces(lbm_ctx *ctx, double *F, double *T, int on_device) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (ctx->np == 0) return on_device ? LBM_OK : ctx_check_flags(ctx);
+    if (!F && !T) { ctx_error(ctx, "F and T are both NULL"); return LBM_ERR_ARG; }
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    size_t v = (size_t)ctx->np * 3 * sizeof(double);
+    if (F) CK(cudaMemcpyAsync(F, ctx->dF, v, kind, ctx->stream), "copy F");
+    if (T) CK(cudaMemcpyAsync(T, ctx->dT, v, kind, ctx->stream), "copy T");
+    if (!on_device) return ctx_check_flags(ctx);
+    return LBM_OK;
+}
+
+static lbm_status ctx_diag(lbm_ctx *ctx, size_t doubles) {
+    if (ctx->diag_cap >= doubles) return LBM_OK;
+    free_dev((void **)&ctx->diag);
+    ctx->diag_cap = 0;
+    CK(cudaMalloc(&ctx->diag, doubles * sizeof(double)), "cudaMalloc(diagnostics)");
+    ctx->diag_cap = doubles;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_macro(lbm_ctx *ctx, double *rho, double *u, int on_device) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!rho && !u) { ctx_error(ctx, "rho and u are both NULL"); return LBM_ERR_ARG; }
+    size_t nc = (size_t)ctx->g.ncell;
+    if (on_device) {
+        CK(launch_gather(ctx->p.storage, ctx->q, ctx->f[ctx->cur], NULL, rho, u, ctx->g, ctx->ph, ctx->stream), "gather");
+        return LBM_OK;
+    }
+    lbm_status st = ctx_diag(ctx, nc * 4);
+    if (st != LBM_OK) return st;
+    double *drho = ctx->diag, *du = ctx->diag + nc;
+    CK(launch_gather(ctx->p.storage, ctx->q, ctx->f[ctx->cur], NULL, drho, du, ctx->g, ctx->ph, ctx->stream), "gather");
+    if (rho) CK(cudaMemcpyAsync(rho, drho, nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy rho");
+    if (u) CK(cudaMemcpyAsync(u, du, 3 * nc * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy u");
+    return ctx_check_flags(ctx);
+}
+
+extern "C" lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device) {
+    if (!ctx || !f) { if (ctx) ctx_error(ctx, "f is NULL"); return LBM_ERR_ARG; }
+    size_t n = (size_t)ctx->g.ncell * ctx->q;
+    if (on_device) {
+        CK(launch_gather(ctx->p.storage, ctx->q, ctx->f[ctx->cur], f, NULL, NULL, ctx->g, ctx->ph, ctx->stream), "gather");
+        return LBM_OK;
+    }
+    lbm_status st = ctx_diag(ctx, n);
+    if (st != LBM_OK) return st;
+    CK(launch_gather(ctx->p.storage, ctx->q, ctx->f[ctx->cur], ctx->diag, NULL, NULL, ctx->g, ctx->ph, ctx->stream), "gather");
+    CK(cudaMemcpyAsync(f, ctx->diag, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "copy f");
+    return ctx_check_flags(ctx);
+}
+
+extern "C" lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device) {
+    if (!ctx || !f) { if (ctx) ctx_error(ctx, "f is NULL"); return LBM_ERR_ARG; }
+    size_t n = (size_t)ctx->g.ncell * ctx->q;
+    const double *src = f;
+    if (!on_device) {
+        lbm_status st = ctx_diag(ctx, n);
+        if (st != LBM_OK) return st;
+        CK(cudaMemcpyAsync(ctx->diag, f, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "copy f");
+        src = ctx->diag;
+    }
+    CK(launch_set(ctx->p.storage, ctx->q, src, ctx->f[ctx->cur], ctx->g, ctx->ph, ctx->stream), "set kernel");
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return LBM_OK;
+}
+
+// Checkpoint layout: header (8 x int64), then the raw current population buffer, then
+// X, U, Omega (n x 3 doubles each) and the radii.
+struct StateHeader {
+    long long magic, q, nx, ny, nz, storage, np, steps;
+};
+static const long long kStateMagic = 0x5053434c424d3031LL;  // "PSCLBM01"
+
+extern "C" lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t *used) {
+    if (!ctx || !used) return LBM_ERR_ARG;
+    size_t pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
+    size_t part = (size_t)ctx->np * 10 * sizeof(double);
+    size_t need = sizeof(StateHeader) + pop + part;
+    *used = need;
+    if (!buf) return LBM_OK;
+    if (cap < need) { ctx_error(ctx, "state buffer too small: need %zu bytes, have %zu", need, cap); return LBM_ERR_ARG; }
+    StateHeader h = {kStateMagic, ctx->q, ctx->g.n[0], ctx->g.n[1], ctx->g.n[2], ctx->p.storage, ctx->np, ctx->steps};
+    memcpy(buf, &h, sizeof(h));
+    char *p = (char *)buf + sizeof(h);
+    CK(cudaMemcpyAsync(p, ctx->f[ctx->cur], pop, cudaMemcpyDeviceToHost, ctx->stream), "save populations");
+    p += pop;
+    size_t v = (size_t)ctx->np * 3 * sizeof(double);
+    if (ctx->np > 0) {
+        CK(cudaMemcpyAsync(p, ctx->dX, v, cudaMemcpyDeviceToHost, ctx->stream), "save X"); p += v;
+        CK(cudaMemcpyAsync(p, ctx->dU, v, cudaMemcpyDeviceToHost, ctx->stream), "save U"); p += v;
+        CK(cudaMemcpyAsync(p, ctx->dOm, v, cudaMemcpyDeviceToHost, ctx->stream), "save Omega"); p += v;
+        CK(cudaMemcpyAsync(p, ctx->dR, (size_t)ctx->np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "save radius");
+    }
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size) {
+    if (!ctx || !buf) return LBM_ERR_ARG;
+    StateHeader h;
+    if (size < sizeof(h)) { ctx_error(ctx, "state buffer too small"); return LBM_ERR_ARG; }
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic || h.q != ctx->q || h.nx != ctx->g.n[0] || h.ny != ctx->g.n[1] || h.nz != ctx->g.n[2] ||
+        h.storage != ctx->p.storage || h.np < 0) {
+        ctx_error(ctx, "state buffer does not match this context");
+        return LBM_ERR_ARG;
+    }
+    size_t pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
+    size_t v = (size_t)h.np * 3 * sizeof(double);
+    if (size < sizeof(h) + pop + (size_t)h.np * 10 * sizeof(double)) { ctx_error(ctx, "state buffer truncated"); return LBM_ERR_ARG; }
+    const char *p = (const char *)buf + sizeof(h);
+    CK(cudaMemcpyAsync(ctx->f[ctx->cur], p, pop, cudaMemcpyHostToDevice, ctx->stream), "load populations");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    p += pop;
+    lbm_status st = lbm_set_particles(ctx, (int)h.np, (const double *)p, (const double *)(p + v),
+                                      (const double *)(p + 2 * v), (const double *)(p + 3 * v), 0);
+    if (st != LBM_OK) return st;
+    ctx->steps = h.steps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_get_info(lbm_ctx *ctx, long long *out, int n) {
+    if (!ctx || !out || n < 1) return LBM_ERR_ARG;
+    int stats[4] = {0, 0, 0, 0};
+    if (ctx->tile_stats) {
+        CK(cudaMemcpyAsync(stats, ctx->tile_stats, sizeof(stats), cudaMemcpyDeviceToHost, ctx->stream), "read stats");
+        CK(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+    long long vals[6] = {ctx->steps, stats[0], stats[1], ctx->np, ctx->launches, ctx->cs_launches};
+    for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_kernel_timing(lbm_ctx *ctx, int enable, double *ms_total, long long *launches) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (ms_total || launches) {
+        double tot = 0.0;
+        if (ctx->ev_used > 0) CK(cudaStreamSynchronize(ctx->stream), "sync");
+        for (int i = 0; i + 1 < ctx->ev_used; i += 2) {
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]), "cudaEventElapsedTime");
+            tot += ms;
+        }
+        if (ms_total) *ms_total = tot;
+        if (launches) *launches = ctx->ev_used / 2;
+    }
+    ctx->ev_used = 0;   // every query (or toggle) starts a new timing window
+    ctx->timing = enable ? 1 : 0;
+    return LBM_OK;
+}

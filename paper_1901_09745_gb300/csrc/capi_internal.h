@@ -1,0 +1,58 @@
+// capi_internal.h -- the library-owned context behind the opaque lbm_ctx handle, shared by
+// the C ABI translation units (fluid and DEM).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/psc_lbm.h"
+#include "psc_internal.h"
+
+struct lbm_ctx {
+    lbm_params p;              // parameters with defaults filled in
+    int q, dim;
+    size_t elem;               // bytes per stored population
+    psc::Geom g;
+    psc::Phys ph;
+    void *f[2];                // population buffers (post-collision state lives in f[cur])
+    int cur;
+    cudaStream_t stream;
+    int own_stream;
+    int device;
+    int *flags;                // device flag word: [0] bit 0 unstable density, [1] DEM failures
+
+    // particles (FP64, device)
+    int np, np_cap;
+    double *dX, *dU, *dOm, *dR, *dFr, *dF, *dT;
+    double rmax;
+
+    // tile candidate lists
+    long long ntiles;
+    int *tile_count, *tile_list, *tile_stats;
+    int bins_valid;
+
+    double *diag;              // scratch for host-side diagnostics (macro, populations)
+    size_t diag_cap;
+
+    long long steps;
+    long long launches;        // kernels this context has launched
+    long long cs_launches;     // of which fused collide-stream launches
+
+    // optional CUDA-event timing of the collide-stream kernel (bench / profiling)
+    int timing;
+    cudaEvent_t *ev;           // pairs (start, stop) per timed launch
+    int ev_cap, ev_used;
+
+    dem_ctx *dem;              // attached DEM context, released with the fluid
+    char err[512];
+};
+
+void ctx_error(lbm_ctx *ctx, const char *fmt, ...);
+lbm_status ctx_cuda(lbm_ctx *ctx, cudaError_t e, const char *what);
+lbm_status ctx_check_flags(lbm_ctx *ctx);
+lbm_status ctx_bin(lbm_ctx *ctx);
+lbm_status ctx_step_once(lbm_ctx *ctx);
+psc::Parts ctx_parts(lbm_ctx *ctx);
+void ctx_update_wrap(lbm_ctx *ctx);
+lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n);
+lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n);
+void dem_release(dem_ctx *dem);

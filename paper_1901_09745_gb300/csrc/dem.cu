@@ -1,0 +1,656 @@
+// dem.cu -- adhesive DEM contact update on the GPU (Liu & Wu, arXiv 1901.09745, Sec. 2.5).
+//
+// Per dem_step call (one LBM step):
+//   1. k_dem_bin:  particles into a uniform bin grid (bin side >= 2 r_max + skin).
+//   2. k_dem_nbr:  one warp per particle builds its neighbour list (every j with
+//                  |X_j - X_i| < r_i + r_j + skin), sorted by j, and carries each pair's
+//                  contact history over from the previous list.
+//   3. k_dem_substep (x substeps): one warp per particle, one lane per neighbour:
+//        contact detection in FP64 with IEEE-rounded operations only (no FMA), so both
+//        ends of a pair and a CPU reference agree bit for bit on delta_N;
+//        the contact law in FP32: JKR normal force (Eq. 26-27) with the contact radius
+//        from a bounded Newton solve, damping, sliding / twisting / rolling
+//        spring-dashpot-sliders capped at Eq. 29, assembly of Eq. 22;
+//        per-particle sums in FP64 (warp shuffles) and semi-implicit Euler in FP64
+//        (Eq. 21) with the hydrodynamic force and torque of the last LBM step held fixed
+//        over the sub-steps.
+// Every pair is evaluated by both of its particles (each keeps its own copy of the pair's
+// history); the two views are exact negations of each other, so no atomics are needed and
+// the result does not depend on scheduling.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "capi_internal.h"
+
+namespace {
+
+constexpr int kNB = 32;        // neighbour slots per particle (one warp lane each)
+constexpr int kH = 8;          // history floats per slot: xi_s[3], xi_t, xi_r[3], contact flag
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr double kPi = 3.14159265358979323846;
+
+struct DemGeom {
+    int dim;
+    int n[3];
+    int periodic[3];
+    int nb[3];          // bins per axis
+    int bin_cap;
+    double skin;
+};
+
+struct DemPhys {
+    float Es;           // effective modulus E* of Eq. 25 (one material)
+    float Gs;           // effective shear modulus G*
+    float gamma, mu_f, theta_crit, alpha_n, kt_scale, etat_scale;
+    double dt, density;
+    double g[3];
+    int adhesive;
+    double dc_coef;     // 1 / (2 cbrt(6)) for delta_C = a0^2 / (2 cbrt(6) R)
+};
+
+struct DemBufs {
+    int n;
+    const double *X, *U, *Om, *R;   // state at the start of the sub-step
+    double *Xo, *Uo, *Omo;          // state at its end
+    const double *Ff, *Tf;          // hydrodynamic force / torque (frozen)
+    const double *Xref;             // positions when the neighbour list was built
+    const int *nbr_n, *nbr;         // neighbour count and slots [n][kNB]
+    float *hist;                    // [n][kNB][kH]
+    int *flags;                     // [1] solve failures, [2] list overflow, [3] skin exceeded
+};
+
+__device__ __forceinline__ double min_image_d(double a, double b, int n, int periodic) {
+    double d = __dsub_rn(a, b);
+    if (periodic) {
+        const double half = 0.5 * n;
+        for (int k = 0; k < 4 && d > half; ++k) d = __dsub_rn(d, (double)n);
+        for (int k = 0; k < 4 && d < -half; ++k) d = __dadd_rn(d, (double)n);
+    }
+    return d;
+}
+
+__device__ __forceinline__ int bin_of(double x, int n, int nb, int periodic) {
+    int b = (int)floor(x * nb / n);
+    if (periodic) { b %= nb; if (b < 0) b += nb; }
+    else { b = b < 0 ? 0 : (b >= nb ? nb - 1 : b); }
+    return b;
+}
+
+__global__ void k_dem_bin(DemGeom g, int n, const double *X, int *count, int *list, int *flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) b[a] = bin_of(X[3 * i + a], g.n[a], g.nb[a], g.periodic[a]);
+    const int bin = b[0] + g.nb[0] * (b[1] + g.nb[1] * b[2]);
+    const int slot = atomicAdd(&count[bin], 1);
+    if (slot < g.bin_cap) list[bin * g.bin_cap + slot] = i;
+    else atomicAdd(&flags[2], 1);
+}
+
+// Distinct bin indices along one axis around b (wrapping, clipping, no duplicates).
+__device__ __forceinline__ int axis_bins(int b, int nb, int periodic, int *out) {
+    int k = 0;
+    for (int o = -1; o <= 1; ++o) {
+        int c = b + o;
+        if (periodic) { c %= nb; if (c < 0) c += nb; }
+        else if (c < 0 || c >= nb) continue;
+        bool dup = false;
+        for (int q = 0; q < k; ++q) dup |= (out[q] == c);
+        if (!dup) out[k++] = c;
+    }
+    return k;
+}
+
+__global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, const int *count,
+                          const int *list, const int *old_n, const int *old_nbr, const float *old_hist,
+                          int *new_n, int *new_nbr, float *new_hist, double *Xref, int *flags) {
+    __shared__ int s_buf[8][kNB];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= n) return;   // whole warp leaves together
+    const double xi[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
+    const double ri = R[i];
+    int bx[3], by[3], bz[3], nbx, nby, nbz = 1;
+    nbx = axis_bins(bin_of(xi[0], g.n[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], bx);
+    nby = axis_bins(bin_of(xi[1], g.n[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], by);
+    if (g.dim == 3) nbz = axis_bins(bin_of(xi[2], g.n[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], bz);
+    else bz[0] = 0;
+    int cnt = 0;
+    for (int a = 0; a < nbz; ++a)
+    for (int b = 0; b < nby; ++b)
+    for (int c = 0; c < nbx; ++c) {
+        const int bin = bx[c] + g.nb[0] * (by[b] + g.nb[1] * bz[a]);
+        const int m = min(count[bin], g.bin_cap);
+        for (int t0 = 0; t0 < m; t0 += 32) {
+            const int t = t0 + lane;
+            bool take = false;
+            int j = -1;
+            if (t < m) {
+                j = list[bin * g.bin_cap + t];
+                if (j != i) {
+                    double d2 = 0.0;
+                    for (int ax = 0; ax < g.dim; ++ax) {
+                        const double d = min_image_d(X[3 * j + ax], xi[ax], g.n[ax], g.periodic[ax]);
+                        d2 += d * d;
+                    }
+                    const double reach = ri + R[j] + g.skin;
+                    take = d2 < reach * reach;
+                }
+            }
+            const unsigned bal = __ballot_sync(kFullMask, take);
+            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (take && pos < kNB) s_buf[warp][pos] = j;
+            cnt += __popc(bal);
+        }
+    }
+    if (cnt > kNB) { if (lane == 0) atomicAdd(&flags[2], 1); cnt = kNB; }
+    __syncwarp();
+    // sort the slots by neighbour index (rank sort within the warp)
+    int j = (lane < cnt) ? s_buf[warp][lane] : 0x7fffffff;
+    int rank = 0;
+    for (int q = 0; q < cnt; ++q) rank += (s_buf[warp][q] < j);
+    __syncwarp();
+    if (lane < cnt) s_buf[warp][rank] = j;
+    __syncwarp();
+    if (lane < cnt) {
+        j = s_buf[warp][lane];
+        // carry the pair's history from the previous (sorted) list of i
+        const int on = old_n[i];
+        int lo = 0, hi = on - 1, found = -1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            const int v = old_nbr[i * kNB + mid];
+            if (v == j) { found = mid; break; }
+            if (v < j) lo = mid + 1; else hi = mid - 1;
+        }
+        new_nbr[i * kNB + lane] = j;
+        for (int h = 0; h < kH; ++h)
+            new_hist[((size_t)i * kNB + lane) * kH + h] = (found >= 0) ? old_hist[((size_t)i * kNB + found) * kH + h] : 0.0f;
+    }
+    if (lane == 0) {
+        new_n[i] = cnt;
+        for (int a = 0; a < 3; ++a) Xref[3 * i + a] = xi[a];
+    }
+}
+
+__device__ __forceinline__ void cross3f(const float *a, const float *b, float *c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3f(const float *a, const float *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+__device__ __forceinline__ void rotate_into_plane(float *xi, const float *n) {
+    const float len0 = sqrtf(dot3f(xi, xi));
+    const float dn = dot3f(xi, n);
+    for (int a = 0; a < 3; ++a) xi[a] -= dn * n[a];
+    const float len1 = sqrtf(dot3f(xi, xi));
+    if (len1 > 0.0f) { const float s = len0 / len1; for (int a = 0; a < 3; ++a) xi[a] *= s; }
+}
+
+// JKR contact radius ratio s = sqrt(a/a0) for t = delta R / a0^2 on the stable branch:
+// root of s^4 - (2/3) s - t = 0 with s >= 6^(-1/3). g is convex and increasing there, so
+// Newton started to the right of the root decreases monotonically onto it.
+__device__ __forceinline__ float jkr_s(float t, int *fail) {
+    float s = fmaxf(1.0f, sqrtf(sqrtf(fmaxf(t, 0.0f) + 1.0f)));
+    for (int k = 0; k < 30 && (s * s * s * s - (2.0f / 3.0f) * s - t) < 0.0f; ++k) s *= 1.5f;
+    const float sc = 0.55032120814910446f;   // 6^(-1/3)
+    int it = 0;
+    for (; it < 60; ++it) {
+        const float g = s * s * s * s - (2.0f / 3.0f) * s - t;
+        const float dg = 4.0f * s * s * s - (2.0f / 3.0f);
+        if (!(dg > 0.0f)) break;
+        const float step = g / dg;
+        const float sn = fmaxf(s - step, sc);
+        if (fabsf(sn - s) <= 2e-7f * s) { s = sn; break; }
+        s = sn;
+    }
+    if (it >= 60 || !(s == s)) *fail = 1;
+    return s;
+}
+
+// One contact seen from particle i (neighbour j): force and torque on i in FP32. hist is
+// this view's copy of the pair history; returns 0 and clears it when not in contact.
+__device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, double dist, double dn,
+                             double ri, double rj, double mi, double mj, const double *Ui,
+                             const double *Uj, const double *Omi, const double *Omj, float *h,
+                             float *fo, float *to, int *fail) {
+    const float Rf = (float)(ri * rj / (ri + rj));
+    const float Es = ph.Es;
+    float FC = 0.0f, a0 = 0.0f;
+    const bool was = h[7] != 0.0f;
+    bool contact;
+    if (ph.adhesive) {
+        FC = (float)(3.0 * kPi) * ph.gamma * Rf;
+        a0 = cbrtf((float)(9.0 * kPi) * ph.gamma * Rf * Rf / Es);
+        if (dn >= 0.0) {
+            contact = true;
+        } else if (was) {
+            // per-pair delta_C in FP64, so the persistence test matches a CPU reference
+            const double R64 = ri * rj / (ri + rj);
+            const double a064 = cbrt(9.0 * kPi * (double)ph.gamma * R64 * R64 / (double)Es);
+            const double dC = a064 * a064 * ph.dc_coef / R64;
+            contact = dn > -dC;
+        } else {
+            contact = false;
+        }
+    } else {
+        contact = dn > 0.0;
+    }
+    if (!contact) {
+        for (int k = 0; k < kH; ++k) h[k] = 0.0f;
+        for (int a = 0; a < 3; ++a) { fo[a] = 0.0f; to[a] = 0.0f; }
+        return false;
+    }
+    const double inv = 1.0 / dist;
+    const float n[3] = {(float)(d64[0] * inv), (float)(d64[1] * inv), (float)(d64[2] * inv)};
+    const float dnf = (float)dn;
+    const float rif = (float)ri, rjf = (float)rj;
+    float ac, Fne, kr = 0.0f;
+    if (ph.adhesive) {
+        const float s = jkr_s(dnf * Rf / (a0 * a0), fail);
+        const float s3 = s * s * s;
+        ac = s * s * a0;
+        Fne = 4.0f * FC * (s3 * s3 - s3);          // Eq. 26 with (a/a0)^3 = s^6, (a/a0)^1.5 = s^3
+        kr = 4.0f * FC * s3;
+    } else {
+        const float dp = fmaxf(dnf, 0.0f);
+        ac = sqrtf(Rf * dp);
+        Fne = (4.0f / 3.0f) * Es * sqrtf(Rf) * dp * sqrtf(dp);
+    }
+    const float ms = (float)(mi * mj / (mi + mj));
+    const float kN = 2.0f * Es * ac;
+    const float etaN = ph.alpha_n * sqrtf(ms * kN);
+    const float kT = ph.kt_scale * 8.0f * ph.Gs * ac;
+    const float etaT = ph.etat_scale * etaN;
+    const float dt = (float)ph.dt;
+
+    // relative velocity of the contact points
+    const float arm_i[3] = {rif * n[0], rif * n[1], rif * n[2]};
+    const float arm_j[3] = {-rjf * n[0], -rjf * n[1], -rjf * n[2]};
+    const float omi[3] = {(float)Omi[0], (float)Omi[1], (float)Omi[2]};
+    const float omj[3] = {(float)Omj[0], (float)Omj[1], (float)Omj[2]};
+    float w1[3], w2[3], vij[3], vt[3];
+    cross3f(omi, arm_i, w1);
+    cross3f(omj, arm_j, w2);
+    for (int a = 0; a < 3; ++a) vij[a] = ((float)Ui[a] + w1[a]) - ((float)Uj[a] + w2[a]);
+    const float vn = dot3f(vij, n);
+    for (int a = 0; a < 3; ++a) vt[a] = vij[a] - vn * n[a];
+
+    const float Fn = Fne + etaN * vn;
+
+    // sliding
+    const float Fscrit = ph.mu_f * fabsf(Fne + 2.0f * FC);
+    float *xs = h, *xr = h + 4;
+    rotate_into_plane(xs, n);
+    for (int a = 0; a < 3; ++a) xs[a] += vt[a] * dt;
+    float Ft[3];
+    for (int a = 0; a < 3; ++a) Ft[a] = -kT * xs[a] - etaT * vt[a];
+    float mag = sqrtf(dot3f(Ft, Ft));
+    if (mag > Fscrit) {
+        const float sc = Fscrit / mag;
+        for (int a = 0; a < 3; ++a) Ft[a] *= sc;
+        if (kT > 0.0f) for (int a = 0; a < 3; ++a) xs[a] = -Ft[a] / kT;
+    }
+
+    // twisting
+    const float omrel[3] = {omi[0] - omj[0], omi[1] - omj[1], omi[2] - omj[2]};
+    const float Omt = dot3f(omrel, n);
+    h[3] += Omt * dt;
+    float Mt = -(kT * ac * ac * 0.5f) * h[3] - (etaT * ac * ac * 0.5f) * Omt;
+    const float Mtcrit = (float)(3.0 * kPi / 16.0) * ac * Fscrit;
+    if (fabsf(Mt) > Mtcrit) {
+        Mt = (Mt > 0.0f ? 1.0f : -1.0f) * Mtcrit;
+        if (kT * ac * ac > 0.0f) h[3] = -Mt / (kT * ac * ac * 0.5f);
+    }
+
+    // rolling
+    float Mr[3] = {0.0f, 0.0f, 0.0f};
+    if (ph.adhesive) {
+        const float Mrcrit = kr * ph.theta_crit * Rf;
+        float vL[3], t[3];
+        rotate_into_plane(xr, n);
+        cross3f(n, omrel, vL);
+        for (int a = 0; a < 3; ++a) xr[a] += Rf * vL[a] * dt;
+        cross3f(n, xr, t);
+        for (int a = 0; a < 3; ++a) Mr[a] = kr * t[a];
+        mag = sqrtf(dot3f(Mr, Mr));
+        if (mag > Mrcrit) {
+            const float sc = Mrcrit / mag;
+            for (int a = 0; a < 3; ++a) { Mr[a] *= sc; xr[a] *= sc; }
+        }
+    }
+    h[7] = 1.0f;
+
+    float tq[3];
+    cross3f(arm_i, Ft, tq);
+    for (int a = 0; a < 3; ++a) {
+        fo[a] = -Fn * n[a] + Ft[a];
+        to[a] = tq[a] + Mt * n[a] + Mr[a];
+    }
+    if (dim == 2) { fo[2] = 0.0f; to[0] = 0.0f; to[1] = 0.0f; }
+    return true;
+}
+
+__device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I) {
+    if (dim == 2) { *m = rho * kPi * r * r; *I = 0.5 * (*m) * r * r; }
+    else { *m = rho * (4.0 / 3.0) * kPi * r * r * r; *I = 0.4 * (*m) * r * r; }
+}
+
+__global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= b.n) return;
+    const int dim = g.dim;
+    const double xi[3] = {b.X[3 * i], b.X[3 * i + 1], b.X[3 * i + 2]};
+    const double ui[3] = {b.U[3 * i], b.U[3 * i + 1], b.U[3 * i + 2]};
+    const double oi[3] = {b.Om[3 * i], b.Om[3 * i + 1], b.Om[3 * i + 2]};
+    const double ri = b.R[i];
+    double mi, Ii;
+    mass_inertia(dim, ph.density, ri, &mi, &Ii);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int nn = b.nbr_n[i];
+    int fail = 0;
+    if (lane < nn) {
+        const int j = b.nbr[i * kNB + lane];
+        // overlap in FP64 with IEEE-rounded operations (bit-identical at both ends)
+        double d[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < dim; ++a) d[a] = min_image_d(b.X[3 * j + a], xi[a], g.n[a], g.periodic[a]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+        const double dist = __dsqrt_rn(d2);
+        const double rj = b.R[j];
+        const double dn = __dsub_rn(__dadd_rn(ri, rj), dist);
+        double mj, Ij;
+        mass_inertia(dim, ph.density, rj, &mj, &Ij);
+        float *h = b.hist + ((size_t)i * kNB + lane) * kH;
+        float hl[kH];
+        for (int k = 0; k < kH; ++k) hl[k] = h[k];
+        float fo[3], to[3];
+        const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
+        const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
+        if (contact_on_i(ph, dim, d, dist, dn, ri, rj, mi, mj, ui, uj, oi, oj, hl, fo, to, &fail)) {
+            for (int a = 0; a < 3; ++a) { acc[a] = (double)fo[a]; acc[3 + a] = (double)to[a]; }
+        }
+        for (int k = 0; k < kH; ++k) h[k] = hl[k];
+    }
+    // per-particle sums in FP64, in a fixed lane order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(kFullMask, acc[q], off);
+    if (__any_sync(kFullMask, fail) && lane == 0) atomicAdd(&b.flags[1], 1);
+    if (lane != 0) return;
+    // Eq. 21, semi-implicit Euler, hydrodynamic force/torque frozen over the sub-steps
+    double un[3], xn[3], on[3];
+    for (int a = 0; a < 3; ++a) {
+        if (a < dim) {
+            un[a] = ui[a] + ph.dt * (b.Ff[3 * i + a] + acc[a] + mi * ph.g[a]) / mi;
+            xn[a] = xi[a] + ph.dt * un[a];
+            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] / g.n[a]);
+        } else {
+            un[a] = ui[a];
+            xn[a] = xi[a];
+        }
+        const bool spin = (dim == 3) || (a == 2);
+        on[a] = spin ? oi[a] + ph.dt * (b.Tf[3 * i + a] + acc[3 + a]) / Ii : oi[a];
+    }
+    double disp2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+        const double dd = min_image_d(xn[a], b.Xref[3 * i + a], g.n[a], g.periodic[a]);
+        disp2 += dd * dd;
+    }
+    if (disp2 > 0.25 * g.skin * g.skin) atomicAdd(&b.flags[3], 1);
+    for (int a = 0; a < 3; ++a) { b.Xo[3 * i + a] = xn[a]; b.Uo[3 * i + a] = un[a]; b.Omo[3 * i + a] = on[a]; }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------ host side
+struct dem_ctx {
+    dem_params p;
+    lbm_ctx *fl;
+    int n, cap_n;
+    DemGeom g;
+    DemPhys ph;
+    double *X2, *U2, *Om2, *Xref;
+    int *bin_count, *bin_list;
+    long long nbins;
+    int *nbr_n[2], *nbr[2];
+    float *hist[2];
+    int cur;                 // which neighbour-list buffer is current
+    int lists_valid;
+    long long launches;
+};
+
+static void dfree(void **p) { if (*p) cudaFree(*p); *p = NULL; }
+
+void dem_release(dem_ctx *d) {
+    if (!d) return;
+    dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
+    dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
+    for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
+    free(d);
+}
+
+#define DCK(call, what)                                          \
+    do {                                                         \
+        lbm_status st_ = ctx_cuda(d->fl, (call), (what));        \
+        if (st_ != LBM_OK) return st_;                           \
+    } while (0)
+
+// The DEM's state buffers are swapped with the fluid context's after every sub-step, so
+// both sets must hold the fluid's full particle capacity (not just the current count).
+static lbm_status dem_reserve(dem_ctx *d) {
+    lbm_ctx *fl = d->fl;
+    const int n = fl->np;
+    const int cap = fl->np_cap;
+    d->n = n;
+    if (cap <= d->cap_n) return LBM_OK;
+    dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
+    for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
+    const size_t v = (size_t)cap * 3 * sizeof(double);
+    DCK(cudaMalloc(&d->X2, v), "cudaMalloc(DEM X)");
+    DCK(cudaMalloc(&d->U2, v), "cudaMalloc(DEM U)");
+    DCK(cudaMalloc(&d->Om2, v), "cudaMalloc(DEM Omega)");
+    DCK(cudaMalloc(&d->Xref, v), "cudaMalloc(DEM Xref)");
+    for (int k = 0; k < 2; ++k) {
+        DCK(cudaMalloc(&d->nbr_n[k], (size_t)cap * sizeof(int)), "cudaMalloc(neighbour counts)");
+        DCK(cudaMalloc(&d->nbr[k], (size_t)cap * kNB * sizeof(int)), "cudaMalloc(neighbour lists)");
+        DCK(cudaMalloc(&d->hist[k], (size_t)cap * kNB * kH * sizeof(float)), "cudaMalloc(contact history)");
+        DCK(cudaMemsetAsync(d->nbr_n[k], 0, (size_t)cap * sizeof(int), fl->stream), "memset");
+        DCK(cudaMemsetAsync(d->hist[k], 0, (size_t)cap * kNB * kH * sizeof(float), fl->stream), "memset");
+    }
+    d->cap_n = cap;
+    d->lists_valid = 0;
+    return LBM_OK;
+}
+
+static lbm_status dem_setup_bins(dem_ctx *d) {
+    lbm_ctx *fl = d->fl;
+    const double side = 2.0 * fl->rmax + d->g.skin;
+    long long nb = 1;
+    for (int a = 0; a < 3; ++a) {
+        d->g.nb[a] = (a < d->g.dim) ? (int)(fl->g.n[a] / side) : 1;
+        if (d->g.nb[a] < 1) d->g.nb[a] = 1;
+        nb *= d->g.nb[a];
+    }
+    // bin capacity from the densest possible packing of the smallest admissible particles
+    const double vol = (d->g.dim == 2) ? side * side : side * side * side;
+    const double rmin = (d->g.dim == 2) ? 0.5 : 0.7071;
+    const double pvol = (d->g.dim == 2) ? kPi * rmin * rmin : 4.0 / 3.0 * kPi * rmin * rmin * rmin;
+    int cap = (int)(vol / pvol) + 8;
+    if (cap > 256) cap = 256;
+    if (nb != d->nbins || cap != d->g.bin_cap) {
+        dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
+        DCK(cudaMalloc(&d->bin_count, (size_t)nb * sizeof(int)), "cudaMalloc(DEM bins)");
+        DCK(cudaMalloc(&d->bin_list, (size_t)nb * cap * sizeof(int)), "cudaMalloc(DEM bin lists)");
+        d->nbins = nb;
+        d->g.bin_cap = cap;
+    }
+    return LBM_OK;
+}
+
+static lbm_status dem_build_lists(dem_ctx *d) {
+    lbm_ctx *fl = d->fl;
+    lbm_status st = dem_setup_bins(d);
+    if (st != LBM_OK) return st;
+    const int n = d->n;
+    DCK(cudaMemsetAsync(d->bin_count, 0, (size_t)d->nbins * sizeof(int), fl->stream), "memset DEM bins");
+    k_dem_bin<<<(n + 127) / 128, 128, 0, fl->stream>>>(d->g, n, fl->dX, d->bin_count, d->bin_list, fl->flags);
+    DCK(cudaGetLastError(), "DEM bin kernel");
+    const int nx = d->cur ^ 1;
+    k_dem_nbr<<<(n + 7) / 8, 256, 0, fl->stream>>>(d->g, n, fl->dX, fl->dR, d->bin_count, d->bin_list,
+                                                    d->nbr_n[d->cur], d->nbr[d->cur], d->hist[d->cur],
+                                                    d->nbr_n[nx], d->nbr[nx], d->hist[nx], d->Xref, fl->flags);
+    DCK(cudaGetLastError(), "DEM neighbour kernel");
+    d->cur = nx;
+    d->lists_valid = 1;
+    d->launches += 2;
+    fl->launches += 2;
+    return LBM_OK;
+}
+
+extern "C" lbm_status dem_create(const dem_params *p, lbm_ctx *fluid, dem_ctx **out) {
+    if (!fluid || !p || !out) return LBM_ERR_ARG;
+    *out = NULL;
+    if (!(p->E > 0) || !(p->poisson > -1.0 && p->poisson < 0.5) || !(p->density > 0) || !(p->dt_dem > 0) ||
+        p->gamma < 0 || p->mu_f < 0 || p->theta_crit < 0 || p->alpha_n < 0 || p->k_t_scale < 0 ||
+        p->eta_t_scale < 0 || (p->adhesive && !(p->gamma > 0))) {
+        ctx_error(fluid, "invalid DEM parameters (E > 0, -1 < poisson < 1/2, density > 0, dt > 0, "
+                         "non-negative friction/damping, gamma > 0 for JKR)");
+        return LBM_ERR_ARG;
+    }
+    if (fluid->dem) { ctx_error(fluid, "the fluid context already has a DEM context"); return LBM_ERR_ARG; }
+    dem_ctx *d = (dem_ctx *)calloc(1, sizeof(dem_ctx));
+    if (!d) return LBM_ERR_OOM;
+    d->p = *p;
+    d->fl = fluid;
+    d->g.dim = fluid->dim;
+    for (int a = 0; a < 3; ++a) { d->g.n[a] = fluid->g.n[a]; d->g.periodic[a] = fluid->g.periodic[a]; }
+    d->g.skin = p->skin > 0 ? p->skin : 0.5;
+    d->ph.Es = (float)(p->E / (2.0 * (1.0 - p->poisson * p->poisson)));
+    d->ph.Gs = (float)(p->E / (4.0 * (2.0 - p->poisson) * (1.0 + p->poisson)));
+    d->ph.gamma = (float)p->gamma;
+    d->ph.mu_f = (float)p->mu_f;
+    d->ph.theta_crit = (float)p->theta_crit;
+    d->ph.alpha_n = (float)p->alpha_n;
+    d->ph.kt_scale = (float)p->k_t_scale;
+    d->ph.etat_scale = (float)p->eta_t_scale;
+    d->ph.dt = p->dt_dem;
+    d->ph.density = p->density;
+    for (int a = 0; a < 3; ++a) d->ph.g[a] = p->gravity[a];
+    d->ph.adhesive = p->adhesive ? 1 : 0;
+    d->ph.dc_coef = 1.0 / (2.0 * cbrt(6.0));
+    fluid->dem = d;
+    *out = d;
+    return LBM_OK;
+}
+
+extern "C" lbm_status dem_destroy(dem_ctx *d) {
+    if (!d) return LBM_OK;
+    if (d->fl) { cudaStreamSynchronize(d->fl->stream); d->fl->dem = NULL; }
+    dem_release(d);
+    return LBM_OK;
+}
+
+extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
+    if (!d) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    if (substeps < 0) { ctx_error(fl, "substeps must be >= 0"); return LBM_ERR_ARG; }
+    if (fl->np == 0 || substeps == 0) return LBM_OK;
+    if (fl->np != d->n) d->lists_valid = 0;
+    lbm_status st = dem_reserve(d);
+    if (st != LBM_OK) return st;
+    st = dem_build_lists(d);
+    if (st != LBM_OK) return st;
+    DemBufs b;
+    b.n = d->n;
+    b.R = fl->dR;
+    b.Ff = fl->dF;
+    b.Tf = fl->dT;
+    b.Xref = d->Xref;
+    b.nbr_n = d->nbr_n[d->cur];
+    b.nbr = d->nbr[d->cur];
+    b.hist = d->hist[d->cur];
+    b.flags = fl->flags;
+    const int blocks = (d->n + 7) / 8;
+    for (int s = 0; s < substeps; ++s) {
+        b.X = fl->dX; b.U = fl->dU; b.Om = fl->dOm;
+        b.Xo = d->X2; b.Uo = d->U2; b.Omo = d->Om2;
+        k_dem_substep<<<blocks, 256, 0, fl->stream>>>(d->g, d->ph, b);
+        DCK(cudaGetLastError(), "DEM sub-step kernel");
+        // the new state becomes the fluid context's particle state
+        double *t;
+        t = fl->dX; fl->dX = d->X2; d->X2 = t;
+        t = fl->dU; fl->dU = d->U2; d->U2 = t;
+        t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
+        d->launches += 1;
+        fl->launches += 1;
+    }
+    fl->bins_valid = 0;   // particles moved: the fluid re-bins before its next step
+    return LBM_OK;
+}
+
+extern "C" lbm_status dem_get_particles(dem_ctx *d, double *X, double *U, double *Om, int on_device) {
+    if (!d) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    const size_t v = (size_t)fl->np * 3 * sizeof(double);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (fl->np == 0) return LBM_OK;
+    if (X) DCK(cudaMemcpyAsync(X, fl->dX, v, k, fl->stream), "copy X");
+    if (U) DCK(cudaMemcpyAsync(U, fl->dU, v, k, fl->stream), "copy U");
+    if (Om) DCK(cudaMemcpyAsync(Om, fl->dOm, v, k, fl->stream), "copy Omega");
+    if (!on_device) return ctx_check_flags(fl);
+    return LBM_OK;
+}
+
+// Contacts as canonical pairs i < j (sorted) and the history seen from i.
+extern "C" lbm_status dem_get_contacts(dem_ctx *d, int *pairs, double *hist, int cap, int *nout) {
+    if (!d || !nout) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    *nout = 0;
+    if (!d->lists_valid || d->n == 0) return ctx_check_flags(fl);
+    const int n = d->n;
+    int *hn = (int *)malloc((size_t)n * sizeof(int));
+    int *hb = (int *)malloc((size_t)n * kNB * sizeof(int));
+    float *hh = (float *)malloc((size_t)n * kNB * kH * sizeof(float));
+    if (!hn || !hb || !hh) { free(hn); free(hb); free(hh); return LBM_ERR_OOM; }
+    cudaError_t e = cudaMemcpyAsync(hn, d->nbr_n[d->cur], (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d->nbr[d->cur], (size_t)n * kNB * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hh, d->hist[d->cur], (size_t)n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(fl->stream);
+    if (e != cudaSuccess) { free(hn); free(hb); free(hh); return ctx_cuda(fl, e, "copy contacts"); }
+    int k = 0;
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < n; ++i) {
+        for (int s = 0; s < hn[i]; ++s) {
+            const int j = hb[i * kNB + s];
+            const float *h = hh + ((size_t)i * kNB + s) * kH;
+            if (j <= i || h[7] == 0.0f) continue;
+            if (k < cap) {
+                if (pairs) { pairs[2 * k] = i; pairs[2 * k + 1] = j; }
+                if (hist) for (int q = 0; q < 7; ++q) hist[7 * (size_t)k + q] = (double)h[q];
+            } else {
+                st = LBM_ERR_OVERFLOW;
+            }
+            ++k;
+        }
+    }
+    free(hn); free(hb); free(hh);
+    *nout = k;
+    if (st != LBM_OK) { ctx_error(fl, "contact buffer holds %d pairs, %d needed", cap, k); return st; }
+    return ctx_check_flags(fl);
+}
+
+extern "C" lbm_status dem_get_info(dem_ctx *d, long long *out, int n) {
+    if (!d || !out || n < 1) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    int h[4] = {0, 0, 0, 0};
+    DCK(cudaMemcpyAsync(h, fl->flags, sizeof(h), cudaMemcpyDeviceToHost, fl->stream), "read flags");
+    DCK(cudaStreamSynchronize(fl->stream), "sync");
+    long long vals[5] = {d->launches, h[1], h[2], h[3], d->n};
+    for (int i = 0; i < n && i < 5; ++i) out[i] = vals[i];
+    return LBM_OK;
+}

@@ -1,0 +1,92 @@
+// psc_bin.cu -- particle binning into lattice-tile candidate lists, and f(r) per particle.
+//
+// Table 1 of the paper loops over particles and, for each, over the cells of its bounding
+// box. On the GPU the loop is inverted: each particle inserts itself into every lattice
+// tile that its (r + h)-widened bounding box meets, so the fused collide-stream kernel can
+// hold the tile's few candidates in shared memory and evaluate every cell against them.
+#include <math.h>
+
+#include "psc_internal.h"
+
+namespace psc {
+
+// Tile ranges along one axis covered by the cell interval [lo, hi] (cell centres within
+// r + h of the particle centre). Periodic axes wrap (at most two pieces, merged when they
+// meet); wall axes clip to the lattice. Returns the number of ranges (0..2).
+__device__ __forceinline__ int axis_tile_ranges(long long lo, long long hi, int n, int t, int nt,
+                                                int periodic, int *a, int *b) {
+    if (periodic) {
+        if (hi - lo + 1 >= n) { a[0] = 0; b[0] = nt - 1; return 1; }
+        const long long A = ((lo % n) + n) % n, B = ((hi % n) + n) % n;
+        if (A <= B) { a[0] = (int)(A / t); b[0] = (int)(B / t); return 1; }
+        const int thi = (int)(A / t), tlo = (int)(B / t);
+        if (tlo >= thi) { a[0] = 0; b[0] = nt - 1; return 1; }
+        a[0] = 0; b[0] = tlo; a[1] = thi; b[1] = nt - 1;
+        return 2;
+    }
+    const long long A = lo < 0 ? 0 : lo, B = hi > n - 1 ? n - 1 : hi;
+    if (A > B) return 0;
+    a[0] = (int)(A / t); b[0] = (int)(B / t);
+    return 1;
+}
+
+__global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= pd.n) return;
+    for (int c = 0; c < 3; ++c) { pd.F[3 * p + c] = 0.0; pd.T[3 * p + c] = 0.0; }
+    int ra[3][2], rb[3][2], nr[3];
+    const double r = pd.R[p];
+    for (int ax = 0; ax < 3; ++ax) {
+        if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; continue; }
+        const double X = pd.X[3 * p + ax];
+        const long long lo = (long long)ceil(X - r - h), hi = (long long)floor(X + r + h);
+        nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
+    }
+    for (int iz = 0; iz < nr[2]; ++iz)
+    for (int tz = ra[2][iz]; tz <= rb[2][iz]; ++tz)
+    for (int iy = 0; iy < nr[1]; ++iy)
+    for (int ty = ra[1][iy]; ty <= rb[1][iy]; ++ty)
+    for (int ix = 0; ix < nr[0]; ++ix)
+    for (int tx = ra[0][ix]; tx <= rb[0][ix]; ++tx) {
+        const long long tile = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+        const int slot = atomicAdd(&tl.count[tile], 1);
+        if (slot < tl.cap) tl.list[tile * tl.cap + slot] = p;
+        else if (slot == tl.cap) atomicAdd(&tl.stats[0], 1);
+        atomicMax(&tl.stats[1], slot + 1);
+    }
+}
+
+// Eq. 18 with V_a of Eq. 17 (3D) or Eq. 19 (2D), the integrand read as the sphere (disc)
+// height sqrt(r^2 - x^2 - y^2) over the unit square (segment); principal arctangents.
+__global__ void k_f_of_r(int dim, const double *R, double *Fr, int n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double r = R[p], r2 = r * r;
+    double va;
+    if (dim == 2) {
+        const double s = sqrt(r2 - 0.25);
+        va = 0.5 * s + r2 * atan(0.5 / s);
+    } else {
+        const double s = sqrt(r2 - 0.5);
+        va = (1.0 / 12.0 - r2) * atan(0.5 * s / (0.5 - r2)) + s / 3.0 +
+             (r2 - 1.0 / 12.0) * atan(0.5 / s) - (4.0 / 3.0) * r2 * r * atan(0.25 / (r * s));
+    }
+    Fr[p] = va - r + 0.5;
+}
+
+cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd,
+                       cudaStream_t s) {
+    if (pd.n <= 0) return cudaSuccess;
+    const int threads = 128;
+    k_bin<<<(pd.n + threads - 1) / threads, threads, 0, s>>>(dim, g, ph.shell_h, tl, pd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 128;
+    k_f_of_r<<<(n + threads - 1) / threads, threads, 0, s>>>(dim, R, Fr, n);
+    return cudaGetLastError();
+}
+
+}  // namespace psc

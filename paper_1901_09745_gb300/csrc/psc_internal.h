@@ -1,0 +1,64 @@
+// psc_internal.h -- plain-data structures passed from the C ABI layer to the kernel
+// launchers of the PSC lattice-Boltzmann library. Host-visible; no CUDA device code here.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psc {
+
+// Lattice geometry and the tiling of the lattice into thread blocks.
+struct Geom {
+    int n[3];            // nx, ny, nz
+    long long ncell;     // nx * ny * nz
+    int periodic[3];     // 1 = periodic axis, 0 = halfway bounce-back walls
+    int wrap_img[3];     // 1 = periodic axis short enough to need a per-cell minimum image
+    int t[3];            // tile extent in cells (32 x 8 x 1 for D2Q9, 32 x 4 x 2 for D3Q19)
+    int nt[3];           // tiles per axis
+};
+
+// Physical parameters (FP64 on the host; kernels convert to their compute type).
+struct Phys {
+    double tau;
+    double body_force[3];
+    double shell_h;      // h of Table 1
+    double scale;        // stored value = scale * (f_i - w_i); 1 except for FP16/BF16
+    int psc;             // 0 modified (Eq. 12-14), 1 original (Eq. 7-9, 11)
+};
+
+// Per-tile candidate lists built by the binning kernel: count[tile] particles whose
+// (r + h)-widened bounding box meets the tile; the first `cap` of them in list[tile*cap+k].
+struct Tiles {
+    int *count;
+    int *list;
+    int cap;
+    int *stats;          // [0] tiles that overflowed cap, [1] largest count
+};
+
+// Particle state on the device (FP64), and the force/torque accumulators (Eq. 14).
+struct Parts {
+    int n;
+    const double *X, *U, *Om, *R, *Fr;   // n x 3, n x 3, n x 3, n, n (f(r) of Eq. 18)
+    double *F, *T;                       // n x 3 each
+};
+
+enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
+
+// Fused solid-fraction + PSC collision + pull streaming + force reduction (one step).
+cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout,
+                                  const Geom &g, const Phys &ph, const Tiles &tl,
+                                  const Parts &pd, int *flags, cudaStream_t s);
+// Pre-collision populations (full f, FP64) and/or Eq. 5 moments of the current state.
+cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out,
+                          double *rho, double *u, const Geom &g, const Phys &ph,
+                          cudaStream_t s);
+// Overwrite the state from pre-collision populations (inverse of the pull).
+cudaError_t launch_set(int storage, int lattice, const double *f, void *fout,
+                       const Geom &g, const Phys &ph, cudaStream_t s);
+// Bin particles into tile candidate lists and zero F, T.
+cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl,
+                       const Parts &pd, cudaStream_t s);
+// f(r) of Eq. 18 (Eq. 17 in 3D, Eq. 19 in 2D) for every particle.
+cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s);
+
+}  // namespace psc
