@@ -175,7 +175,10 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     for (int a = 0; a < 3; ++a) { g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC); g.wrap_img[a] = 0; }
     if (ctx->dim == 2) { g.t[0] = D2Q9::TX; g.t[1] = D2Q9::TY; g.t[2] = D2Q9::TZ; }
     else { g.t[0] = D3Q19::TX; g.t[1] = D3Q19::TY; g.t[2] = D3Q19::TZ; }
-    for (int a = 0; a < 3; ++a) g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
+    for (int a = 0; a < 3; ++a) {
+        g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
+        g.inv_n[a] = 1.0 / g.n[a];
+    }
     ctx->ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     Phys &ph = ctx->ph;
     ph.tau = p->tau;
@@ -219,6 +222,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     free_dev((void **)&ctx->flags);
     free_particles(ctx);
     free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
+    free_dev(&ctx->tile_blocks);
     free_dev((void **)&ctx->diag);
     for (int i = 0; i < ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
     free(ctx->ev);
@@ -237,6 +241,7 @@ Parts ctx_parts(lbm_ctx *ctx) {
 static Tiles ctx_tiles(lbm_ctx *ctx) {
     Tiles tl;
     tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap; tl.stats = ctx->tile_stats;
+    tl.blocks = ctx->tile_blocks;
     return tl;
 }
 
@@ -292,6 +297,8 @@ static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
     CK(cudaMalloc(&ctx->tile_count, (size_t)ctx->ntiles * sizeof(int)), "cudaMalloc(tile counts)");
     CK(cudaMalloc(&ctx->tile_list, (size_t)ctx->ntiles * ctx->p.tile_cap * sizeof(int)), "cudaMalloc(tile lists)");
     CK(cudaMalloc(&ctx->tile_stats, 4 * sizeof(int)), "cudaMalloc(tile stats)");
+    CK(cudaMalloc(&ctx->tile_blocks, (size_t)ctx->ntiles * pack_block_bytes(ctx->p.storage == LBM_F64, ctx->p.tile_cap)),
+       "cudaMalloc(tile candidate blocks)");
     CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
     return LBM_OK;
 }
@@ -299,7 +306,7 @@ static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
 extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
                                         const double *Omega, const double *radius, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
-    if (n < 0) { ctx_error(ctx, "particle count must be >= 0, got %d", n); return LBM_ERR_ARG; }
+    if (n < 0 || n > (1 << 24)) { ctx_error(ctx, "particle count must be in [0, 2^24], got %d", n); return LBM_ERR_ARG; }
     if (n > 0 && (!X || !U || !Omega || !radius)) { ctx_error(ctx, "particle arrays must not be NULL"); return LBM_ERR_ARG; }
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     // validate radii on the host (device radii are copied back once)
@@ -350,7 +357,8 @@ lbm_status ctx_bin(lbm_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->tile_count, 0, (size_t)ctx->ntiles * sizeof(int), ctx->stream), "memset tile counts");
     CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
     CK(launch_bin(ctx->dim, ctx->g, ctx->ph, tl, ctx_parts(ctx), ctx->stream), "bin kernel");
-    ctx->launches += 1;
+    CK(launch_pack(ctx->q, ctx->p.storage == LBM_F64, ctx->g, tl, ctx_parts(ctx), ctx->ntiles, ctx->stream), "pack kernel");
+    ctx->launches += 2;
     ctx->bins_valid = 1;
     return LBM_OK;
 }

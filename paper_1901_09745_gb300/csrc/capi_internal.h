@@ -28,6 +28,7 @@ struct lbm_ctx {
     // tile candidate lists
     long long ntiles;
     int *tile_count, *tile_list, *tile_stats;
+    void *tile_blocks;         // packed candidate records per tile
     int bins_valid;
 
     double *diag;              // scratch for host-side diagnostics (macro, populations)

@@ -58,7 +58,9 @@ struct DemBufs {
     const double *Xref;             // positions when the neighbour list was built
     const int *nbr_n, *nbr;         // neighbour count and slots [n][kNB]
     float *hist;                    // [n][kNB][kH]
+    const double *minv;             // [n][2]: 1/m, 1/I
     int *flags;                     // [1] solve failures, [2] list overflow, [3] skin exceeded
+    float reject;                   // pairs with an FP32 overlap below -reject cannot touch
 };
 
 __device__ __forceinline__ double min_image_d(double a, double b, int n, int periodic) {
@@ -103,9 +105,12 @@ __device__ __forceinline__ int axis_bins(int b, int nb, int periodic, int *out) 
     return k;
 }
 
+__device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I);
+
 __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, const int *count,
                           const int *list, const int *old_n, const int *old_nbr, const float *old_hist,
-                          int *new_n, int *new_nbr, float *new_hist, double *Xref, int *flags) {
+                          int *new_n, int *new_nbr, float *new_hist, double *Xref, double *minv,
+                          double density, int *flags) {
     __shared__ int s_buf[8][kNB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -172,6 +177,10 @@ __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, co
     if (lane == 0) {
         new_n[i] = cnt;
         for (int a = 0; a < 3; ++a) Xref[3 * i + a] = xi[a];
+        double m, I;
+        mass_inertia(g.dim, density, ri, &m, &I);
+        minv[2 * i] = 1.0 / m;
+        minv[2 * i + 1] = 1.0 / I;
     }
 }
 
@@ -190,25 +199,32 @@ __device__ __forceinline__ void rotate_into_plane(float *xi, const float *n) {
     if (len1 > 0.0f) { const float s = len0 / len1; for (int a = 0; a < 3; ++a) xi[a] *= s; }
 }
 
-// JKR contact radius ratio s = sqrt(a/a0) for t = delta R / a0^2 on the stable branch:
-// root of s^4 - (2/3) s - t = 0 with s >= 6^(-1/3). g is convex and increasing there, so
-// Newton started to the right of the root decreases monotonically onto it.
+// JKR contact radius ratio s = sqrt(a/a0) for t = delta R / a0^2 on the stable branch, i.e.
+// the root s >= s_c = 6^(-1/3) of s^4 - (2/3) s - t = 0 (t >= t_c = -s_c/2 at pull-off).
+// Written as s = s_c + e, the linear terms cancel exactly (4 s_c^3 = 2/3) and the equation
+// becomes e^2 (6 s_c^2 + 4 s_c e + e^2) = t - t_c, which stays well conditioned near the
+// pull-off point where the original form loses all digits to cancellation. The left side
+// is increasing and convex for e >= 0, and both starting guesses below lie to the right of
+// the root, so Newton decreases monotonically onto it.
 __device__ __forceinline__ float jkr_s(float t, int *fail) {
-    float s = fmaxf(1.0f, sqrtf(sqrtf(fmaxf(t, 0.0f) + 1.0f)));
-    for (int k = 0; k < 30 && (s * s * s * s - (2.0f / 3.0f) * s - t) < 0.0f; ++k) s *= 1.5f;
-    const float sc = 0.55032120814910446f;   // 6^(-1/3)
-    int it = 0;
-    for (; it < 60; ++it) {
-        const float g = s * s * s * s - (2.0f / 3.0f) * s - t;
-        const float dg = 4.0f * s * s * s - (2.0f / 3.0f);
-        if (!(dg > 0.0f)) break;
-        const float step = g / dg;
-        const float sn = fmaxf(s - step, sc);
-        if (fabsf(sn - s) <= 2e-7f * s) { s = sn; break; }
-        s = sn;
+    const float sc = 0.55032120814910446f;            // 6^(-1/3)
+    const float tau = fmaxf(t + 0.5f * sc, 0.0f);      // t - t_c
+    const float c2 = 6.0f * sc * sc, c1 = 4.0f * sc;
+    float e = fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
+    if (tau > 0.0f) {
+        int it = 0;
+        for (; it < 40; ++it) {
+            const float h = e * e * (c2 + c1 * e + e * e) - tau;
+            const float dh = e * (2.0f * c2 + 3.0f * c1 * e + 4.0f * e * e);
+            if (!(dh > 0.0f)) break;
+            const float en = fmaxf(e - h / dh, 0.0f);
+            const bool done = fabsf(en - e) <= 4e-7f * e;   // a few ulps: FP32 may cycle by one
+            e = en;
+            if (done) break;
+        }
+        if (it >= 40 || !(e == e)) *fail = 1;
     }
-    if (it >= 60 || !(s == s)) *fail = 1;
-    return s;
+    return sc + e;
 }
 
 // One contact seen from particle i (neighbour j): force and torque on i in FP32. hist is
@@ -339,69 +355,96 @@ __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, doub
     else { *m = rho * (4.0 / 3.0) * kPi * r * r * r; *I = 0.4 * (*m) * r * r; }
 }
 
+constexpr int kLPP = 4;   // lanes per particle in the sub-step kernel
+
+// One DEM sub-step. kLPP lanes share a particle and split its neighbour slots; their FP64
+// sums are combined with shuffles in a fixed order, then the first lane integrates.
 __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= b.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kLPP, sub = t % kLPP;
+    const bool valid = i < b.n;
     const int dim = g.dim;
-    const double xi[3] = {b.X[3 * i], b.X[3 * i + 1], b.X[3 * i + 2]};
-    const double ui[3] = {b.U[3 * i], b.U[3 * i + 1], b.U[3 * i + 2]};
-    const double oi[3] = {b.Om[3 * i], b.Om[3 * i + 1], b.Om[3 * i + 2]};
-    const double ri = b.R[i];
-    double mi, Ii;
-    mass_inertia(dim, ph.density, ri, &mi, &Ii);
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    const int nn = b.nbr_n[i];
+    double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0}, ri = 1.0;
     int fail = 0;
-    if (lane < nn) {
-        const int j = b.nbr[i * kNB + lane];
-        // overlap in FP64 with IEEE-rounded operations (bit-identical at both ends)
-        double d[3] = {0.0, 0.0, 0.0};
-        for (int a = 0; a < dim; ++a) d[a] = min_image_d(b.X[3 * j + a], xi[a], g.n[a], g.periodic[a]);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-        const double dist = __dsqrt_rn(d2);
-        const double rj = b.R[j];
-        const double dn = __dsub_rn(__dadd_rn(ri, rj), dist);
-        double mj, Ij;
-        mass_inertia(dim, ph.density, rj, &mj, &Ij);
-        float *h = b.hist + ((size_t)i * kNB + lane) * kH;
-        float hl[kH];
-        for (int k = 0; k < kH; ++k) hl[k] = h[k];
-        float fo[3], to[3];
-        const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
-        const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
-        if (contact_on_i(ph, dim, d, dist, dn, ri, rj, mi, mj, ui, uj, oi, oj, hl, fo, to, &fail)) {
-            for (int a = 0; a < 3; ++a) { acc[a] = (double)fo[a]; acc[3 + a] = (double)to[a]; }
+    if (valid) {
+        for (int a = 0; a < 3; ++a) { xi[a] = b.X[3 * i + a]; ui[a] = b.U[3 * i + a]; oi[a] = b.Om[3 * i + a]; }
+        ri = b.R[i];
+        const double mi = 1.0 / b.minv[2 * i];
+        const int nn = b.nbr_n[i];
+        for (int s = sub; s < nn; s += kLPP) {
+            const int j = b.nbr[i * kNB + s];
+            float *hp = b.hist + ((size_t)i * kNB + s) * kH;
+            // separation X_j - X_i in FP64 (exact subtraction), minimum image; the periodic
+            // shift is decided on the FP32 copy, exact for neighbours (|d| << n/2)
+            double d[3] = {0.0, 0.0, 0.0};
+            float df[3] = {0.0f, 0.0f, 0.0f};
+            for (int a = 0; a < dim; ++a) {
+                d[a] = __dsub_rn(b.X[3 * j + a], xi[a]);
+                if (g.periodic[a]) {
+                    const float half = 0.5f * (float)g.n[a], v = (float)d[a];
+                    if (v > half) d[a] = __dsub_rn(d[a], (double)g.n[a]);
+                    else if (v < -half) d[a] = __dadd_rn(d[a], (double)g.n[a]);
+                }
+                df[a] = (float)d[a];
+            }
+            const double rj = b.R[j];
+            const float dnf = (float)(ri + rj) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+            const bool was = hp[7] != 0.0f;
+            if (dnf < -b.reject) {
+                // provably out of contact (FP32 error is far below the margin)
+                if (was) for (int k = 0; k < kH; ++k) hp[k] = 0.0f;
+                continue;
+            }
+            // exact overlap in FP64 with IEEE-rounded operations (bit-identical at both ends)
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
+            const double dist = __dsqrt_rn(d2);
+            const double dn = __dsub_rn(__dadd_rn(ri, rj), dist);
+            const double mj = 1.0 / b.minv[2 * j];
+            float hl[kH];
+            for (int k = 0; k < kH; ++k) hl[k] = hp[k];
+            float fo[3], to[3];
+            const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
+            const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
+            if (contact_on_i(ph, dim, d, dist, dn, ri, rj, mi, mj, ui, uj, oi, oj, hl, fo, to, &fail)) {
+                for (int a = 0; a < 3; ++a) { acc[a] += (double)fo[a]; acc[3 + a] += (double)to[a]; }
+            }
+            if (was || hl[7] != 0.0f) for (int k = 0; k < kH; ++k) hp[k] = hl[k];
         }
-        for (int k = 0; k < kH; ++k) h[k] = hl[k];
     }
-    // per-particle sums in FP64, in a fixed lane order
+    // combine the kLPP partial sums (fixed butterfly order)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
+    for (int off = 1; off < kLPP; off <<= 1)
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(kFullMask, acc[q], off);
-    if (__any_sync(kFullMask, fail) && lane == 0) atomicAdd(&b.flags[1], 1);
-    if (lane != 0) return;
+    if (fail) atomicAdd(&b.flags[1], 1);
+    if (!valid || sub != 0) return;
     // Eq. 21, semi-implicit Euler, hydrodynamic force/torque frozen over the sub-steps
+    const double im = b.minv[2 * i], iI = b.minv[2 * i + 1];
     double un[3], xn[3], on[3];
     for (int a = 0; a < 3; ++a) {
         if (a < dim) {
-            un[a] = ui[a] + ph.dt * (b.Ff[3 * i + a] + acc[a] + mi * ph.g[a]) / mi;
+            un[a] = ui[a] + ph.dt * ((b.Ff[3 * i + a] + acc[a]) * im + ph.g[a]);
             xn[a] = xi[a] + ph.dt * un[a];
-            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] / g.n[a]);
+            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] * (1.0 / g.n[a]));
         } else {
             un[a] = ui[a];
             xn[a] = xi[a];
         }
         const bool spin = (dim == 3) || (a == 2);
-        on[a] = spin ? oi[a] + ph.dt * (b.Tf[3 * i + a] + acc[3 + a]) / Ii : oi[a];
+        on[a] = spin ? oi[a] + ph.dt * (b.Tf[3 * i + a] + acc[3 + a]) * iI : oi[a];
     }
-    double disp2 = 0.0;
+    float disp2 = 0.0f;
     for (int a = 0; a < dim; ++a) {
-        const double dd = min_image_d(xn[a], b.Xref[3 * i + a], g.n[a], g.periodic[a]);
+        float dd = (float)(xn[a] - b.Xref[3 * i + a]);
+        if (g.periodic[a]) {
+            const float half = 0.5f * (float)g.n[a];
+            if (dd > half) dd -= (float)g.n[a];
+            else if (dd < -half) dd += (float)g.n[a];
+        }
         disp2 += dd * dd;
     }
-    if (disp2 > 0.25 * g.skin * g.skin) atomicAdd(&b.flags[3], 1);
+    if (disp2 > 0.25f * (float)(g.skin * g.skin)) atomicAdd(&b.flags[3], 1);
     for (int a = 0; a < 3; ++a) { b.Xo[3 * i + a] = xn[a]; b.Uo[3 * i + a] = un[a]; b.Omo[3 * i + a] = on[a]; }
 }
 
@@ -414,7 +457,8 @@ struct dem_ctx {
     int n, cap_n;
     DemGeom g;
     DemPhys ph;
-    double *X2, *U2, *Om2, *Xref;
+    double *X2, *U2, *Om2, *Xref, *minv;
+    float reject;
     int *bin_count, *bin_list;
     long long nbins;
     int *nbr_n[2], *nbr[2];
@@ -429,6 +473,7 @@ static void dfree(void **p) { if (*p) cudaFree(*p); *p = NULL; }
 void dem_release(dem_ctx *d) {
     if (!d) return;
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
+    dfree((void **)&d->minv);
     dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     free(d);
@@ -449,8 +494,10 @@ static lbm_status dem_reserve(dem_ctx *d) {
     d->n = n;
     if (cap <= d->cap_n) return LBM_OK;
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
+    dfree((void **)&d->minv);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     const size_t v = (size_t)cap * 3 * sizeof(double);
+    DCK(cudaMalloc(&d->minv, (size_t)cap * 2 * sizeof(double)), "cudaMalloc(DEM inverse mass)");
     DCK(cudaMalloc(&d->X2, v), "cudaMalloc(DEM X)");
     DCK(cudaMalloc(&d->U2, v), "cudaMalloc(DEM U)");
     DCK(cudaMalloc(&d->Om2, v), "cudaMalloc(DEM Omega)");
@@ -503,7 +550,8 @@ static lbm_status dem_build_lists(dem_ctx *d) {
     const int nx = d->cur ^ 1;
     k_dem_nbr<<<(n + 7) / 8, 256, 0, fl->stream>>>(d->g, n, fl->dX, fl->dR, d->bin_count, d->bin_list,
                                                     d->nbr_n[d->cur], d->nbr[d->cur], d->hist[d->cur],
-                                                    d->nbr_n[nx], d->nbr[nx], d->hist[nx], d->Xref, fl->flags);
+                                                    d->nbr_n[nx], d->nbr[nx], d->hist[nx], d->Xref, d->minv,
+                                                    d->ph.density, fl->flags);
     DCK(cudaGetLastError(), "DEM neighbour kernel");
     d->cur = nx;
     d->lists_valid = 1;
@@ -574,12 +622,22 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     b.nbr_n = d->nbr_n[d->cur];
     b.nbr = d->nbr[d->cur];
     b.hist = d->hist[d->cur];
+    b.minv = d->minv;
     b.flags = fl->flags;
-    const int blocks = (d->n + 7) / 8;
+    // largest delta_C of any pair (R <= r_max / 2) plus a margin far above FP32 error
+    {
+        const double Es = d->p.E / (2.0 * (1.0 - d->p.poisson * d->p.poisson));
+        const double Rm = 0.5 * fl->rmax;
+        const double a0 = cbrt(9.0 * kPi * d->p.gamma * Rm * Rm / Es);
+        const double dC = d->p.adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * Rm) : 0.0;
+        b.reject = (float)(dC + 1e-3);
+    }
+    const int threads = 128;
+    const int blocks = (int)(((long long)d->n * kLPP + threads - 1) / threads);
     for (int s = 0; s < substeps; ++s) {
         b.X = fl->dX; b.U = fl->dU; b.Om = fl->dOm;
         b.Xo = d->X2; b.Uo = d->U2; b.Omo = d->Om2;
-        k_dem_substep<<<blocks, 256, 0, fl->stream>>>(d->g, d->ph, b);
+        k_dem_substep<<<blocks, threads, 0, fl->stream>>>(d->g, d->ph, b);
         DCK(cudaGetLastError(), "DEM sub-step kernel");
         // the new state becomes the fluid context's particle state
         double *t;

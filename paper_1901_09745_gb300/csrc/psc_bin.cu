@@ -6,7 +6,7 @@
 // hold the tile's few candidates in shared memory and evaluate every cell against them.
 #include <math.h>
 
-#include "psc_internal.h"
+#include "psc_kernels.cuh"
 
 namespace psc {
 
@@ -79,6 +79,24 @@ cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl, 
     if (pd.n <= 0) return cudaSuccess;
     const int threads = 128;
     k_bin<<<(pd.n + threads - 1) / threads, threads, 0, s>>>(dim, g, ph.shell_h, tl, pd);
+    return cudaGetLastError();
+}
+
+long long pack_block_bytes(int rec_double, int cap) {
+    return rec_double ? block_elems<double>(cap) * (long long)sizeof(double)
+                      : block_elems<float>(cap) * (long long)sizeof(float);
+}
+
+cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles &tl, const Parts &pd,
+                        long long ntiles, cudaStream_t s) {
+    const unsigned blocks = (unsigned)((ntiles + kWarps - 1) / kWarps);
+    if (lattice == 9) {
+        if (rec_double) k_pack_tiles<D2Q9, double><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
+        else k_pack_tiles<D2Q9, float><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
+    } else {
+        if (rec_double) k_pack_tiles<D3Q19, double><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
+        else k_pack_tiles<D3Q19, float><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
+    }
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ struct Geom {
     int wrap_img[3];     // 1 = periodic axis short enough to need a per-cell minimum image
     int t[3];            // tile extent in cells (32 x 8 x 1 for D2Q9, 32 x 4 x 2 for D3Q19)
     int nt[3];           // tiles per axis
+    double inv_n[3];     // 1 / n per axis (no FP64 division on the device)
 };
 
 // Physical parameters (FP64 on the host; kernels convert to their compute type).
@@ -33,6 +34,7 @@ struct Tiles {
     int *list;
     int cap;
     int *stats;          // [0] tiles that overflowed cap, [1] largest count
+    void *blocks;        // per-tile packed candidate records (compute type), see psc_kernels.cuh
 };
 
 // Particle state on the device (FP64), and the force/torque accumulators (Eq. 14).
@@ -58,6 +60,11 @@ cudaError_t launch_set(int storage, int lattice, const double *f, void *fout,
 // Bin particles into tile candidate lists and zero F, T.
 cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl,
                        const Parts &pd, cudaStream_t s);
+// Sort each tile's list and write its packed candidate records (rec_double: FP64 records).
+cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles &tl, const Parts &pd,
+                        long long ntiles, cudaStream_t s);
+// Bytes of one tile's packed block for the given candidate capacity.
+long long pack_block_bytes(int rec_double, int cap);
 // f(r) of Eq. 18 (Eq. 17 in 3D, Eq. 19 in 2D) for every particle.
 cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s);
 

@@ -83,133 +83,297 @@ pull_one(const S *__restrict__ fin, const Geom &g, int x, int y, int z, long lon
     return Store<S>::ld(fin, (long long)i * g.ncell + src, sc);
 }
 
-// Shared-memory candidate table of one tile: positions relative to the tile origin
-// (minimum image), radius, f(r), velocity and spin, all in the compute type.
-template <typename T> struct CandSmem {
-    T *px, *py, *pz, *r, *fr, *ux, *uy, *uz, *ox, *oy, *oz;
-    T *part;        // [kWarps][NC][cap] warp partial sums of force/torque
-    int *id;        // [cap] particle index of each slot (sorted ascending)
-    int *idraw;     // [cap] unsorted list as read from global memory
-};
+// ------------------------------------------------------------------- candidate records
+// Each lattice tile owns one block of candidate records in global memory, written by the
+// packing kernel after binning: a 16-byte header whose first element is the tile's
+// candidate count, then up to `cap` records of RW values of the compute type, sorted by
+// particle index (so per-cell sums do not depend on the binning's atomic order). A record
+// holds the particle's position relative to the tile origin (minimum image), radius,
+// f(r) of Eq. 18, velocity, spin and index. The collide-stream kernel fetches a tile's
+// header and first kPre records in one coalesced round trip issued before its population
+// loads, so the candidate table costs no extra latency on the critical path.
+constexpr int RW = 12;
+enum { R_PX = 0, R_PY, R_PZ, R_R, R_FR, R_UX, R_UY, R_UZ, R_OX, R_OY, R_OZ, R_ID };
+constexpr int kPre = 16;
 
-template <typename T>
-__host__ __device__ inline size_t cand_smem_bytes(int cap, int nc) {
-    return (size_t)cap * (11 + (size_t)kWarps * nc) * sizeof(T) + (size_t)cap * 2 * sizeof(int);
+template <typename T> __host__ __device__ constexpr int head_elems() { return 16 / (int)sizeof(T); }
+template <typename T> __host__ __device__ inline long long block_elems(int cap) {
+    return ((head_elems<T>() + (long long)cap * RW + 3) / 4) * 4;
+}
+template <typename T> __host__ __device__ inline size_t cs_smem_bytes(int cap, int nc) {
+    return (size_t)cap * RW * sizeof(T) + (size_t)kWarps * cap * nc * sizeof(T);
 }
 
-template <typename T>
-__device__ __forceinline__ CandSmem<T> carve(unsigned char *smem, int cap, int nc) {
-    CandSmem<T> c;
-    T *p = reinterpret_cast<T *>(smem);
-    c.px = p; c.py = p + cap; c.pz = p + 2 * cap; c.r = p + 3 * cap; c.fr = p + 4 * cap;
-    c.ux = p + 5 * cap; c.uy = p + 6 * cap; c.uz = p + 7 * cap;
-    c.ox = p + 8 * cap; c.oy = p + 9 * cap; c.oz = p + 10 * cap;
-    c.part = p + 11 * cap;
-    c.id = reinterpret_cast<int *>(c.part + (size_t)kWarps * nc * cap);
-    c.idraw = c.id + cap;
-    return c;
-}
+// Particle index stored in a record slot as raw bits (no conversion instruction).
+template <typename T> __device__ __forceinline__ T id_bits(int id);
+template <> __device__ __forceinline__ float id_bits<float>(int id) { return __int_as_float(id); }
+template <> __device__ __forceinline__ double id_bits<double>(int id) { return __longlong_as_double((long long)id); }
+__device__ __forceinline__ int bits_id(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_id(double v) { return (int)__double_as_longlong(v); }
 
-// Load one chunk of candidates into shared memory. Normal case: the tile's list, sorted by
-// particle index (so the per-cell summation order does not depend on the binning's atomic
-// order). Overflow case: particles [ch*cap, ch*cap + nk) of the global array.
+// Record of particle `id` for the tile with origin (x0, y0, z0).
 template <class L, typename T>
-__device__ void load_chunk(const CandSmem<T> &c, const Geom &g, const Tiles &tl, const Parts &pd,
-                           long long tile, bool ovf, int ch, int nk, int x0, int y0, int z0,
-                           int tid) {
-    int pos = tid, id = 0;
-    if (ovf) {
-        id = ch * tl.cap + tid;
-    } else {
-        if (tid < nk) c.idraw[tid] = tl.list[tile * tl.cap + tid];
-        __syncthreads();
-        if (tid < nk) {
-            id = c.idraw[tid];
-            int rank = 0;
-            for (int j = 0; j < nk; ++j) rank += (c.idraw[j] < id);
-            pos = rank;
-        }
-    }
-    if (tid < nk) {
-        const int org[3] = {x0, y0, z0};
-        const int ext[3] = {L::TX, L::TY, L::TZ};
-        T rel[3];
+__device__ __forceinline__ void write_record(T *rec, const Geom &g, const Parts &pd, int id, int x0,
+                                             int y0, int z0) {
+    const int org[3] = {x0, y0, z0};
+    const int ext[3] = {L::TX, L::TY, L::TZ};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (a >= L::D) { rel[a] = (T)0; continue; }
+    for (int a = 0; a < 3; ++a) {
+        T rel = (T)0;
+        if (a < L::D) {
             double d = pd.X[3 * id + a] - (double)org[a];
             if (g.periodic[a]) {
                 // minimum image with respect to the tile centre
-                double cen = 0.5 * (ext[a] - 1);
+                const double cen = 0.5 * (ext[a] - 1);
                 double e = d - cen;
-                e -= (double)g.n[a] * rint(e / (double)g.n[a]);
+                e -= (double)g.n[a] * rint(e * g.inv_n[a]);
                 d = e + cen;
             }
-            rel[a] = (T)d;
+            rel = (T)d;
         }
-        c.px[pos] = rel[0]; c.py[pos] = rel[1]; c.pz[pos] = rel[2];
-        c.r[pos] = (T)pd.R[id];
-        c.fr[pos] = (T)pd.Fr[id];
-        c.ux[pos] = (T)pd.U[3 * id + 0]; c.uy[pos] = (T)pd.U[3 * id + 1]; c.uz[pos] = (T)pd.U[3 * id + 2];
-        c.ox[pos] = (T)pd.Om[3 * id + 0]; c.oy[pos] = (T)pd.Om[3 * id + 1]; c.oz[pos] = (T)pd.Om[3 * id + 2];
-        c.id[pos] = id;
+        rec[R_PX + a] = rel;
+    }
+    rec[R_R] = (T)pd.R[id];
+    rec[R_FR] = (T)pd.Fr[id];
+    rec[R_UX] = (T)pd.U[3 * id + 0]; rec[R_UY] = (T)pd.U[3 * id + 1]; rec[R_UZ] = (T)pd.U[3 * id + 2];
+    rec[R_OX] = (T)pd.Om[3 * id + 0]; rec[R_OY] = (T)pd.Om[3 * id + 1]; rec[R_OZ] = (T)pd.Om[3 * id + 2];
+    rec[R_ID] = id_bits<T>(id);
+}
+
+// Packing kernel: one warp per tile sorts the tile's candidate list and writes its block.
+template <class L, typename T>
+__global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
+    __shared__ int s_id[kWarps][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long tile = (long long)blockIdx.x * kWarps + warp;
+    if (tile >= ntiles) return;
+    const int cnt = tl.count[tile];
+    const int m = min(cnt, tl.cap);
+    T *blk = reinterpret_cast<T *>(tl.blocks) + tile * block_elems<T>(tl.cap);
+    if (lane == 0) blk[0] = (T)cnt;
+    for (int k = lane; k < m; k += 32) s_id[warp][k] = tl.list[tile * tl.cap + k];
+    __syncwarp();
+    const int tx = (int)(tile % g.nt[0]);
+    const int ty = (int)((tile / g.nt[0]) % g.nt[1]);
+    const int tz = (int)(tile / ((long long)g.nt[0] * g.nt[1]));
+    for (int k = lane; k < m; k += 32) {
+        const int id = s_id[warp][k];
+        int rank = 0;
+        for (int q = 0; q < m; ++q) rank += (s_id[warp][q] < id);
+        write_record<L, T>(blk + head_elems<T>() + (long long)rank * RW, g, pd, id, tx * L::TX, ty * L::TY,
+                           tz * L::TZ);
     }
 }
 
-// Solid fraction of candidate k at the cell with tile-relative centre (cx, cy, cz):
-// Table 1 Steps 2-4 with the inside/outside branches as stated in Sec. 2.4 (distance
-// <= r - h -> 1, >= r + h -> 0), else clamp(f(r) - D, 0, 1) with D = distance - r (Eq. 15).
-// Returns 0 outside; on return (dx, dy, dz) is the arm x_n - X_p.
+// The geometric part of a record (position, radius) and the rest (f(r), U, Omega, index),
+// read from shared memory with 16-byte loads (records are 16-byte aligned).
+template <typename T> struct Vec4 { T x, y, z, w; };
+template <typename T> __device__ __forceinline__ Vec4<T> ld4(const T *p);
+template <> __device__ __forceinline__ Vec4<float> ld4<float>(const float *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+template <> __device__ __forceinline__ Vec4<double> ld4<double>(const double *p) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    return {a.x, a.y, b.x, b.y};
+}
+
+// Solid fraction of the candidate in record `rec` at the cell with tile-relative centre
+// (cx, cy, cz): Table 1 Steps 2-4 with the inside/outside branches as stated in Sec. 2.4
+// (distance <= r - h -> 1, >= r + h -> 0), else clamp(f(r) - D, 0, 1) with D = distance - r
+// (Eq. 15). Returns 0 outside; on return (dx, dy, dz) is the arm x_n - X_p.
 template <class L, typename T>
-__device__ __forceinline__ T cand_eps(const CandSmem<T> &c, const Geom &g, int k, T cx, T cy, T cz,
-                                      T h, T &dx, T &dy, T &dz) {
-    dx = cx - c.px[k];
-    dy = cy - c.py[k];
-    dz = (L::D == 3) ? cz - c.pz[k] : (T)0;
+__device__ __forceinline__ T cand_eps(const T *rec, const Geom &g, T cx, T cy, T cz, T h, T &dx, T &dy,
+                                      T &dz) {
+    const Vec4<T> pr = ld4<T>(rec);                      // px, py, pz, r
+    dx = cx - pr.x;
+    dy = cy - pr.y;
+    dz = (L::D == 3) ? cz - pr.z : (T)0;
     if (g.wrap_img[0]) dx -= (T)g.n[0] * rint_t(dx / (T)g.n[0]);
     if (g.wrap_img[1]) dy -= (T)g.n[1] * rint_t(dy / (T)g.n[1]);
     if (L::D == 3 && g.wrap_img[2]) dz -= (T)g.n[2] * rint_t(dz / (T)g.n[2]);
     const T d2 = dx * dx + dy * dy + dz * dz;
-    const T r = c.r[k];
+    const T r = pr.w;
     const T rh = r + h;
     if (!(d2 < rh * rh)) return (T)0;
     const T dist = sqrt_t(d2);
     if (dist <= r - h) return (T)1;
-    T e = c.fr[k] - (dist - r);
+    T e = rec[R_FR] - (dist - r);
     e = e < (T)0 ? (T)0 : e;
     e = e > (T)1 ? (T)1 : e;
     return e;
 }
 
+// Plain-fluid tiles (no candidate particle): BGK + Guo collision and pull streaming only
+// (Eq. 1-6). No shared memory and no barrier, so each warp's loads overlap freely with
+// other warps' arithmetic; the small register footprint keeps six blocks per SM resident.
+// Tiles that have candidates return at once and are done by k_collide_stream.
+template <class L, typename S, bool HASF>
+__global__ void __launch_bounds__(kThreads, (L::Q == 9) ? 6 : 4)
+k_fluid(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph,
+        Tiles tl, int np, int *flags) {
+    using T = typename Store<S>::T;
+    constexpr int Q = L::Q;
+    const long long tile = blockIdx.x + (long long)g.nt[0] * (blockIdx.y + (long long)g.nt[1] * blockIdx.z);
+    if (np > 0 && tl.count[tile] > 0) return;
+    const int x0 = blockIdx.x * L::TX, y0 = blockIdx.y * L::TY, z0 = blockIdx.z * L::TZ;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) return;
+    const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+    const long long N = g.ncell;
+    T df[Q];
+    const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
+                          (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+    if (interior) {
+        const S *base = fin + cell;
+        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
+    }
+    T drho = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += df[i];
+        if (L::ex(i)) jx += L::ex(i) * df[i];
+        if (L::ey(i)) jy += L::ey(i) * df[i];
+        if (L::ez(i)) jz += L::ez(i) * df[i];
+    }
+    const T rho = (T)1 + drho;
+    const T irho = (T)1 / rho;
+    const T ux = (HASF ? jx + (T)0.5 * ph.F[0] : jx) * irho;
+    const T uy = (HASF ? jy + (T)0.5 * ph.F[1] : jy) * irho;
+    const T uz = (HASF ? jz + (T)0.5 * ph.F[2] : jz) * irho;
+    if (!(rho > (T)0)) atomicOr(flags, 1);
+    const T uu = ux * ux + uy * uy + uz * uz;
+    const T base_eq = drho - (T)1.5 * rho * uu;
+    const T uF = HASF ? ux * ph.F[0] + uy * ph.F[1] + uz * ph.F[2] : (T)0;
+    S *obase = fout + cell;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T w = (T)weight<L>(i);
+        const T eu = L::ex(i) * ux + L::ey(i) * uy + L::ez(i) * uz;
+        const T dfeq = w * (base_eq + rho * eu * ((T)3 + (T)4.5 * eu));
+        T out = df[i] - ph.omega * (df[i] - dfeq);
+        if (HASF) {
+            const T eF = L::ex(i) * ph.F[0] + L::ey(i) * ph.F[1] + L::ez(i) * ph.F[2];
+            out += ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
+        }
+        Store<S>::st(obase, (long long)i * N, out, ph.sc);
+    }
+}
+
+// Arm x_n - X_p from the cell (cx, cy, cz) to the candidate at (px, py, pz), all relative
+// to the tile origin, with the per-cell minimum image on short periodic axes.
+template <class L, typename T>
+__device__ __forceinline__ void cand_arm(const Geom &g, T cx, T cy, T cz, T px, T py, T pz, T &dx, T &dy,
+                                         T &dz) {
+    dx = cx - px;
+    dy = cy - py;
+    dz = (L::D == 3) ? cz - pz : (T)0;
+    if (g.wrap_img[0]) dx -= (T)g.n[0] * rint_t(dx / (T)g.n[0]);
+    if (g.wrap_img[1]) dy -= (T)g.n[1] * rint_t(dy / (T)g.n[1]);
+    if (L::D == 3 && g.wrap_img[2]) dz -= (T)g.n[2] * rint_t(dz / (T)g.n[2]);
+}
+
+// Table 1 Steps 2-4 for a cell at squared distance d2 from a candidate of radius r:
+// distance <= r - h -> 1, >= r + h -> 0, else clamp(f(r) - D, 0, 1) with D = distance - r.
+template <typename T>
+__device__ __forceinline__ T shell_eps(T d2, T r, T fr, T h) {
+    const T rh = r + h;
+    if (!(d2 < rh * rh)) return (T)0;
+    const T dist = sqrt_t(d2);
+    if (dist <= r - h) return (T)1;
+    T e = fr - (dist - r);
+    e = e < (T)0 ? (T)0 : e;
+    e = e > (T)1 ? (T)1 : e;
+    return e;
+}
+
+// Can the candidate at (px, py, pz) with reach R = r + h touch any cell of this warp's row
+// (tile-relative y = cy, z = cz, x = 0..xmax)? Conservative: a false "yes" only costs time.
+template <class L, typename T>
+__device__ __forceinline__ bool row_hits(const Geom &g, T px, T py, T pz, T R, T cy, T cz, T xmax) {
+    T dx, dy, dz;
+    cand_arm<L, T>(g, (T)0, cy, cz, (T)0, py, pz, dx, dy, dz);
+    const T rem = R * R - dy * dy - dz * dz;
+    if (!(rem > (T)0)) return false;
+    if (g.wrap_img[0]) return true;
+    const T hw = sqrt_t(rem);
+    return (px - hw <= xmax + (T)1) && (px + hw >= (T)-1);
+}
+
+template <class L, typename T> constexpr int psc_min_blocks() {
+    return sizeof(T) == 8 ? 1 : (L::Q == 9 ? 4 : 3);
+}
+
+// Tiles with candidate particles. The tile's records are staged in shared memory while the
+// population loads are in flight. Each warp is one row of the tile: it culls the candidates
+// that cannot reach its row (one lane per candidate, ballot), then every lane evaluates the
+// remaining ones from shared memory (broadcast reads). Warps with no solid cell run the plain
+// BGK + Guo update. Forces: each warp reduces each of its candidates' momentum exchange with
+// shuffles; partial sums meet in shared memory and are added in a fixed order, one FP64
+// atomic per particle and component per tile. Tiles with more candidates than the block
+// holds take the same path chunk by chunk over all particles (exact, slow, rare).
 template <class L, typename S, int PSC>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, (psc_min_blocks<L, typename Store<S>::T>()))
 k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
                  PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
     using T = typename Store<S>::T;
     constexpr int Q = L::Q;
     constexpr int NC = (L::D == 2) ? 3 : 6;
+    constexpr int NSLOT = 4;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_mask[kWarps];
     const int cap = tl.cap;
-    const CandSmem<T> c = carve<T>(smem, cap, NC);
+    T *srec = reinterpret_cast<T *>(smem);                 // [cap][RW] candidate records
+    T *part = srec + (size_t)cap * RW;                     // [kWarps][cap][NC] warp partials
+
+    // tiles in launch order (x fastest): neighbouring tiles run close in time and share the
+    // halo sectors of their pulls in L2
+    const long long tile = blockIdx.x;
+    const int tx = (int)(tile % g.nt[0]);
+    const int ty = (int)((tile / g.nt[0]) % g.nt[1]);
+    const int tz = (int)(tile / ((long long)g.nt[0] * g.nt[1]));
+    const int cnt = tl.count[tile];
+    if (cnt == 0) return;                                   // plain-fluid tile: k_fluid does it
+    const bool ovf = cnt > cap;
+    const int nchunk = ovf ? (pd.n + cap - 1) / cap : 1;
+    const T *recs = reinterpret_cast<const T *>(tl.blocks) + tile * block_elems<T>(cap) + head_elems<T>();
 
     const int tid = threadIdx.x + L::TX * (threadIdx.y + L::TY * threadIdx.z);
     const int lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * L::TX, y0 = blockIdx.y * L::TY, z0 = blockIdx.z * L::TZ;
+    const int x0 = tx * L::TX, y0 = ty * L::TY, z0 = tz * L::TZ;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
     const bool active = x < g.n[0] && y < g.n[1] && z < g.n[2];
-    const long long tile = blockIdx.x + (long long)g.nt[0] * (blockIdx.y + (long long)g.nt[1] * blockIdx.z);
     const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
     const long long N = g.ncell;
+
+    // ---- 0. this thread's share of the tile's records (cap <= 64 records of RW values),
+    //         loaded now, written to shared memory once the pull loads are in flight
+    constexpr int kRecWords = (64 * RW + kThreads - 1) / kThreads;
+    T rw[kRecWords];
+    const int nwords = ovf ? 0 : cnt * RW;
+#pragma unroll
+    for (int j = 0; j < kRecWords; ++j) {
+        const int w = tid + j * kThreads;
+        rw[j] = (w < nwords) ? recs[w] : (T)0;
+    }
 
     // ---- 1. pull (Eq. 1, Eq. 6)
     T df[Q];
     const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
     if (interior) {
+        const S *base = fin + cell;
         const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            df[i] = Store<S>::ld(fin, (long long)i * N + cell - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
+            df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
     } else if (active) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
@@ -234,57 +398,93 @@ k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
     const T uz = (jz + (T)0.5 * ph.F[2]) * irho;
     if (active && !(rho > (T)0)) atomicOr(flags, 1);
 
-    // ---- 3. candidates: solid fractions and the u_s moments of the cell
-    const int cnt = (pd.n > 0) ? tl.count[tile] : 0;
-    const bool ovf = cnt > cap;
-    const int nchunk = ovf ? (pd.n + cap - 1) / cap : (cnt > 0 ? 1 : 0);
-    const T cx = (T)(x - x0), cy = (T)(y - y0), cz = (T)(z - z0);
+#pragma unroll
+    for (int j = 0; j < kRecWords; ++j) {
+        const int w = tid + j * kThreads;
+        if (w < nwords) srec[w] = rw[j];
+    }
+
+    // ---- 3. candidates reaching this row: solid fractions and u_s moments of the cell
+    const T cx = (T)threadIdx.x, cy = (T)threadIdx.y, cz = (T)threadIdx.z;
+    const T xmax = (T)(min(L::TX, g.n[0] - x0) - 1);
     T seps = 0, mx = 0, my = 0, mz = 0, Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0;
-    unsigned long long mask = 0ull;
-    int nk = 0;
+    unsigned long long wmask = 0ull;     // relevant candidates of this row (normal tiles)
+    T eslot[NSLOT] = {};                 // eps of the first relevant candidates, for step 6
+    int nk = cnt;
     for (int ch = 0; ch < nchunk; ++ch) {
-        nk = ovf ? min(cap, pd.n - ch * cap) : cnt;
+        if (ovf) {
+            nk = min(cap, pd.n - ch * cap);
+            __syncthreads();
+            if (tid < nk) write_record<L, T>(srec + tid * RW, g, pd, ch * cap + tid, x0, y0, z0);
+        }
         __syncthreads();
-        load_chunk<L, T>(c, g, tl, pd, tile, ovf, ch, nk, x0, y0, z0, tid);
-        __syncthreads();
-        if (!active) continue;
-        for (int k = 0; k < nk; ++k) {
-            T dx, dy, dz;
-            const T e = cand_eps<L, T>(c, g, k, cx, cy, cz, ph.h, dx, dy, dz);
-            if (e > (T)0) {
-                // u_s = U + Omega x (x_n - X_p)
-                const T usx = c.ux[k] + c.oy[k] * dz - c.oz[k] * dy;
-                const T usy = c.uy[k] + c.oz[k] * dx - c.ox[k] * dz;
-                const T usz = (L::D == 3) ? c.uz[k] + c.ox[k] * dy - c.oy[k] * dx : (T)0;
-                // modified scheme weights by eps_s (normalised below); original by B(eps_s)
-                const T wgt = (PSC == 0) ? e : e * ph.tmh / (((T)1 - e) + ph.tmh);
-                seps += wgt;
-                mx += wgt * usx; my += wgt * usy; mz += wgt * usz;
-                Mxx += wgt * usx * usx; Myy += wgt * usy * usy; Mxy += wgt * usx * usy;
-                if (L::D == 3) { Mzz += wgt * usz * usz; Mxz += wgt * usx * usz; Myz += wgt * usy * usz; }
-                if (!ovf) mask |= (1ull << k);
+        int js = 0;
+        for (int kb = 0; kb < nk; kb += 32) {
+            const int k = kb + lane;
+            bool rel = false;
+            if (k < nk) {
+                const Vec4<T> a = ld4<T>(srec + k * RW);
+                rel = row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, cy, cz, xmax);
+            }
+            unsigned bal = __ballot_sync(kFull, rel);
+            if (!ovf) wmask |= (unsigned long long)bal << kb;
+            while (bal) {
+                const int kk = kb + __ffs(bal) - 1;
+                bal &= bal - 1u;
+                const T *rk = srec + kk * RW;
+                const Vec4<T> a = ld4<T>(rk);
+                const Vec4<T> b = ld4<T>(rk + 4);      // f(r), Ux, Uy, Uz
+                T dx, dy, dz;
+                cand_arm<L, T>(g, cx, cy, cz, a.x, a.y, a.z, dx, dy, dz);
+                const T e = active ? shell_eps<T>(dx * dx + dy * dy + dz * dz, a.w, b.x, ph.h) : (T)0;
+                if (!ovf) {
+#pragma unroll
+                    for (int q = 0; q < NSLOT; ++q) if (js == q) eslot[q] = e;
+                }
+                ++js;
+                if (e > (T)0) {
+                    const Vec4<T> c = ld4<T>(rk + 8);  // Ox, Oy, Oz, id
+                    // u_s = U + Omega x (x_n - X_p)
+                    const T usx = b.y + c.y * dz - c.z * dy;
+                    const T usy = b.z + c.z * dx - c.x * dz;
+                    const T usz = (L::D == 3) ? b.w + c.x * dy - c.y * dx : (T)0;
+                    // modified scheme weights by eps_s (normalised below); original by B(eps_s)
+                    const T wgt = (PSC == 0) ? e : e * ph.tmh / (((T)1 - e) + ph.tmh);
+                    seps += wgt;
+                    mx += wgt * usx; my += wgt * usy; mz += wgt * usz;
+                    Mxx += wgt * usx * usx; Myy += wgt * usy * usy; Mxy += wgt * usx * usy;
+                    if (L::D == 3) { Mzz += wgt * usz * usz; Mxz += wgt * usx * usz; Myz += wgt * usy * usz; }
+                }
             }
         }
     }
 
     // ---- 4. weights: eps_n = min(1, sum eps) (Table 1 Step 5), B_n by Eq. 9 at eps_n,
-    //         B_{n,s} = B_n eps_s / sum eps (Eq. 13; bounded by one when fractions overlap)
-    T Bn, cB;
-    if (PSC == 0) {
-        const T en = seps < (T)1 ? seps : (T)1;
-        Bn = en * ph.tmh / (((T)1 - en) + ph.tmh);
-        cB = seps > (T)0 ? Bn / seps : (T)0;
-    } else {
-        Bn = seps;    // Eq. 8: B_n = sum_s B(eps_s)
-        cB = (T)1;
+    //         B_{n,s} = B_n eps_s / sum eps = cB eps_s (Eq. 13; cells with overlapping
+    //         fractions keep B_n = 1). Original scheme: B_n = sum_s B(eps_s) (Eq. 8).
+    const bool any_solid = __any_sync(kFull, seps > (T)0);
+    T Bn = 0, cB = 0;
+    if (any_solid && seps > (T)0) {
+        if (PSC == 0) {
+            if (seps < (T)1) {
+                const T c = ph.tmh / (((T)1 - seps) + ph.tmh);
+                Bn = seps * c;
+                cB = c;
+            } else {
+                Bn = (T)1;
+                cB = (T)1 / seps;
+            }
+        } else {
+            Bn = seps;
+            cB = (T)1;
+        }
+        mx *= cB; my *= cB; mz *= cB;
+        Mxx *= cB; Myy *= cB; Mzz *= cB; Mxy *= cB; Mxz *= cB; Myz *= cB;
     }
-    mx *= cB; my *= cB; mz *= cB;
-    Mxx *= cB; Myy *= cB; Mzz *= cB; Mxy *= cB; Mxz *= cB; Myz *= cB;
 
     // ---- 5. collision (Eq. 2-4, 10, 12) in deviation form, then store
     const T uu = ux * ux + uy * uy + uz * uz;
     const T uF = ux * ph.F[0] + uy * ph.F[1] + uz * ph.F[2];
-    const bool any_solid = __any_sync(kFull, Bn > (T)0);
     if (!any_solid) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -322,70 +522,117 @@ k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
 
     // ---- 6. force and torque (Eq. 14; Eq. 11 in original mode):
     //         F_p -= B_{n,s} (rho u_s + F/2 - j),  T_p -= (x_n - X_p) x (same)
-    const bool touched = __syncthreads_or(seps > (T)0);
-    if (!touched) return;
+    const bool solid = active && seps > (T)0;
     const T px = (T)0.5 * ph.F[0] - jx, py = (T)0.5 * ph.F[1] - jy, pz = (T)0.5 * ph.F[2] - jz;
-    for (int ch = 0; ch < nchunk; ++ch) {
-        if (nchunk > 1) {
-            nk = ovf ? min(cap, pd.n - ch * cap) : cnt;
-            __syncthreads();
-            load_chunk<L, T>(c, g, tl, pd, tile, ovf, ch, nk, x0, y0, z0, tid);
-            __syncthreads();
-        }
-        for (int k = 0; k < nk; ++k) {
-            const bool has = active && (ovf || ((mask >> k) & 1ull));
-            T v[NC];
+    if (!ovf && lane == 0) s_mask[warp] = any_solid ? wmask : 0ull;
+    if (any_solid) {
+        for (int ch = 0; ch < nchunk; ++ch) {
+            if (ovf) {
+                nk = min(cap, pd.n - ch * cap);
+                __syncwarp();
+                // overflow tiles: each warp restages nothing; records come from global memory
+            }
+            int js = 0;
+            for (int kb = 0; kb < nk; kb += 32) {
+                const int k = kb + lane;
+                bool rel;
+                T ovr[RW];
+                if (!ovf) {
+                    rel = (wmask >> k) & 1ull;
+                } else {
+                    rel = false;
+                    if (k < nk) {
+                        write_record<L, T>(ovr, g, pd, ch * cap + k, x0, y0, z0);
+                        rel = row_hits<L, T>(g, ovr[R_PX], ovr[R_PY], ovr[R_PZ], ovr[R_R] + ph.h, cy, cz, xmax);
+                    }
+                }
+                unsigned bal = __ballot_sync(kFull, rel);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const int kk = kb + src;
+                    bal &= bal - 1u;
+                    T a[RW];
+                    if (!ovf) {
 #pragma unroll
-            for (int q = 0; q < NC; ++q) v[q] = (T)0;
-            bool hit = false;
-            if (has) {
-                T dx, dy, dz;
-                const T e = cand_eps<L, T>(c, g, k, cx, cy, cz, ph.h, dx, dy, dz);
-                if (e > (T)0) {
-                    hit = true;
-                    const T usx = c.ux[k] + c.oy[k] * dz - c.oz[k] * dy;
-                    const T usy = c.uy[k] + c.oz[k] * dx - c.ox[k] * dz;
-                    const T usz = (L::D == 3) ? c.uz[k] + c.ox[k] * dy - c.oy[k] * dx : (T)0;
-                    const T Bs = (PSC == 0) ? cB * e : Bn;
-                    const T dPx = Bs * (rho * usx + px);
-                    const T dPy = Bs * (rho * usy + py);
-                    const T dPz = (L::D == 3) ? Bs * (rho * usz + pz) : (T)0;
-                    if (L::D == 2) {
-                        v[0] = dPx; v[1] = dPy; v[2] = dx * dPy - dy * dPx;
+                        for (int q = 0; q < RW; ++q) a[q] = srec[kk * RW + q];
                     } else {
-                        v[0] = dPx; v[1] = dPy; v[2] = dPz;
-                        v[3] = dy * dPz - dz * dPy;
-                        v[4] = dz * dPx - dx * dPz;
-                        v[5] = dx * dPy - dy * dPx;
+#pragma unroll
+                        for (int q = 0; q < RW; ++q) a[q] = __shfl_sync(kFull, ovr[q], src);
+                    }
+                    T v[NC];
+#pragma unroll
+                    for (int q = 0; q < NC; ++q) v[q] = (T)0;
+                    if (solid) {
+                        T dx, dy, dz;
+                        cand_arm<L, T>(g, cx, cy, cz, a[R_PX], a[R_PY], a[R_PZ], dx, dy, dz);
+                        T e = (T)0;
+                        if (!ovf && js < NSLOT) {
+#pragma unroll
+                            for (int q = 0; q < NSLOT; ++q) if (js == q) e = eslot[q];
+                        } else {
+                            e = shell_eps<T>(dx * dx + dy * dy + dz * dz, a[R_R], a[R_FR], ph.h);
+                        }
+                        if (e > (T)0) {
+                            const T usx = a[R_UX] + a[R_OY] * dz - a[R_OZ] * dy;
+                            const T usy = a[R_UY] + a[R_OZ] * dx - a[R_OX] * dz;
+                            const T usz = (L::D == 3) ? a[R_UZ] + a[R_OX] * dy - a[R_OY] * dx : (T)0;
+                            const T Bs = (PSC == 0) ? cB * e : Bn;
+                            const T dPx = Bs * (rho * usx + px);
+                            const T dPy = Bs * (rho * usy + py);
+                            const T dPz = (L::D == 3) ? Bs * (rho * usz + pz) : (T)0;
+                            if (L::D == 2) {
+                                v[0] = dPx; v[1] = dPy; v[2] = dx * dPy - dy * dPx;
+                            } else {
+                                v[0] = dPx; v[1] = dPy; v[2] = dPz;
+                                v[3] = dy * dPz - dz * dPy;
+                                v[4] = dz * dPx - dx * dPz;
+                                v[5] = dx * dPy - dy * dPx;
+                            }
+                        }
+                    }
+                    ++js;
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                        for (int q = 0; q < NC; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
+                    }
+                    if (lane == 0) {
+                        if (!ovf) {
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) part[((size_t)warp * cap + kk) * NC + q] = v[q];
+                        } else {
+                            const int pid = bits_id(a[R_ID]);
+#pragma unroll
+                            for (int q = 0; q < NC; ++q) {
+                                if (v[q] == (T)0) continue;
+                                double *dst;
+                                if (L::D == 2) dst = (q < 2) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + 2];
+                                else dst = (q < 3) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + q - 3];
+                                atomicAdd(dst, -(double)v[q]);
+                            }
+                        }
                     }
                 }
             }
-            const unsigned b = __ballot_sync(kFull, hit);
-            if (b != 0u) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-                    for (int q = 0; q < NC; ++q) v[q] += __shfl_xor_sync(kFull, v[q], off);
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int q = 0; q < NC; ++q) c.part[((size_t)warp * NC + q) * cap + k] = (b != 0u) ? v[q] : (T)0;
-            }
         }
-        __syncthreads();
-        for (int idx = tid; idx < nk * NC; idx += kThreads) {
-            const int k = idx / NC, q = idx - k * NC;
-            T s = 0;
+    }
+    if (ovf) return;   // uniform over the block
+    __syncthreads();
+    // tile totals in a fixed warp order, one FP64 atomic per particle component
+    for (int idx = tid; idx < cnt * NC; idx += kThreads) {
+        const int k = idx / NC, q = idx - k * NC;
+        T sum = 0;
+        bool any = false;
 #pragma unroll
-            for (int w = 0; w < kWarps; ++w) s += c.part[((size_t)w * NC + q) * cap + k];
-            if (s != (T)0) {
-                const int p = c.id[k];
-                double *dst;
-                if (L::D == 2) dst = (q < 2) ? &pd.F[3 * p + q] : &pd.T[3 * p + 2];
-                else dst = (q < 3) ? &pd.F[3 * p + q] : &pd.T[3 * p + q - 3];
-                atomicAdd(dst, -(double)s);
-            }
+        for (int w = 0; w < kWarps; ++w) {
+            if ((s_mask[w] >> k) & 1ull) { sum += part[((size_t)w * cap + k) * NC + q]; any = true; }
+        }
+        if (any && sum != (T)0) {
+            const int p = bits_id(srec[k * RW + R_ID]);
+            double *dst;
+            if (L::D == 2) dst = (q < 2) ? &pd.F[3 * p + q] : &pd.T[3 * p + 2];
+            else dst = (q < 3) ? &pd.F[3 * p + q] : &pd.T[3 * p + q - 3];
+            atomicAdd(dst, -(double)sum);
         }
     }
 }
@@ -447,7 +694,7 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
                                     const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s) {
     using T = typename Store<S>::T;
     constexpr int NC = (L::D == 2) ? 3 : 6;
-    const size_t smem = cand_smem_bytes<T>(tl.cap, NC);
+    const size_t smem = cs_smem_bytes<T>(tl.cap, NC);
     auto kern = k_collide_stream<L, S, PSC>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -455,7 +702,14 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     }
     dim3 grid(g.nt[0], g.nt[1], g.nt[2]);
     dim3 block(L::TX, L::TY, L::TZ);
-    kern<<<grid, block, smem, s>>>((const S *)fin, (S *)fout, g, make_phys<T>(ph), tl, pd, flags);
+    const PhysT<T> pt = make_phys<T>(ph);
+    const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
+    if (hasF) k_fluid<L, S, true><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+    else k_fluid<L, S, false><<<grid, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || pd.n == 0) return e;
+    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
+    kern<<<(unsigned)ntiles, block, smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
     return cudaGetLastError();
 }
 
