@@ -178,6 +178,49 @@ lbm_status dem_get_contacts(dem_ctx *dem, int *pairs, double *hist, int cap, int
  * out[2] bin/neighbour-list overflows, out[3] skin violations, out[4] particles. */
 lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
 
+/* -------------------------------------------------- stepping without device allocation --- */
+/* The paper has no counterpart to this entry point; it is a service for callers that may
+ * not allocate GPU memory themselves or let a library do it: for example a host program
+ * whose own memory manager owns every device allocation, a plugin living inside such a
+ * program, or a real-time loop that forbids allocation (and the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause) once it runs.
+ *
+ * lbm_psc_step_noalloc performs the same single step as lbm_step (binning, solid fractions,
+ * PSC collision, pull streaming, force and torque) on buffers the caller owns, and
+ * allocates nothing: no cudaMalloc, no cudaFree, no host heap. Its working memory (tile
+ * candidate lists and packed records, f(r) per particle, flag words) is one fixed array of
+ * LBM_NOALLOC_SCRATCH_BYTES bytes that lives in the library image on every GPU that loads
+ * the library, until the process exits. A lattice/particle set needing more working memory
+ * than that is rejected with LBM_ERR_ARG and a message from lbm_noalloc_last_error().
+ *
+ *   p       lattice, extent, bc, tau, body force, storage, psc, shell_h, dev_scale as for
+ *           lbm_create; p->stream is the stream to queue on (NULL = legacy default stream);
+ *           tile_cap is ignored (16 candidate records per tile, more take an exact slow
+ *           path).
+ *   f_in    device buffer with the current state in the storage format of lbm_create's
+ *           contexts: post-collision deviations f_i - w_i, [Q][nz][ny][nx], element type
+ *           double / float / half / bfloat16 (FP16 scaled by dev_scale, default 4096), the
+ *           bytes lbm_save_state writes after its 64-byte header.
+ *   f_out   device buffer of the same size receiving the state after the step (must not
+ *           alias f_in).
+ *   n, X, U, Omega, radius   particles as for lbm_set_particles, but device pointers; the
+ *           caller guarantees the radius and box-size conditions stated there (the device
+ *           data is not inspected on the host).
+ *   F, T    device buffers (n x 3) receiving the force and torque of this step.
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. The call is
+ * asynchronous on p->stream; device-side instability is not reported by this entry point.
+ * Every call shares the one array and finds whatever the previous call left there: each
+ * call clears what must start at zero, but calls that overlap on the GPU (different streams
+ * or host threads at the same time) corrupt each other's results — serialise them. */
+#define LBM_NOALLOC_SCRATCH_BYTES (32u << 20)
+lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in, void *f_out, int n,
+                                const double *X, const double *U, const double *Omega,
+                                const double *radius, double *F, double *T);
+/* Message of the last failed lbm_psc_step_noalloc call (never NULL). */
+const char *lbm_noalloc_last_error(void);
+
 /* Lattice tables: e (Q x 3), w (Q), opposite index (Q). Returns Q, or -1 for an unknown
  * lattice. Pure host function. */
 int lbm_lattice_tables(int lattice, int *e, double *w, int *opp);

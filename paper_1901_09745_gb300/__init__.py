@@ -110,6 +110,8 @@ def lib():
         "dem_get_contacts": ([vp, vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "dem_get_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "dem_get_info": ([vp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
+        "lbm_psc_step_noalloc": ([C.POINTER(LbmParams), vp, vp, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
+        "lbm_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -384,3 +386,15 @@ def dem_get_info(dem):
     _check(dem.fluid, lib().dem_get_info(dem.handle, out, 5))
     return dict(launches=out[0], solve_failures=out[1], overflows=out[2], skin_violations=out[3],
                 particles=out[4])
+
+
+# ------------------------------------------------------------ step without device allocation
+def lbm_psc_step_noalloc(params, f_in, f_out, X=None, U=None, Om=None, radius=None, F=None, T=None):
+    """One PSC step on caller-owned device tensors, allocating nothing (see the header).
+    ``params`` is an ``LbmParams`` (e.g. ``ctx.params``); every array is a CUDA tensor."""
+    n = 0 if radius is None else int(radius.numel())
+    ptr = lambda a: None if a is None else C.c_void_p(a.data_ptr())
+    st = lib().lbm_psc_step_noalloc(C.byref(params), ptr(f_in), ptr(f_out), n, ptr(X), ptr(U), ptr(Om),
+                                    ptr(radius), ptr(F), ptr(T))
+    if st != LBM_OK:
+        raise LbmError(st, lib().lbm_noalloc_last_error().decode())
