@@ -38,6 +38,7 @@ struct DemGeom {
     int nb[3];          // bins per axis
     int bin_cap;
     double skin;
+    float margin;       // slack for FP32 position copies (>> their rounding error)
 };
 
 struct DemPhys {
@@ -53,6 +54,8 @@ struct DemPhys {
 struct DemBufs {
     int n;
     const double *X, *U, *Om, *R;   // state at the start of the sub-step
+    const float4 *Xf;               // FP32 copy (x, y, z, r) of the same positions
+    float4 *Xfo;                    // FP32 copy of the new positions
     double *Xo, *Uo, *Omo;          // state at its end
     const double *Ff, *Tf;          // hydrodynamic force / torque (frozen)
     const double *Xref;             // positions when the neighbour list was built
@@ -63,16 +66,6 @@ struct DemBufs {
     float reject;                   // pairs with an FP32 overlap below -reject cannot touch
 };
 
-__device__ __forceinline__ double min_image_d(double a, double b, int n, int periodic) {
-    double d = __dsub_rn(a, b);
-    if (periodic) {
-        const double half = 0.5 * n;
-        for (int k = 0; k < 4 && d > half; ++k) d = __dsub_rn(d, (double)n);
-        for (int k = 0; k < 4 && d < -half; ++k) d = __dadd_rn(d, (double)n);
-    }
-    return d;
-}
-
 __device__ __forceinline__ int bin_of(double x, int n, int nb, int periodic) {
     int b = (int)floor(x * nb / n);
     if (periodic) { b %= nb; if (b < 0) b += nb; }
@@ -80,11 +73,15 @@ __device__ __forceinline__ int bin_of(double x, int n, int nb, int periodic) {
     return b;
 }
 
-__global__ void k_dem_bin(DemGeom g, int n, const double *X, int *count, int *list, int *flags) {
+__global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, float4 *Xf, int *count,
+                          int *list, int *flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    Xf[i] = make_float4((float)X[3 * i], (float)X[3 * i + 1], (float)X[3 * i + 2], (float)R[i]);
     int b[3] = {0, 0, 0};
-    for (int a = 0; a < g.dim; ++a) b[a] = bin_of(X[3 * i + a], g.n[a], g.nb[a], g.periodic[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (a < g.dim) b[a] = bin_of(X[3 * i + a], g.n[a], g.nb[a], g.periodic[a]);
     const int bin = b[0] + g.nb[0] * (b[1] + g.nb[1] * b[2]);
     const int slot = atomicAdd(&count[bin], 1);
     if (slot < g.bin_cap) list[bin * g.bin_cap + slot] = i;
@@ -107,48 +104,80 @@ __device__ __forceinline__ int axis_bins(int b, int nb, int periodic, int *out) 
 
 __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I);
 
-__global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, const int *count,
-                          const int *list, const int *old_n, const int *old_nbr, const float *old_hist,
-                          int *new_n, int *new_nbr, float *new_hist, double *Xref, double *minv,
-                          double density, int *flags) {
+__global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, const float4 *Xf,
+                          const int *count, const int *list, const int *old_n, const int *old_nbr,
+                          const float *old_hist, int *new_n, int *new_nbr, float *new_hist, double *Xref,
+                          double *minv, double density, int *flags) {
     __shared__ int s_buf[8][kNB];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
     if (i >= n) return;   // whole warp leaves together
     const double xi[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
     const double ri = R[i];
+    const float4 pi = Xf[i];
     int bx[3], by[3], bz[3], nbx, nby, nbz = 1;
     nbx = axis_bins(bin_of(xi[0], g.n[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], bx);
     nby = axis_bins(bin_of(xi[1], g.n[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], by);
     if (g.dim == 3) nbz = axis_bins(bin_of(xi[2], g.n[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], bz);
     else bz[0] = 0;
+    // the (up to 27) neighbouring bins: lane b holds bin b and its slot count, then a warp
+    // prefix sum lets the lanes walk all slots of all bins 32 at a time
+    const int nbins = nbx * nby * nbz;
+    int mybin = 0, mycnt = 0;
+    if (lane < nbins) {
+        const int c = lane % nbx, bb = (lane / nbx) % nby, aa = lane / (nbx * nby);
+        mybin = bx[c] + g.nb[0] * (by[bb] + g.nb[1] * bz[aa]);
+        mycnt = min(count[mybin], g.bin_cap);
+    }
+    int incl = mycnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(kFullMask, incl, off);
+        if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    const int excl = incl - mycnt;
+    const float reach0 = (float)ri + (float)g.skin + g.margin;
     int cnt = 0;
-    for (int a = 0; a < nbz; ++a)
-    for (int b = 0; b < nby; ++b)
-    for (int c = 0; c < nbx; ++c) {
-        const int bin = bx[c] + g.nb[0] * (by[b] + g.nb[1] * bz[a]);
-        const int m = min(count[bin], g.bin_cap);
-        for (int t0 = 0; t0 < m; t0 += 32) {
-            const int t = t0 + lane;
-            bool take = false;
-            int j = -1;
-            if (t < m) {
-                j = list[bin * g.bin_cap + t];
-                if (j != i) {
-                    double d2 = 0.0;
-                    for (int ax = 0; ax < g.dim; ++ax) {
-                        const double d = min_image_d(X[3 * j + ax], xi[ax], g.n[ax], g.periodic[ax]);
-                        d2 += d * d;
-                    }
-                    const double reach = ri + R[j] + g.skin;
-                    take = d2 < reach * reach;
-                }
-            }
-            const unsigned bal = __ballot_sync(kFullMask, take);
-            const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (take && pos < kNB) s_buf[warp][pos] = j;
-            cnt += __popc(bal);
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        // which bin holds slot t: the last bin whose exclusive prefix is <= t (all lanes
+        // take part in the shuffles; lanes past the end use the last slot and discard it)
+        const int tc = min(t, total - 1);
+        int owner = 0;
+        for (int q = 0; q < nbins; ++q) {
+            const int eq = __shfl_sync(kFullMask, excl, q);
+            owner = (eq <= tc) ? q : owner;
         }
+        const int ob = __shfl_sync(kFullMask, mybin, owner);
+        const int oe = __shfl_sync(kFullMask, excl, owner);
+        bool take = false;
+        int j = -1;
+        if (t < total) {
+            j = list[ob * g.bin_cap + (t - oe)];
+            if (j != i) {
+                const float4 pj = Xf[j];
+                float d2 = 0.0f;
+                const float dd[3] = {pj.x - pi.x, pj.y - pi.y, pj.z - pi.z};
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    if (ax >= g.dim) break;
+                    float d = dd[ax];
+                    if (g.periodic[ax]) {
+                        const float half = 0.5f * (float)g.n[ax];
+                        if (d > half) d -= (float)g.n[ax];
+                        else if (d < -half) d += (float)g.n[ax];
+                    }
+                    d2 += d * d;
+                }
+                const float reach = reach0 + pj.w;
+                take = d2 < reach * reach;
+            }
+        }
+        const unsigned bal = __ballot_sync(kFullMask, take);
+        const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+        if (take && pos < kNB) s_buf[warp][pos] = j;
+        cnt += __popc(bal);
     }
     if (cnt > kNB) { if (lane == 0) atomicAdd(&flags[2], 1); cnt = kNB; }
     __syncwarp();
@@ -230,7 +259,7 @@ __device__ __forceinline__ float jkr_s(float t, int *fail) {
 // One contact seen from particle i (neighbour j): force and torque on i in FP32. hist is
 // this view's copy of the pair history; returns 0 and clears it when not in contact.
 __device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, double dist, double dn,
-                             double ri, double rj, double mi, double mj, const double *Ui,
+                             double ri, double rj, float imi, float imj, const double *Ui,
                              const double *Uj, const double *Omi, const double *Omj, float *h,
                              float *fo, float *to, int *fail) {
     const float Rf = (float)(ri * rj / (ri + rj));
@@ -276,7 +305,7 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, doub
         ac = sqrtf(Rf * dp);
         Fne = (4.0f / 3.0f) * Es * sqrtf(Rf) * dp * sqrtf(dp);
     }
-    const float ms = (float)(mi * mj / (mi + mj));
+    const float ms = 1.0f / (imi + imj);        // m* = m_i m_j / (m_i + m_j)
     const float kN = 2.0f * Es * ac;
     const float etaN = ph.alpha_n * sqrtf(ms * kN);
     const float kT = ph.kt_scale * 8.0f * ph.Gs * ac;
@@ -368,45 +397,59 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
     double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0}, ri = 1.0;
     int fail = 0;
     if (valid) {
+#pragma unroll
         for (int a = 0; a < 3; ++a) { xi[a] = b.X[3 * i + a]; ui[a] = b.U[3 * i + a]; oi[a] = b.Om[3 * i + a]; }
         ri = b.R[i];
-        const double mi = 1.0 / b.minv[2 * i];
+        const float4 pif = b.Xf[i];
+        const float imi = (float)b.minv[2 * i];
         const int nn = b.nbr_n[i];
         for (int s = sub; s < nn; s += kLPP) {
             const int j = b.nbr[i * kNB + s];
             float *hp = b.hist + ((size_t)i * kNB + s) * kH;
+            // FP32 pre-filter on the position copies: pairs clearly apart skip the FP64 work
+            const float4 pj = b.Xf[j];
+            float df[3] = {pj.x - pif.x, pj.y - pif.y, pj.z - pif.z};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= dim) { df[a] = 0.0f; continue; }
+                if (g.periodic[a]) {
+                    const float half = 0.5f * (float)g.n[a];
+                    if (df[a] > half) df[a] -= (float)g.n[a];
+                    else if (df[a] < -half) df[a] += (float)g.n[a];
+                }
+            }
+            const bool was = hp[7] != 0.0f;
+            const float dnf = (pif.w + pj.w) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+            if (dnf < -b.reject) {
+                // provably out of contact (the margin dwarfs the FP32 error)
+                if (was) for (int k = 0; k < kH; ++k) hp[k] = 0.0f;
+                continue;
+            }
             // separation X_j - X_i in FP64 (exact subtraction), minimum image; the periodic
             // shift is decided on the FP32 copy, exact for neighbours (|d| << n/2)
             double d[3] = {0.0, 0.0, 0.0};
-            float df[3] = {0.0f, 0.0f, 0.0f};
-            for (int a = 0; a < dim; ++a) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (a >= dim) break;
                 d[a] = __dsub_rn(b.X[3 * j + a], xi[a]);
                 if (g.periodic[a]) {
                     const float half = 0.5f * (float)g.n[a], v = (float)d[a];
                     if (v > half) d[a] = __dsub_rn(d[a], (double)g.n[a]);
                     else if (v < -half) d[a] = __dadd_rn(d[a], (double)g.n[a]);
                 }
-                df[a] = (float)d[a];
             }
             const double rj = b.R[j];
-            const float dnf = (float)(ri + rj) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
-            const bool was = hp[7] != 0.0f;
-            if (dnf < -b.reject) {
-                // provably out of contact (FP32 error is far below the margin)
-                if (was) for (int k = 0; k < kH; ++k) hp[k] = 0.0f;
-                continue;
-            }
             // exact overlap in FP64 with IEEE-rounded operations (bit-identical at both ends)
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
             const double dist = __dsqrt_rn(d2);
             const double dn = __dsub_rn(__dadd_rn(ri, rj), dist);
-            const double mj = 1.0 / b.minv[2 * j];
+            const float imj = (float)b.minv[2 * j];
             float hl[kH];
             for (int k = 0; k < kH; ++k) hl[k] = hp[k];
             float fo[3], to[3];
             const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
             const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
-            if (contact_on_i(ph, dim, d, dist, dn, ri, rj, mi, mj, ui, uj, oi, oj, hl, fo, to, &fail)) {
+            if (contact_on_i(ph, dim, d, dist, dn, ri, rj, imi, imj, ui, uj, oi, oj, hl, fo, to, &fail)) {
                 for (int a = 0; a < 3; ++a) { acc[a] += (double)fo[a]; acc[3 + a] += (double)to[a]; }
             }
             if (was || hl[7] != 0.0f) for (int k = 0; k < kH; ++k) hp[k] = hl[k];
@@ -422,6 +465,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
     // Eq. 21, semi-implicit Euler, hydrodynamic force/torque frozen over the sub-steps
     const double im = b.minv[2 * i], iI = b.minv[2 * i + 1];
     double un[3], xn[3], on[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < dim) {
             un[a] = ui[a] + ph.dt * ((b.Ff[3 * i + a] + acc[a]) * im + ph.g[a]);
@@ -435,7 +479,9 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         on[a] = spin ? oi[a] + ph.dt * (b.Tf[3 * i + a] + acc[3 + a]) * iI : oi[a];
     }
     float disp2 = 0.0f;
-    for (int a = 0; a < dim; ++a) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dim) break;
         float dd = (float)(xn[a] - b.Xref[3 * i + a]);
         if (g.periodic[a]) {
             const float half = 0.5f * (float)g.n[a];
@@ -445,7 +491,9 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         disp2 += dd * dd;
     }
     if (disp2 > 0.25f * (float)(g.skin * g.skin)) atomicAdd(&b.flags[3], 1);
+#pragma unroll
     for (int a = 0; a < 3; ++a) { b.Xo[3 * i + a] = xn[a]; b.Uo[3 * i + a] = un[a]; b.Omo[3 * i + a] = on[a]; }
+    b.Xfo[i] = make_float4((float)xn[0], (float)xn[1], (float)xn[2], (float)ri);
 }
 
 }  // namespace
@@ -458,7 +506,12 @@ struct dem_ctx {
     DemGeom g;
     DemPhys ph;
     double *X2, *U2, *Om2, *Xref, *minv;
+    float4 *Xf[2];           // FP32 copies of the positions (current, next)
     float reject;
+    // CUDA graph of one dem_step call (even sub-step counts), one per neighbour-list parity
+    cudaGraphExec_t gexec[2];
+    const void *gkey[2][16];
+    int gsub[2];
     int *bin_count, *bin_list;
     long long nbins;
     int *nbr_n[2], *nbr[2];
@@ -474,6 +527,8 @@ void dem_release(dem_ctx *d) {
     if (!d) return;
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
     dfree((void **)&d->minv);
+    dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
+    for (int k = 0; k < 2; ++k) if (d->gexec[k]) cudaGraphExecDestroy(d->gexec[k]);
     dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     free(d);
@@ -495,8 +550,11 @@ static lbm_status dem_reserve(dem_ctx *d) {
     if (cap <= d->cap_n) return LBM_OK;
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
     dfree((void **)&d->minv);
+    dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     const size_t v = (size_t)cap * 3 * sizeof(double);
+    DCK(cudaMalloc(&d->Xf[0], (size_t)cap * sizeof(float4)), "cudaMalloc(DEM FP32 positions)");
+    DCK(cudaMalloc(&d->Xf[1], (size_t)cap * sizeof(float4)), "cudaMalloc(DEM FP32 positions)");
     DCK(cudaMalloc(&d->minv, (size_t)cap * 2 * sizeof(double)), "cudaMalloc(DEM inverse mass)");
     DCK(cudaMalloc(&d->X2, v), "cudaMalloc(DEM X)");
     DCK(cudaMalloc(&d->U2, v), "cudaMalloc(DEM U)");
@@ -536,27 +594,6 @@ static lbm_status dem_setup_bins(dem_ctx *d) {
         d->nbins = nb;
         d->g.bin_cap = cap;
     }
-    return LBM_OK;
-}
-
-static lbm_status dem_build_lists(dem_ctx *d) {
-    lbm_ctx *fl = d->fl;
-    lbm_status st = dem_setup_bins(d);
-    if (st != LBM_OK) return st;
-    const int n = d->n;
-    DCK(cudaMemsetAsync(d->bin_count, 0, (size_t)d->nbins * sizeof(int), fl->stream), "memset DEM bins");
-    k_dem_bin<<<(n + 127) / 128, 128, 0, fl->stream>>>(d->g, n, fl->dX, d->bin_count, d->bin_list, fl->flags);
-    DCK(cudaGetLastError(), "DEM bin kernel");
-    const int nx = d->cur ^ 1;
-    k_dem_nbr<<<(n + 7) / 8, 256, 0, fl->stream>>>(d->g, n, fl->dX, fl->dR, d->bin_count, d->bin_list,
-                                                    d->nbr_n[d->cur], d->nbr[d->cur], d->hist[d->cur],
-                                                    d->nbr_n[nx], d->nbr[nx], d->hist[nx], d->Xref, d->minv,
-                                                    d->ph.density, fl->flags);
-    DCK(cudaGetLastError(), "DEM neighbour kernel");
-    d->cur = nx;
-    d->lists_valid = 1;
-    d->launches += 2;
-    fl->launches += 2;
     return LBM_OK;
 }
 
@@ -603,6 +640,45 @@ extern "C" lbm_status dem_destroy(dem_ctx *d) {
     return LBM_OK;
 }
 
+// Queue one dem_step call (list rebuild + sub-steps) without touching host-side state: the
+// particle buffers alternate between the fluid context's and the DEM's own each sub-step,
+// and `flip` (an odd count) tells the caller to swap them afterwards.
+static cudaError_t dem_enqueue(dem_ctx *d, int substeps, int cur) {
+    lbm_ctx *fl = d->fl;
+    cudaStream_t s = fl->stream;
+    const int n = d->n;
+    const int nx = cur ^ 1;
+    cudaError_t e = cudaMemsetAsync(d->bin_count, 0, (size_t)d->nbins * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_dem_bin<<<(n + 127) / 128, 128, 0, s>>>(d->g, n, fl->dX, fl->dR, d->Xf[0], d->bin_count, d->bin_list,
+                                               fl->flags);
+    k_dem_nbr<<<(n + 7) / 8, 256, 0, s>>>(d->g, n, fl->dX, fl->dR, d->Xf[0], d->bin_count, d->bin_list,
+                                           d->nbr_n[cur], d->nbr[cur], d->hist[cur], d->nbr_n[nx], d->nbr[nx],
+                                           d->hist[nx], d->Xref, d->minv, d->ph.density, fl->flags);
+    DemBufs b;
+    b.n = n;
+    b.R = fl->dR;
+    b.Ff = fl->dF;
+    b.Tf = fl->dT;
+    b.Xref = d->Xref;
+    b.nbr_n = d->nbr_n[nx];
+    b.nbr = d->nbr[nx];
+    b.hist = d->hist[nx];
+    b.minv = d->minv;
+    b.flags = fl->flags;
+    b.reject = d->reject;
+    const int threads = 128;
+    const int blocks = (int)(((long long)n * kLPP + threads - 1) / threads);
+    double *X[2] = {fl->dX, d->X2}, *U[2] = {fl->dU, d->U2}, *Om[2] = {fl->dOm, d->Om2};
+    for (int k = 0; k < substeps; ++k) {
+        const int src = k & 1, dst = src ^ 1;
+        b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src];
+        b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst];
+        k_dem_substep<<<blocks, threads, 0, s>>>(d->g, d->ph, b);
+    }
+    return cudaGetLastError();
+}
+
 extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     if (!d) return LBM_ERR_ARG;
     lbm_ctx *fl = d->fl;
@@ -611,42 +687,67 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     if (fl->np != d->n) d->lists_valid = 0;
     lbm_status st = dem_reserve(d);
     if (st != LBM_OK) return st;
-    st = dem_build_lists(d);
+    st = dem_setup_bins(d);
     if (st != LBM_OK) return st;
-    DemBufs b;
-    b.n = d->n;
-    b.R = fl->dR;
-    b.Ff = fl->dF;
-    b.Tf = fl->dT;
-    b.Xref = d->Xref;
-    b.nbr_n = d->nbr_n[d->cur];
-    b.nbr = d->nbr[d->cur];
-    b.hist = d->hist[d->cur];
-    b.minv = d->minv;
-    b.flags = fl->flags;
-    // largest delta_C of any pair (R <= r_max / 2) plus a margin far above FP32 error
+    // largest delta_C of any pair (R <= r_max / 2) plus a margin far above the FP32 error of
+    // the position copies
     {
+        int nmax = 1;
+        for (int a = 0; a < d->g.dim; ++a) nmax = fl->g.n[a] > nmax ? fl->g.n[a] : nmax;
+        d->g.margin = (float)(1e-3 + 8.0 * nmax / 16777216.0);
         const double Es = d->p.E / (2.0 * (1.0 - d->p.poisson * d->p.poisson));
         const double Rm = 0.5 * fl->rmax;
         const double a0 = cbrt(9.0 * kPi * d->p.gamma * Rm * Rm / Es);
         const double dC = d->p.adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * Rm) : 0.0;
-        b.reject = (float)(dC + 1e-3);
+        d->reject = (float)(dC + d->g.margin);
     }
-    const int threads = 128;
-    const int blocks = (int)(((long long)d->n * kLPP + threads - 1) / threads);
-    for (int s = 0; s < substeps; ++s) {
-        b.X = fl->dX; b.U = fl->dU; b.Om = fl->dOm;
-        b.Xo = d->X2; b.Uo = d->U2; b.Omo = d->Om2;
-        k_dem_substep<<<blocks, threads, 0, fl->stream>>>(d->g, d->ph, b);
-        DCK(cudaGetLastError(), "DEM sub-step kernel");
-        // the new state becomes the fluid context's particle state
-        double *t;
-        t = fl->dX; fl->dX = d->X2; d->X2 = t;
-        t = fl->dU; fl->dU = d->U2; d->U2 = t;
-        t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
-        d->launches += 1;
-        fl->launches += 1;
+    const int cur = d->cur;
+    const int kernels = 2 + substeps;
+    // even sub-step counts leave every buffer where it started, so the whole call can be
+    // replayed from a CUDA graph (one per neighbour-list parity), keyed on every pointer
+    // and size it was captured with
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DCK(cudaStreamIsCapturing(fl->stream, &cs), "cudaStreamIsCapturing");
+    unsigned rbits;
+    memcpy(&rbits, &d->reject, sizeof(rbits));
+    const void *key[16] = {fl->dX, fl->dU, fl->dOm, fl->dR, fl->dF, fl->dT, d->X2, d->U2, d->Om2, d->Xf[0],
+                           d->minv, d->bin_count, (const void *)(size_t)d->n, (const void *)(size_t)rbits,
+                           (const void *)(size_t)(d->g.nb[0] + 4096LL * (d->g.nb[1] + 4096LL * d->g.nb[2])),
+                           (const void *)(size_t)d->g.bin_cap};
+    bool replayed = false;
+    if (substeps % 2 == 0 && cs == cudaStreamCaptureStatusNone) {
+        bool same = d->gexec[cur] && d->gsub[cur] == substeps;
+        for (int k = 0; same && k < 16; ++k) same = (d->gkey[cur][k] == key[k]);
+        if (!same) {
+            if (d->gexec[cur]) { cudaGraphExecDestroy(d->gexec[cur]); d->gexec[cur] = NULL; }
+            cudaGraph_t graph = NULL;
+            DCK(cudaStreamBeginCapture(fl->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            cudaError_t eq = dem_enqueue(d, substeps, cur);
+            cudaError_t ec = cudaStreamEndCapture(fl->stream, &graph);
+            DCK(eq, "DEM kernels (capture)");
+            DCK(ec, "cudaStreamEndCapture");
+            cudaError_t ei = cudaGraphInstantiate(&d->gexec[cur], graph, 0);
+            cudaGraphDestroy(graph);
+            DCK(ei, "cudaGraphInstantiate");
+            d->gsub[cur] = substeps;
+            for (int k = 0; k < 16; ++k) d->gkey[cur][k] = key[k];
+        }
+        DCK(cudaGraphLaunch(d->gexec[cur], fl->stream), "cudaGraphLaunch");
+        replayed = true;
     }
+    if (!replayed) {
+        DCK(dem_enqueue(d, substeps, cur), "DEM kernels");
+        if (substeps & 1) {
+            double *t;
+            t = fl->dX; fl->dX = d->X2; d->X2 = t;
+            t = fl->dU; fl->dU = d->U2; d->U2 = t;
+            t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
+        }
+    }
+    d->cur = cur ^ 1;
+    d->lists_valid = 1;
+    d->launches += kernels;
+    fl->launches += kernels;
     fl->bins_valid = 0;   // particles moved: the fluid re-bins before its next step
     return LBM_OK;
 }
