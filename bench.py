@@ -270,6 +270,24 @@ def run_ours(args, rank, local_rank, world):
     e2e_s = reduce_max(time.perf_counter() - h0, world, dev)
     P.lbm_destroy(ctx)
 
+    # the collide-stream kernel alone on the same grid and particles, per storage form
+    storage_cmp = {}
+    if rank == 0:
+        for st in ("f32", "f16", "bf16"):
+            c2 = P.lbm_create(w["lattice"], nx, ny, nz, bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                              storage=st, stream=stream.cuda_stream)
+            P.lbm_set_particles(c2, w["X"], w["U"], w["Om"], w["r"])
+            P.lbm_step(c2, 5)
+            P.lbm_kernel_timing(c2, 1)
+            P.lbm_step(c2, 200)
+            kms, kn = P.lbm_kernel_timing(c2, 0)
+            P.lbm_destroy(c2)
+            us = kms / max(kn, 1) * 1e3
+            byt = 2.0 * w["lattice"] * BYTES[st] * ncell
+            storage_cmp[st] = {"kernel_us": round(us, 2), "kernel_mlups": round(ncell / us, 1),
+                               "bytes_per_cell": 2 * w["lattice"] * BYTES[st],
+                               "GBs": round(byt / (us * 1e-6) / 1e9, 1)}
+
     if rank != 0:
         return None
     q, sbytes = w["lattice"], BYTES[storage]
@@ -307,6 +325,9 @@ def run_ours(args, rank, local_rank, world):
                 "h2d_bytes_per_step": int(n * 10 * 8), "d2h_bytes_per_step": int(n * 6 * 8),
                 "steps": e2e_steps},
         "gpu_launches": int(launches1 - launches0),
+        "storage_compare": {"note": "collide-stream kernels only (fluid + PSC tiles), static particles, "
+                                    "same grid; error against FP64 reported by the test suite",
+                            **storage_cmp},
         "clocks": clocks,
     }
     return line
