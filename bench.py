@@ -46,6 +46,7 @@ def parse_args(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dem", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args(argv)
 
 
@@ -184,6 +185,8 @@ WORKLOAD_TEXT = {
     "c3": "D3Q19 256^3 periodic, tau 0.6, 2000 static spheres r=6, body force 1e-6",
     "c3dense": "D3Q19 256^3 periodic, tau 0.6, 5563 static spheres r=6 (solid fraction 0.3)",
     "c5": "D3Q19 512^3 channel (walls z), tau 0.55, 50000 spheres r~U(3,8)",
+    "c4": "D3Q19 128^3 periodic, tau 0.7, 200 static spheres r=5, body force 1e-6, 500 steps, "
+          "checkpoint every 50",
 }
 DEFAULT_STORAGE = {"c2": "f32", "c3": "f32", "c3dense": "f32", "c5": "f16", "c4": "f32", "c1": "f64"}
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
@@ -288,6 +291,8 @@ def run_ours(args, rank, local_rank, world):
                                "bytes_per_cell": 2 * w["lattice"] * BYTES[st],
                                "GBs": round(byt / (us * 1e-6) / 1e9, 1)}
 
+    adjoint = adjoint_timing(P, torch, stream) if (rank == 0 and not args.no_adjoint) else None
+
     if rank != 0:
         return None
     q, sbytes = w["lattice"], BYTES[storage]
@@ -330,7 +335,47 @@ def run_ours(args, rank, local_rank, world):
                             **storage_cmp},
         "clocks": clocks,
     }
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     return line
+
+
+def adjoint_timing(P, torch, stream):
+    """Adjoint/forward time on the adjoint workload (D3Q19 128^3, 200 static spheres, 500
+    steps, checkpoint every 50), FP32 storage: the forward is T plain steps (forces every
+    step); the adjoint call runs the same T steps with checkpoints, re-runs each segment and
+    sweeps back. Both timed with CUDA events on the context's stream after one untimed call
+    (which also sizes the adjoint workspace)."""
+    import synth
+    w = synth.workload("c4")
+    T, K = w["steps"], w["checkpoint"]
+    ncell = int(np.prod(w["n"]))
+    ctx = P.lbm_create(19, *w["n"], bc=w["bc"], tau=w["tau"], body_force=w["body_force"], storage="f32",
+                       stream=stream.cuda_stream)
+    P.lbm_set_particles(ctx, w["X"], w["U"], w["Om"], w["r"])
+    P.lbm_adjoint_drag(ctx, T, K)
+    P.lbm_step(ctx, 20)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    P.lbm_step(ctx, T)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    J, dX, dF = P.lbm_adjoint_drag(ctx, T, K)
+    ev[3].record(stream)
+    torch.cuda.synchronize()
+    P.lbm_destroy(ctx)
+    fwd, adj = ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+    q, s = 19, 4
+    return {"workload": "c4: " + WORKLOAD_TEXT["c4"], "storage": "f32",
+            "fwd_ms": round(fwd, 3), "adjoint_ms": round(adj, 3), "ratio": round(adj / fwd, 3),
+            "fwd_mlups": round(ncell * T / (fwd * 1e-3) / 1e6, 1),
+            "bytes_per_cell_step": {"forward": 2 * q * s, "adjoint_min": 7 * q * s},
+            "ratio_at_roofline": 3.5,
+            "note": "adjoint = forward with checkpoints (2Qs) + segment re-run (2Qs) + reverse sweep "
+                    "(reads state and adjoint, writes adjoint: 3Qs) per cell and step",
+            "J": J, "max_abs_dJdX": float(np.max(np.abs(dX))), "dJdF": [float(v) for v in dF]}
 
 
 # ------------------------------------------------------------------------ CPU oracle

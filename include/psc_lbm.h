@@ -120,6 +120,24 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t *used);
 lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size);
 
+/* Replace the macroscopic body force F of Eq. 4 for the steps that follow. */
+lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F);
+
+/* Gradient of the time-averaged drag J = (1/T) sum_{t<T} sum_p F_{p,x}(t) (F_p of Eq. 14)
+ * over the next T = nsteps steps, with respect to every particle position (dJdX, n x 3)
+ * and the body force (dJdF, 3), by a hand-written reverse of the collide-stream step (the
+ * paper has no adjoint; this is a derived quantity of Eq. 1-18). The particles must be
+ * static (U = Omega = 0: LBM_ERR_UNSUPPORTED otherwise), storage FP32 or FP64, the
+ * modified scheme, and every tile's candidates within tile_cap. Runs the T forward steps
+ * (the context ends at step T as after lbm_step(ctx, T)), keeping a checkpoint every
+ * checkpoint_every steps, then the reverse sweep, re-running each segment forward. The
+ * gradient is exact for the discrete step except at the clamps of Table 1 (eps = 0 or 1,
+ * sum eps = 1), where the one-sided derivative inside the unclamped region is used.
+ * Memory: about (T / checkpoint_every + checkpoint_every + 2) population buffers.
+ * J, dJdX and dJdF go to device memory when on_device, else host (synchronises). */
+lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J, double *dJdX,
+                            double *dJdF, int on_device);
+
 /* Counters (the first n of): out[0] = steps taken, out[1] = tiles whose candidate list
  * overflowed tile_cap in the last binning (handled by a slower exact path, never an
  * error), out[2] = largest candidate count of a tile in the last binning, out[3] =

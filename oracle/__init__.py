@@ -124,6 +124,9 @@ def _extra_signatures(L):
     L.ora_pairs_within.restype = C.c_int
     L.ora_dem_pair_force.argtypes = [pp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
     L.ora_dem_pair_force.restype = C.c_int
+    Pp = C.POINTER(Params)
+    L.ora_drag.argtypes = [Pp, dp, C.c_int, C.c_int, dp, dp, dp, dp, dp]
+    L.ora_drag.restype = C.c_int
 
 
 def jkr_delta(a, a0, R):
@@ -313,3 +316,13 @@ def run(p, f, nsteps, X=None, U=None, Om=None, rad=None):
                        _d(F), _d(T))
     _check(rc, "run")
     return F[:n], T[:n]
+
+
+def drag(p, f0, nsteps, X, rad, U=None, Om=None):
+    """J = (1/T) sum_t sum_p F_{p,x}(t) over nsteps from a copy of f0 (static particles)."""
+    f = np.ascontiguousarray(np.array(f0, dtype=np.float64))
+    X, U, Om, rad = _particles(X, U, Om, rad)
+    J = np.zeros(1)
+    _check(lib().ora_drag(C.byref(p), _d(f), int(nsteps), X.shape[0], _d(X), _d(U), _d(Om), _d(rad), _d(J)),
+           "drag")
+    return float(J[0])

@@ -475,3 +475,23 @@ int ora_equilibrium(const ora_params *p, const double *rho, const double *u, dou
         for (i = 0; i < L.q; ++i) f[i * ncell + c] = feq(&L, i, rho[c], &u[3 * c]);
     return ORA_OK;
 }
+
+/* Time-averaged x-drag J = (1/T) sum_{t<T} sum_p F_{p,x}(t) over nsteps steps (Eq. 14
+ * forces, static particles); f advances by nsteps. The finite-difference gradient of this
+ * objective is the oracle's gradient for the adjoint checks. */
+int ora_drag(const ora_params *p, double *f, int nsteps, int np, const double *X, const double *U,
+             const double *Om, const double *rad, double *J)
+{
+    double *F = (double *)malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
+    double *T = (double *)malloc(sizeof(double) * 3 * (size_t)(np > 0 ? np : 1));
+    int t, s, rc = ORA_OK;
+    if (!F || !T) { free(F); free(T); return ORA_ERR_OOM; }
+    *J = 0.0;
+    for (t = 0; t < nsteps && rc == ORA_OK; ++t) {
+        rc = ora_step(p, f, np, X, U, Om, rad, F, T, NULL);
+        for (s = 0; s < np; ++s) *J += F[3 * s] / nsteps;
+    }
+    free(F);
+    free(T);
+    return rc;
+}

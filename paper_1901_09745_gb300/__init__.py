@@ -102,6 +102,8 @@ def lib():
         "lbm_lattice_tables": ([C.c_int, ip, dp, ip], C.c_int),
         "lbm_last_error": ([vp], C.c_char_p),
         "lbm_kernel_timing": ([vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
+        "lbm_set_body_force": ([vp, vp], C.c_int),
+        "lbm_adjoint_drag": ([vp, C.c_int, C.c_int, vp, vp, vp, C.c_int], C.c_int),
     }
     optional = {
         "dem_create": ([C.POINTER(DemParams), vp, C.POINTER(C.c_void_p)], C.c_int),
@@ -398,3 +400,48 @@ def lbm_psc_step_noalloc(params, f_in, f_out, X=None, U=None, Om=None, radius=No
                                     ptr(radius), ptr(F), ptr(T))
     if st != LBM_OK:
         raise LbmError(st, lib().lbm_noalloc_last_error().decode())
+
+
+# --------------------------------------------------------------------------------- adjoint
+def lbm_set_body_force(ctx, F):
+    F = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(3))
+    _check(ctx, lib().lbm_set_body_force(ctx.handle, F.ctypes.data_as(C.c_void_p)))
+    ctx.params.body_force[0], ctx.params.body_force[1], ctx.params.body_force[2] = (float(v) for v in F)
+
+
+def lbm_adjoint_drag(ctx, nsteps, checkpoint_every):
+    """(J, dJ/dX (n, 3), dJ/dF (3,)) of the time-averaged x-drag over the next nsteps."""
+    J = np.zeros(1)
+    dX = np.zeros((max(ctx.np, 1), 3))
+    dF = np.zeros(3)
+    _check(ctx, lib().lbm_adjoint_drag(ctx.handle, int(nsteps), int(checkpoint_every),
+                                       J.ctypes.data_as(C.c_void_p), dX.ctypes.data_as(C.c_void_p),
+                                       dF.ctypes.data_as(C.c_void_p), 0))
+    return float(J[0]), dX[: ctx.np].copy(), dF
+
+
+def psc_drag(ctx, f0, X, radius, F, nsteps, checkpoint_every):
+    """Differentiable time-averaged drag: a torch scalar J(X, F) whose backward pass uses the
+    library's adjoint. ``ctx`` is a context whose particles are static; ``f0`` (numpy,
+    pre-collision populations) is the initial state of every evaluation."""
+    import torch
+
+    class _PscDrag(torch.autograd.Function):
+        @staticmethod
+        def forward(actx, Xt, Ft):
+            lbm_set_body_force(ctx, Ft.detach().cpu().numpy())
+            lbm_set_populations(ctx, f0)
+            Xn = Xt.detach().cpu().numpy()
+            z = np.zeros_like(Xn)
+            lbm_set_particles(ctx, Xn, z, z, np.asarray(radius, dtype=np.float64))
+            J, dX, dF = lbm_adjoint_drag(ctx, nsteps, checkpoint_every)
+            actx.save_for_backward(torch.as_tensor(dX, dtype=Xt.dtype, device=Xt.device),
+                                   torch.as_tensor(dF, dtype=Ft.dtype, device=Ft.device))
+            return torch.as_tensor(J, dtype=Xt.dtype, device=Xt.device)
+
+        @staticmethod
+        def backward(actx, g):
+            dX, dF = actx.saved_tensors
+            return g * dX, g * dF
+
+    return _PscDrag.apply(X, F)

@@ -1,0 +1,360 @@
+// adjoint.cu -- hand-written reverse of the PSC collide-stream step (Liu & Wu, arXiv
+// 1901.09745, Eq. 1-6, 9, 12-18) for gradients of the time-averaged drag
+//     J = (1/T) sum_{t<T} sum_p F_{p,x}(t)        (F_p of Eq. 14)
+// with respect to every particle position X_p and the body force F, for particles that do
+// not move or spin during the rollout (u_s = 0).
+//
+// With u_s = 0 the solid term of Eq. 12 is sum_s B_{n,s} Omega^s_i = B_n (f_-i - f^eq_-i
+// - f_i) + B_n rho w_i and the per-step drag is J_t = sum_n B_n (j_x - F_x/2): both depend
+// on the positions only through each cell's total weight B_n (the split B_{n,s} of Eq. 13
+// drops out). Writing g_t for the stored post-collision field and p_t = S(g_t) for the
+// pulled pre-collision populations, g_{t+1} = C(p_t), the reverse sweep is
+//     a_t = (dC/dp)^T lambda_{t+1} + (1/T) dJ_t/dp,      lambda_t = S^T a_t,
+//     dJ/dX += sum_n Lambda_n dB_n/dX,   Lambda_n = lambda.dC/dB + (1/T)(j_x - F_x/2),
+//     dJ/dF += (dC/dF)^T lambda_{t+1} + (1/T) dJ_t/dF.
+// dC/dp is applied exactly: the direct (diagonal + opposite) part plus the part through
+// rho and u, which costs O(Q) per cell. S^T is the push along the same links (bounce-back
+// links return to the own cell), a permutation, so every adjoint value is written once.
+// dB_n/dX follows Eq. 9 at eps_n and Eq. 15: dB/deps = a (1 + a)/((1 - eps) + a)^2 with
+// a = tau - 1/2, deps_s/dX_p = (x_n - X_p)/|x_n - X_p| on unclamped shell cells, zero
+// where eps is clamped to 0 or 1 or where sum eps >= 1 (eps_n = 1, Table 1 Step 5).
+//
+// The forward rollout keeps a checkpoint every K steps; the reverse sweep re-runs each
+// segment forward (storing its K states) and then walks it backwards.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "capi_internal.h"
+#include "psc_kernels.cuh"
+
+namespace psc {
+
+template <class L, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict__ lam_out, Geom g,
+          PhysT<T> ph, Tiles tl, Parts pd, T invT, double *dJdX, double *dJdF) {
+    constexpr int Q = L::Q;
+    constexpr int D = L::D;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *srec = reinterpret_cast<T *>(smem);                 // [cap][RW]
+    T *part = srec + (size_t)tl.cap * RW;                  // [kWarps][cap][D] warp partials
+    __shared__ T s_dF[kWarps][3];
+
+    const int tid = threadIdx.x + L::TX * (threadIdx.y + L::TY * threadIdx.z);
+    const int lane = tid & 31, warp = tid >> 5;
+    const int x0 = blockIdx.x * L::TX, y0 = blockIdx.y * L::TY, z0 = blockIdx.z * L::TZ;
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
+    const bool active = x < g.n[0] && y < g.n[1] && z < g.n[2];
+    const long long tile = blockIdx.x + (long long)g.nt[0] * (blockIdx.y + (long long)g.nt[1] * blockIdx.z);
+    const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
+    const long long N = g.ncell;
+    const int cap = tl.cap;
+    const int cnt = (pd.n > 0) ? min(tl.count[tile], cap) : 0;   // overflow is refused on the host
+    const T *recs = reinterpret_cast<const T *>(tl.blocks) + tile * block_elems<T>(cap) + head_elems<T>();
+    for (int w = tid; w < cnt * RW; w += kThreads) srec[w] = recs[w];
+
+    // ---- forward quantities of this step (pull, Eq. 5)
+    T d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = active ? pull_one<L, T>(gt, g, x, y, z, cell, i, ph.sc) : (T)0;
+    T drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        drho += d[i];
+        j[0] += L::ex(i) * d[i]; j[1] += L::ey(i) * d[i]; j[2] += L::ez(i) * d[i];
+    }
+    const T rho = (T)1 + drho;
+    const T u[3] = {(j[0] + (T)0.5 * ph.F[0]) / rho, (j[1] + (T)0.5 * ph.F[1]) / rho, (j[2] + (T)0.5 * ph.F[2]) / rho};
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T uF = u[0] * ph.F[0] + u[1] * ph.F[1] + u[2] * ph.F[2];
+    __syncthreads();
+
+    // ---- the cell's total solid fraction and weight (Table 1, Eq. 9 at eps_n)
+    const T cx = (T)threadIdx.x, cy = (T)threadIdx.y, cz = (T)threadIdx.z;
+    T seps = 0;
+    for (int k = 0; k < cnt && active; ++k) {
+        const T *rk = srec + k * RW;
+        T dx, dy, dz;
+        cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
+        seps += shell_eps<T>(dx * dx + dy * dy + dz * dz, rk[R_R], rk[R_FR], ph.h);
+    }
+    const T en = seps < (T)1 ? seps : (T)1;
+    const T den = ((T)1 - en) + ph.tmh;
+    const T B = en * ph.tmh / den;
+    const T dBde = (seps > (T)0 && seps < (T)1) ? ph.tmh * ((T)1 + ph.tmh) / (den * den) : (T)0;
+    const T omB = (T)1 - B;
+
+    // ---- adjoint of the collision at this cell
+    T lam[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) lam[i] = active ? lam_in[(long long)i * N + cell] : (T)0;
+    T Arho = 0, Au[3] = {0, 0, 0}, dCdB = 0, dFu[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int o = opp<L>(i);
+        const T w = (T)weight<L>(i);
+        const T e[3] = {(T)L::ex(i), (T)L::ey(i), (T)L::ez(i)};
+        const T eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+        const T eF = e[0] * ph.F[0] + e[1] * ph.F[1] + e[2] * ph.F[2];
+        const T poly_i = (T)1 + (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu;   // feq_i / (rho w)
+        const T poly_o = (T)1 - (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu;   // feq_-i / (rho w)
+        const T dfeq_i = w * (drho + rho * (poly_i - (T)1));                    // feq_i - w
+        const T dfeq_o = w * (drho + rho * (poly_o - (T)1));
+        const T G = ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
+        const T li = lam[i];
+        // d C_i / d B: the solid term is B (f_-i - feq_-i - f_i) + B (rho - 1) w_i in deviations
+        dCdB += li * (ph.omega * (d[i] - dfeq_i) + (d[o] - dfeq_o - d[i]) + drho * w - G);
+        // through rho: feq/rho, and the solid term B rho w_i
+        Arho += li * (omB * ph.omega * w * poly_i - B * w * poly_o + B * w);
+        // through u: grad_u feq_i = rho w (3 e + 9 (e.u) e - 3 u), grad_u feq_-i likewise with -e,
+        // grad_u G_i = guo w (-3 F + 9 (e.F) e)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const T gi = rho * w * ((T)3 * e[a] + (T)9 * eu * e[a] - (T)3 * u[a]);
+            const T go = rho * w * (-(T)3 * e[a] + (T)9 * eu * e[a] - (T)3 * u[a]);
+            const T gG = ph.guo * w * (-(T)3 * ph.F[a] + (T)9 * eF * e[a]);
+            Au[a] += li * (omB * ph.omega * gi - B * go + omB * gG);
+            // explicit dependence of G_i on F at fixed u
+            dFu[a] += li * omB * ph.guo * w * ((T)3 * (e[a] - u[a]) + (T)9 * eu * e[a]);
+        }
+    }
+    // a_k = lambda_k (1 - (1-B) omega - B) + B lambda_-k + Arho + Au.(e_k - u)/rho + (B/T) e_kx,
+    // pushed back along the link it was pulled from (S^T)
+    const T Auu = Au[0] * u[0] + Au[1] * u[1] + Au[2] * u[2];
+    const T diag = (T)1 - omB * ph.omega - B;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        const T ek[3] = {(T)L::ex(k), (T)L::ey(k), (T)L::ez(k)};
+        const T a = lam[k] * diag + B * lam[opp<L>(k)] + Arho +
+                    (Au[0] * ek[0] + Au[1] * ek[1] + Au[2] * ek[2] - Auu) / rho + invT * B * ek[0];
+        if (!active) continue;
+        int s[3] = {x - L::ex(k), y - L::ey(k), z - L::ez(k)};
+        bool bounce = false;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (s[q] < 0 || s[q] >= g.n[q]) {
+                if (g.periodic[q]) s[q] += (s[q] < 0) ? g.n[q] : -g.n[q];
+                else bounce = true;
+            }
+        }
+        if (bounce) lam_out[(long long)opp<L>(k) * N + cell] = a;
+        else lam_out[(long long)k * N + (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2])] = a;
+    }
+
+    // ---- body force: through u (du/dF = I/(2 rho)), explicit in G, and J_t's -B F_x/2
+    T vF[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) vF[a] = active ? Au[a] / ((T)2 * rho) + dFu[a] : (T)0;
+    vF[0] += active ? -invT * B * (T)0.5 : (T)0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) vF[a] += __shfl_xor_sync(kFull, vF[a], off);
+    if (lane == 0) for (int a = 0; a < 3; ++a) s_dF[warp][a] = vF[a];
+
+    // ---- positions: Lambda_n dB/deps_n deps_s/dX_s on unclamped shell cells
+    const T Lam = dCdB + invT * (j[0] - (T)0.5 * ph.F[0]);
+    const T coef = (active && dBde != (T)0) ? Lam * dBde : (T)0;
+    const bool any = __syncthreads_or(coef != (T)0);
+    if (tid < 3) {
+        T sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += s_dF[w][tid];
+        if (sum != (T)0) atomicAdd(&dJdF[tid], (double)sum);
+    }
+    if (!any) return;
+    for (int k = 0; k < cnt; ++k) {
+        const T *rk = srec + k * RW;
+        T v[3] = {0, 0, 0};
+        if (coef != (T)0) {
+            T dx, dy, dz;
+            cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
+            const T d2 = dx * dx + dy * dy + dz * dz;
+            const T r = rk[R_R];
+            if (d2 < (r + ph.h) * (r + ph.h)) {
+                const T dist = sqrt_t(d2);
+                const T e = rk[R_FR] - (dist - r);
+                if (dist > r - ph.h && e > (T)0 && e < (T)1 && dist > (T)0) {
+                    const T c = coef / dist;
+                    v[0] = c * dx; v[1] = c * dy; v[2] = c * dz;
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(kFull, v[a], off);
+        if (lane == 0) for (int a = 0; a < D; ++a) part[((size_t)warp * cap + k) * D + a] = v[a];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < cnt * D; idx += kThreads) {
+        const int k = idx / D, a = idx - k * D;
+        T sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += part[((size_t)w * cap + k) * D + a];
+        if (sum != (T)0) atomicAdd(&dJdX[3 * bits_id(srec[k * RW + R_ID]) + a], (double)sum);
+    }
+}
+
+// J += (1/T) sum_p F_{p,x} of the step just taken
+__global__ void k_sum_fx(const double *F, int n, double invT, double *J) {
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) a += F[3 * p];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *J += invT * s[0];
+}
+
+template <class L, typename T>
+cudaError_t launch_adjoint_t(const void *gt, const void *lam_in, void *lam_out, const Geom &g, const Phys &ph,
+                             const Tiles &tl, const Parts &pd, double invT, double *dJdX, double *dJdF,
+                             cudaStream_t s) {
+    const size_t smem = (size_t)tl.cap * RW * sizeof(T) + (size_t)kWarps * tl.cap * L::D * sizeof(T);
+    auto kern = k_adjoint<L, T>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(g.nt[0], g.nt[1], g.nt[2]);
+    dim3 block(L::TX, L::TY, L::TZ);
+    kern<<<grid, block, smem, s>>>((const T *)gt, (const T *)lam_in, (T *)lam_out, g, make_phys<T>(ph), tl, pd,
+                                   (T)invT, dJdX, dJdF);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(int storage, int lattice, const void *gt, const void *lam_in, void *lam_out,
+                           const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd, double invT,
+                           double *dJdX, double *dJdF, cudaStream_t s) {
+    if (storage == ST_F64) {
+        return lattice == 9 ? launch_adjoint_t<D2Q9, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s)
+                            : launch_adjoint_t<D3Q19, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s);
+    }
+    return lattice == 9 ? launch_adjoint_t<D2Q9, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s)
+                        : launch_adjoint_t<D3Q19, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s);
+}
+
+}  // namespace psc
+
+using namespace psc;
+
+#define ACK(call, what)                                         \
+    do {                                                        \
+        lbm_status st_ = ctx_cuda(ctx, (call), (what));         \
+        if (st_ != LBM_OK) { status = st_; goto done; }         \
+    } while (0)
+
+extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J,
+                                       double *dJdX, double *dJdF, int on_device) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 1 || checkpoint_every < 1) { ctx_error(ctx, "nsteps and checkpoint_every must be >= 1"); return LBM_ERR_ARG; }
+    if (ctx->p.storage != LBM_F32 && ctx->p.storage != LBM_F64) {
+        ctx_error(ctx, "the adjoint supports FP32 and FP64 storage");
+        return LBM_ERR_UNSUPPORTED;
+    }
+    if (ctx->p.psc != LBM_PSC_MODIFIED) { ctx_error(ctx, "the adjoint supports the modified PSC scheme"); return LBM_ERR_UNSUPPORTED; }
+    const int n = ctx->np;
+    const int K = checkpoint_every;
+    const int nseg = (nsteps + K - 1) / K;
+    const size_t pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
+    const size_t v3 = (size_t)(n > 0 ? n : 1) * 3 * sizeof(double);
+    lbm_status status = LBM_OK;
+    Parts scratch_parts;
+    Tiles tl;
+    // static, non-moving particles only (u_s = 0)
+    if (n > 0) {
+        double *h = (double *)malloc(2 * v3);
+        if (!h) return LBM_ERR_OOM;
+        cudaError_t e = cudaMemcpyAsync(h, ctx->dU, v3, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char *)h + v3, ctx->dOm, v3, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        bool moving = false;
+        for (int i = 0; i < 6 * n && e == cudaSuccess; ++i) moving |= (h[i] != 0.0);
+        free(h);
+        if (e != cudaSuccess) return ctx_cuda(ctx, e, "read particle velocities");
+        if (moving) { ctx_error(ctx, "the adjoint is for static particles (U = Omega = 0)"); return LBM_ERR_UNSUPPORTED; }
+    }
+    // one workspace, kept by the context between calls: checkpoints [nseg], segment states
+    // [K], two adjoint fields, gradients + J, scratch forces and torques
+    const size_t v3a = (v3 + 255) & ~(size_t)255;
+    const size_t popa = (pop + 255) & ~(size_t)255;      // buffer stride, 256-byte aligned
+    const size_t need = popa * ((size_t)nseg + (size_t)K + 2) + 3 * v3a + 256;
+    if (ctx->adj_cap < need) {
+        if (ctx->adj) cudaFree(ctx->adj);
+        ctx->adj = NULL;
+        ctx->adj_cap = 0;
+        cudaError_t e = cudaMalloc(&ctx->adj, need);
+        if (e != cudaSuccess) { ctx->adj = NULL; return ctx_cuda(ctx, e, "cudaMalloc(adjoint workspace)"); }
+        ctx->adj_cap = need;
+    }
+    char *ckpt = (char *)ctx->adj;
+    char *seg = ckpt + popa * (size_t)nseg;
+    char *lam[2] = {seg + popa * (size_t)K, seg + popa * (size_t)(K + 1)};
+    double *dacc = (double *)(lam[1] + popa);
+    double *sF = (double *)((char *)dacc + v3a + 256);
+    double *sT = (double *)((char *)sF + v3a);
+    ACK(cudaMemsetAsync(dacc, 0, v3 + 4 * sizeof(double), ctx->stream), "memset gradients");
+    ACK(cudaMemsetAsync(lam[0], 0, pop, ctx->stream), "memset adjoint");
+    {
+        double *dJX = dacc, *dJF = dacc + 3 * (size_t)(n > 0 ? n : 1), *dJ = dJF + 3;
+        const double invT = 1.0 / nsteps;
+        // ---- forward rollout with checkpoints, accumulating J
+        for (int t = 0; t < nsteps; ++t) {
+            if (t % K == 0) ACK(cudaMemcpyAsync(ckpt + popa * (size_t)(t / K), ctx->f[ctx->cur], pop,
+                                                cudaMemcpyDeviceToDevice, ctx->stream), "checkpoint");
+            lbm_status st = ctx_step_once(ctx);
+            if (st != LBM_OK) { status = st; goto done; }
+            if (n > 0) {
+                k_sum_fx<<<1, 256, 0, ctx->stream>>>(ctx->dF, n, invT, dJ);
+                ACK(cudaGetLastError(), "drag sum");
+            }
+        }
+        if (n > 0) {
+            int stats[4];
+            ACK(cudaMemcpyAsync(stats, ctx->tile_stats, sizeof(stats), cudaMemcpyDeviceToHost, ctx->stream), "stats");
+            ACK(cudaStreamSynchronize(ctx->stream), "sync");
+            if (stats[0] > 0) {
+                ctx_error(ctx, "the adjoint needs every tile's candidates to fit tile_cap (raise it)");
+                status = LBM_ERR_UNSUPPORTED;
+                goto done;
+            }
+        }
+        tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap;
+        tl.stats = ctx->tile_stats; tl.blocks = ctx->tile_blocks;
+        scratch_parts = ctx_parts(ctx);
+        scratch_parts.F = sF;
+        scratch_parts.T = sT;
+        // ---- reverse sweep, segment by segment
+        int cur = 0;
+        for (int sidx = nseg - 1; sidx >= 0; --sidx) {
+            const int t0 = sidx * K, t1 = (t0 + K < nsteps) ? t0 + K : nsteps;
+            ACK(cudaMemcpyAsync(seg, ckpt + popa * (size_t)sidx, pop, cudaMemcpyDeviceToDevice, ctx->stream),
+                "restore checkpoint");
+            for (int t = t0 + 1; t < t1; ++t) {
+                ACK(launch_collide_stream(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - 1 - t0),
+                                          seg + popa * (size_t)(t - t0), ctx->g, ctx->ph, tl, scratch_parts,
+                                          ctx->flags, ctx->stream),
+                    "segment recompute");
+            }
+            for (int t = t1 - 1; t >= t0; --t) {
+                ACK(launch_adjoint(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - t0), lam[cur], lam[cur ^ 1],
+                                   ctx->g, ctx->ph, tl, ctx_parts(ctx), invT, dJX, dJF, ctx->stream),
+                    "adjoint kernel");
+                cur ^= 1;
+            }
+        }
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (J) ACK(cudaMemcpyAsync(J, dJ, sizeof(double), kind, ctx->stream), "copy J");
+        if (dJdF) ACK(cudaMemcpyAsync(dJdF, dJF, 3 * sizeof(double), kind, ctx->stream), "copy dJ/dF");
+        if (dJdX && n > 0) ACK(cudaMemcpyAsync(dJdX, dJX, (size_t)n * 3 * sizeof(double), kind, ctx->stream), "copy dJ/dX");
+        ACK(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+done:
+    cudaStreamSynchronize(ctx->stream);
+    if (status == LBM_OK) status = ctx_check_flags(ctx);
+    return status;
+}

@@ -224,6 +224,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
     free_dev(&ctx->tile_blocks);
     free_dev((void **)&ctx->diag);
+    free_dev(&ctx->adj);
     for (int i = 0; i < ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
     free(ctx->ev);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -540,6 +541,14 @@ extern "C" lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size)
                                       (const double *)(p + 2 * v), (const double *)(p + 3 * v), 0);
     if (st != LBM_OK) return st;
     ctx->steps = h.steps;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F) {
+    if (!ctx || !F) return LBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(F[a])) { ctx_error(ctx, "body force must be finite"); return LBM_ERR_ARG; }
+    for (int a = 0; a < 3; ++a) { ctx->p.body_force[a] = F[a]; ctx->ph.body_force[a] = F[a]; }
     return LBM_OK;
 }
 

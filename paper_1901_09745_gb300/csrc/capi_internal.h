@@ -34,6 +34,9 @@ struct lbm_ctx {
     double *diag;              // scratch for host-side diagnostics (macro, populations)
     size_t diag_cap;
 
+    void *adj;                 // adjoint workspace (checkpoints, segment states, adjoint
+    size_t adj_cap;            // fields, gradients), grown on demand, kept until destroy
+
     long long steps;
     long long launches;        // kernels this context has launched
     long long cs_launches;     // of which fused collide-stream launches

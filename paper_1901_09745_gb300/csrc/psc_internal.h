@@ -65,6 +65,11 @@ cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles 
                         long long ntiles, cudaStream_t s);
 // Bytes of one tile's packed block for the given candidate capacity.
 long long pack_block_bytes(int rec_double, int cap);
+// One reverse step of the collide-stream step (static particles): lam_out = S^T (dC/dp)^T
+// lam_in + drag terms; accumulates dJ/dX (n x 3) and dJ/dF (3).
+cudaError_t launch_adjoint(int storage, int lattice, const void *gt, const void *lam_in, void *lam_out,
+                           const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd, double invT,
+                           double *dJdX, double *dJdF, cudaStream_t s);
 // f(r) of Eq. 18 (Eq. 17 in 3D, Eq. 19 in 2D) for every particle.
 cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s);
 

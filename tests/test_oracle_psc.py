@@ -373,3 +373,24 @@ def test_periodic_translation_invariance(lattice):
     assert np.allclose(F1, F2, rtol=1e-11, atol=1e-17)
     assert np.allclose(T1, T2, rtol=1e-11, atol=1e-16)
     assert np.allclose(np.roll(f, shift=tuple(shift[::-1]), axis=(1, 2, 3)), f2, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_time_averaged_drag_from_the_momentum_budget(lattice):
+    """The drag functional behind the adjoint, J = (1/T) sum_t sum_p F_{p,x}(t) (Eq. 14),
+    against the momentum budget of a periodic box with static particles: summing the per-step
+    identity gives J = F_x sum_n (1 - B_n) - (M_x(T) - M_x(0)) / T, which reads only the
+    populations before and after and the cell weights."""
+    p, f, X, U, Om, r = _moving_setup(lattice, 0)
+    U = np.zeros_like(U); Om = np.zeros_like(Om)
+    e = O.lattice_tables(lattice)[0].astype(np.float64)
+    T = 7
+    J = O.drag(p, f, T, X, r, U, Om)
+    g = f.copy()
+    M0 = np.einsum("izyx,ia->a", g, e)
+    _, _, Bn = O.step(p, g, X, U, Om, r, want_Bn=True)
+    O.run(p, g, T - 1, X, U, Om, r)
+    M1 = np.einsum("izyx,ia->a", g, e)
+    expect = p.body_force[0] * (1.0 - Bn).sum() - (M1[0] - M0[0]) / T
+    assert J == pytest.approx(expect, rel=1e-10, abs=1e-15)
+    assert abs(J) > 1e-6
