@@ -32,15 +32,16 @@
 namespace psc {
 
 template <class L, typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict__ lam_out, Geom g,
-          PhysT<T> ph, Tiles tl, Parts pd, T invT, double *dJdX, double *dJdF) {
+          PhysT<T> ph, Tiles tl, Parts pd, T invT, double *dJdX, double *dFpart) {
     constexpr int Q = L::Q;
     constexpr int D = L::D;
     extern __shared__ __align__(16) unsigned char smem[];
     T *srec = reinterpret_cast<T *>(smem);                 // [cap][RW]
     T *part = srec + (size_t)tl.cap * RW;                  // [kWarps][cap][D] warp partials
     __shared__ T s_dF[kWarps][3];
+    __shared__ int s_wany[kWarps];
 
     const int tid = threadIdx.x + L::TX * (threadIdx.y + L::TY * threadIdx.z);
     const int lane = tid & 31, warp = tid >> 5;
@@ -55,30 +56,45 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
     const T *recs = reinterpret_cast<const T *>(tl.blocks) + tile * block_elems<T>(cap) + head_elems<T>();
     for (int w = tid; w < cnt * RW; w += kThreads) srec[w] = recs[w];
 
-    // ---- forward quantities of this step (pull, Eq. 5)
+    // ---- forward quantities of this step (pull, Eq. 5); tiles one cell clear of every face
+    // address their neighbours by a fixed offset (no wrap or wall tests)
+    const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
+                          (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+    const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
     T d[Q];
+    if (interior) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = active ? pull_one<L, T>(gt, g, x, y, z, cell, i, ph.sc) : (T)0;
+        for (int i = 0; i < Q; ++i) d[i] = gt[(long long)i * N + cell - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = active ? pull_one<L, T>(gt, g, x, y, z, cell, i, ph.sc) : (T)0;
+    }
     T drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         drho += d[i];
-        j[0] += L::ex(i) * d[i]; j[1] += L::ey(i) * d[i]; j[2] += L::ez(i) * d[i];
+        if (L::ex(i)) j[0] += L::ex(i) > 0 ? d[i] : -d[i];
+        if (L::ey(i)) j[1] += L::ey(i) > 0 ? d[i] : -d[i];
+        if (L::ez(i)) j[2] += L::ez(i) > 0 ? d[i] : -d[i];
     }
     const T rho = (T)1 + drho;
-    const T u[3] = {(j[0] + (T)0.5 * ph.F[0]) / rho, (j[1] + (T)0.5 * ph.F[1]) / rho, (j[2] + (T)0.5 * ph.F[2]) / rho};
+    const T irho = (T)1 / rho;
+    const T F[3] = {ph.F[0], ph.F[1], ph.F[2]};
+    const T u[3] = {(j[0] + (T)0.5 * F[0]) * irho, (j[1] + (T)0.5 * F[1]) * irho, (j[2] + (T)0.5 * F[2]) * irho};
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    const T uF = u[0] * ph.F[0] + u[1] * ph.F[1] + u[2] * ph.F[2];
-    __syncthreads();
+    const T uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
 
     // ---- the cell's total solid fraction and weight (Table 1, Eq. 9 at eps_n)
     const T cx = (T)threadIdx.x, cy = (T)threadIdx.y, cz = (T)threadIdx.z;
     T seps = 0;
-    for (int k = 0; k < cnt && active; ++k) {
-        const T *rk = srec + k * RW;
-        T dx, dy, dz;
-        cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
-        seps += shell_eps<T>(dx * dx + dy * dy + dz * dz, rk[R_R], rk[R_FR], ph.h);
+    if (cnt > 0) {
+        __syncthreads();
+        for (int k = 0; k < cnt && active; ++k) {
+            const T *rk = srec + k * RW;
+            T dx, dy, dz;
+            cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
+            seps += shell_eps<T>(dx * dx + dy * dy + dz * dz, rk[R_R], rk[R_FR], ph.h);
+        }
     }
     const T en = seps < (T)1 ? seps : (T)1;
     const T den = ((T)1 - en) + ph.tmh;
@@ -86,68 +102,97 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
     const T dBde = (seps > (T)0 && seps < (T)1) ? ph.tmh * ((T)1 + ph.tmh) / (den * den) : (T)0;
     const T omB = (T)1 - B;
 
-    // ---- adjoint of the collision at this cell
+    // ---- adjoint of the collision at this cell. Everything the transpose needs is a
+    // moment of w_i lambda_i (S0, S1 = sum w lambda e, M2 = sum w lambda e e^T) or one of the
+    // two products lambda.d, lambda.d_opp, because f^eq and the Guo term are quadratic in e.
     T lam[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) lam[i] = active ? lam_in[(long long)i * N + cell] : (T)0;
-    T Arho = 0, Au[3] = {0, 0, 0}, dCdB = 0, dFu[3] = {0, 0, 0};
+    T S0 = 0, S1[3] = {0, 0, 0}, Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0, Ld = 0, Ldo = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const int o = opp<L>(i);
-        const T w = (T)weight<L>(i);
-        const T e[3] = {(T)L::ex(i), (T)L::ey(i), (T)L::ez(i)};
-        const T eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
-        const T eF = e[0] * ph.F[0] + e[1] * ph.F[1] + e[2] * ph.F[2];
-        const T poly_i = (T)1 + (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu;   // feq_i / (rho w)
-        const T poly_o = (T)1 - (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu;   // feq_-i / (rho w)
-        const T dfeq_i = w * (drho + rho * (poly_i - (T)1));                    // feq_i - w
-        const T dfeq_o = w * (drho + rho * (poly_o - (T)1));
-        const T G = ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
-        const T li = lam[i];
-        // d C_i / d B: the solid term is B (f_-i - feq_-i - f_i) + B (rho - 1) w_i in deviations
-        dCdB += li * (ph.omega * (d[i] - dfeq_i) + (d[o] - dfeq_o - d[i]) + drho * w - G);
-        // through rho: feq/rho, and the solid term B rho w_i
-        Arho += li * (omB * ph.omega * w * poly_i - B * w * poly_o + B * w);
-        // through u: grad_u feq_i = rho w (3 e + 9 (e.u) e - 3 u), grad_u feq_-i likewise with -e,
-        // grad_u G_i = guo w (-3 F + 9 (e.F) e)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const T gi = rho * w * ((T)3 * e[a] + (T)9 * eu * e[a] - (T)3 * u[a]);
-            const T go = rho * w * (-(T)3 * e[a] + (T)9 * eu * e[a] - (T)3 * u[a]);
-            const T gG = ph.guo * w * (-(T)3 * ph.F[a] + (T)9 * eF * e[a]);
-            Au[a] += li * (omB * ph.omega * gi - B * go + omB * gG);
-            // explicit dependence of G_i on F at fixed u
-            dFu[a] += li * omB * ph.guo * w * ((T)3 * (e[a] - u[a]) + (T)9 * eu * e[a]);
-        }
+        const T wl = (T)weight<L>(i) * lam[i];
+        const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+        S0 += wl;
+        if (ex) S1[0] += ex > 0 ? wl : -wl;
+        if (ey) S1[1] += ey > 0 ? wl : -wl;
+        if (ez) S1[2] += ez > 0 ? wl : -wl;
+        if (ex) Mxx += wl;
+        if (ey) Myy += wl;
+        if (ez) Mzz += wl;
+        if (ex && ey) Mxy += (ex == ey) ? wl : -wl;
+        if (ex && ez) Mxz += (ex == ez) ? wl : -wl;
+        if (ey && ez) Myz += (ey == ez) ? wl : -wl;
+        Ld += lam[i] * d[i];
+        Ldo += lam[i] * d[opp<L>(i)];
     }
+    const T M2u[3] = {Mxx * u[0] + Mxy * u[1] + Mxz * u[2], Mxy * u[0] + Myy * u[1] + Myz * u[2],
+                      Mxz * u[0] + Myz * u[1] + Mzz * u[2]};
+    const T M2F[3] = {Mxx * F[0] + Mxy * F[1] + Mxz * F[2], Mxy * F[0] + Myy * F[1] + Myz * F[2],
+                      Mxz * F[0] + Myz * F[1] + Mzz * F[2]};
+    const T uS1 = u[0] * S1[0] + u[1] * S1[1] + u[2] * S1[2];
+    const T FS1 = F[0] * S1[0] + F[1] * S1[1] + F[2] * S1[2];
+    const T uMu = u[0] * M2u[0] + u[1] * M2u[1] + u[2] * M2u[2];
+    const T FMu = F[0] * M2u[0] + F[1] * M2u[1] + F[2] * M2u[2];
+    const T s0q = S0 * ((T)1 - (T)1.5 * uu);
+    // sum_i lambda_i feq_i / rho and sum_i lambda_i feq_-i / rho
+    const T Pe = s0q + (T)3 * uS1 + (T)4.5 * uMu;
+    const T Po = s0q - (T)3 * uS1 + (T)4.5 * uMu;
+    const T oo = omB * ph.omega;
+    // through rho at fixed u: (1-B) omega feq_i/rho - B feq_-i/rho + B w_i
+    const T Arho = oo * Pe - B * Po + B * S0;
+    // through u at fixed rho: grad_u feq_i = rho w (3 e + 9 (e.u) e - 3 u), feq_-i with -e,
+    // grad_u G_i = guo w (-3 F + 9 (e.F) e); and G_i's explicit F at fixed u
+    T Au[3], dFu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const T gi = (T)3 * S1[a] + (T)9 * M2u[a] - (T)3 * u[a] * S0;
+        const T go = -(T)3 * S1[a] + (T)9 * M2u[a] - (T)3 * u[a] * S0;
+        Au[a] = rho * (oo * gi - B * go) + omB * ph.guo * ((T)9 * M2F[a] - (T)3 * F[a] * S0);
+        dFu[a] = omB * ph.guo * gi;
+    }
+    // dC/dB . lambda: omega (d - dfeq) + (d_-i - dfeq_-i - d_i) + (rho - 1) w_i - G_i
+    const T Ldfe = drho * S0 + rho * (Pe - S0);
+    const T Ldfo = drho * S0 + rho * (Po - S0);
+    const T LG = ph.guo * ((T)3 * FS1 - (T)3 * uF * S0 + (T)9 * FMu);
+    const T dCdB = ph.omega * (Ld - Ldfe) + (Ldo - Ldfo - Ld) + drho * S0 - LG;
+
     // a_k = lambda_k (1 - (1-B) omega - B) + B lambda_-k + Arho + Au.(e_k - u)/rho + (B/T) e_kx,
     // pushed back along the link it was pulled from (S^T)
-    const T Auu = Au[0] * u[0] + Au[1] * u[1] + Au[2] * u[2];
-    const T diag = (T)1 - omB * ph.omega - B;
+    const T diag = (T)1 - oo - B;
+    const T c0 = Arho - (Au[0] * u[0] + Au[1] * u[1] + Au[2] * u[2]) * irho;
+    const T Av[3] = {Au[0] * irho + invT * B, Au[1] * irho, Au[2] * irho};
+    if (active) {
 #pragma unroll
-    for (int k = 0; k < Q; ++k) {
-        const T ek[3] = {(T)L::ex(k), (T)L::ey(k), (T)L::ez(k)};
-        const T a = lam[k] * diag + B * lam[opp<L>(k)] + Arho +
-                    (Au[0] * ek[0] + Au[1] * ek[1] + Au[2] * ek[2] - Auu) / rho + invT * B * ek[0];
-        if (!active) continue;
-        int s[3] = {x - L::ex(k), y - L::ey(k), z - L::ez(k)};
-        bool bounce = false;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            if (s[q] < 0 || s[q] >= g.n[q]) {
-                if (g.periodic[q]) s[q] += (s[q] < 0) ? g.n[q] : -g.n[q];
-                else bounce = true;
+        for (int k = 0; k < Q; ++k) {
+            T a = lam[k] * diag + B * lam[opp<L>(k)] + c0;
+            if (L::ex(k)) a += L::ex(k) > 0 ? Av[0] : -Av[0];
+            if (L::ey(k)) a += L::ey(k) > 0 ? Av[1] : -Av[1];
+            if (L::ez(k)) a += L::ez(k) > 0 ? Av[2] : -Av[2];
+            if (interior) {
+                lam_out[(long long)k * N + cell - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)] = a;
+                continue;
             }
+            int s[3] = {x - L::ex(k), y - L::ey(k), z - L::ez(k)};
+            bool bounce = false;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                if (s[q] < 0 || s[q] >= g.n[q]) {
+                    if (g.periodic[q]) s[q] += (s[q] < 0) ? g.n[q] : -g.n[q];
+                    else bounce = true;
+                }
+            }
+            if (bounce) lam_out[(long long)opp<L>(k) * N + cell] = a;
+            else lam_out[(long long)k * N + (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2])] = a;
         }
-        if (bounce) lam_out[(long long)opp<L>(k) * N + cell] = a;
-        else lam_out[(long long)k * N + (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2])] = a;
     }
 
-    // ---- body force: through u (du/dF = I/(2 rho)), explicit in G, and J_t's -B F_x/2
+    // ---- body force: through u (du/dF = I/(2 rho)), explicit in G, and J_t's -B F_x/2;
+    // one partial per block, accumulated over the steps without atomics
     T vF[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) vF[a] = active ? Au[a] / ((T)2 * rho) + dFu[a] : (T)0;
-    vF[0] += active ? -invT * B * (T)0.5 : (T)0;
+    for (int a = 0; a < 3; ++a) vF[a] = active ? (T)0.5 * Au[a] * irho + dFu[a] : (T)0;
+    vF[0] -= active ? (T)0.5 * invT * B : (T)0;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -155,45 +200,71 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
     if (lane == 0) for (int a = 0; a < 3; ++a) s_dF[warp][a] = vF[a];
 
     // ---- positions: Lambda_n dB/deps_n deps_s/dX_s on unclamped shell cells
-    const T Lam = dCdB + invT * (j[0] - (T)0.5 * ph.F[0]);
+    const T Lam = dCdB + invT * (j[0] - (T)0.5 * F[0]);
     const T coef = (active && dBde != (T)0) ? Lam * dBde : (T)0;
-    const bool any = __syncthreads_or(coef != (T)0);
+    const bool wany = __any_sync(kFull, coef != (T)0);
+    if (lane == 0) s_wany[warp] = wany;
+    __syncthreads();
     if (tid < 3) {
         T sum = 0;
         for (int w = 0; w < kWarps; ++w) sum += s_dF[w][tid];
-        if (sum != (T)0) atomicAdd(&dJdF[tid], (double)sum);
+        const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        dFpart[3 * blk + tid] += (double)sum;
     }
-    if (!any) return;
-    for (int k = 0; k < cnt; ++k) {
-        const T *rk = srec + k * RW;
-        T v[3] = {0, 0, 0};
-        if (coef != (T)0) {
-            T dx, dy, dz;
-            cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
-            const T d2 = dx * dx + dy * dy + dz * dz;
-            const T r = rk[R_R];
-            if (d2 < (r + ph.h) * (r + ph.h)) {
-                const T dist = sqrt_t(d2);
-                const T e = rk[R_FR] - (dist - r);
-                if (dist > r - ph.h && e > (T)0 && e < (T)1 && dist > (T)0) {
-                    const T c = coef / dist;
-                    v[0] = c * dx; v[1] = c * dy; v[2] = c * dz;
+    if (cnt == 0) return;
+    if (wany) {
+        for (int k = 0; k < cnt; ++k) {
+            const T *rk = srec + k * RW;
+            T v[3] = {0, 0, 0};
+            bool hit = false;
+            if (coef != (T)0) {
+                T dx, dy, dz;
+                cand_arm<L, T>(g, cx, cy, cz, rk[R_PX], rk[R_PY], rk[R_PZ], dx, dy, dz);
+                const T d2 = dx * dx + dy * dy + dz * dz;
+                const T r = rk[R_R];
+                if (d2 < (r + ph.h) * (r + ph.h)) {
+                    const T dist = sqrt_t(d2);
+                    const T e = rk[R_FR] - (dist - r);
+                    if (dist > r - ph.h && e > (T)0 && e < (T)1 && dist > (T)0) {
+                        const T c = coef / dist;
+                        v[0] = c * dx; v[1] = c * dy; v[2] = c * dz;
+                        hit = true;
+                    }
                 }
             }
+            if (__any_sync(kFull, hit)) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                    for (int a = 0; a < D; ++a) v[a] += __shfl_xor_sync(kFull, v[a], off);
+            }
+            if (lane == 0) for (int a = 0; a < D; ++a) part[((size_t)warp * cap + k) * D + a] = v[a];
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) v[a] += __shfl_xor_sync(kFull, v[a], off);
-        if (lane == 0) for (int a = 0; a < D; ++a) part[((size_t)warp * cap + k) * D + a] = v[a];
     }
     __syncthreads();
     for (int idx = tid; idx < cnt * D; idx += kThreads) {
         const int k = idx / D, a = idx - k * D;
         T sum = 0;
-        for (int w = 0; w < kWarps; ++w) sum += part[((size_t)w * cap + k) * D + a];
+        for (int w = 0; w < kWarps; ++w)
+            if (s_wany[w]) sum += part[((size_t)w * cap + k) * D + a];
         if (sum != (T)0) atomicAdd(&dJdX[3 * bits_id(srec[k * RW + R_ID]) + a], (double)sum);
     }
+}
+
+// dJ/dF = sum of the per-block partials
+__global__ void k_sum_parts(const double *part, long long nblk, double *out) {
+    __shared__ double s[3][256];
+    double a[3] = {0.0, 0.0, 0.0};
+    for (long long b = threadIdx.x; b < nblk; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) a[c] += part[3 * b + c];
+    for (int c = 0; c < 3; ++c) s[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) s[c][threadIdx.x] += s[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) out[threadIdx.x] = s[threadIdx.x][0];
 }
 
 // J += (1/T) sum_p F_{p,x} of the step just taken
@@ -212,7 +283,7 @@ __global__ void k_sum_fx(const double *F, int n, double invT, double *J) {
 
 template <class L, typename T>
 cudaError_t launch_adjoint_t(const void *gt, const void *lam_in, void *lam_out, const Geom &g, const Phys &ph,
-                             const Tiles &tl, const Parts &pd, double invT, double *dJdX, double *dJdF,
+                             const Tiles &tl, const Parts &pd, double invT, double *dJdX, double *dFpart,
                              cudaStream_t s) {
     const size_t smem = (size_t)tl.cap * RW * sizeof(T) + (size_t)kWarps * tl.cap * L::D * sizeof(T);
     auto kern = k_adjoint<L, T>;
@@ -223,19 +294,19 @@ cudaError_t launch_adjoint_t(const void *gt, const void *lam_in, void *lam_out, 
     dim3 grid(g.nt[0], g.nt[1], g.nt[2]);
     dim3 block(L::TX, L::TY, L::TZ);
     kern<<<grid, block, smem, s>>>((const T *)gt, (const T *)lam_in, (T *)lam_out, g, make_phys<T>(ph), tl, pd,
-                                   (T)invT, dJdX, dJdF);
+                                   (T)invT, dJdX, dFpart);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(int storage, int lattice, const void *gt, const void *lam_in, void *lam_out,
                            const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd, double invT,
-                           double *dJdX, double *dJdF, cudaStream_t s) {
+                           double *dJdX, double *dFpart, cudaStream_t s) {
     if (storage == ST_F64) {
-        return lattice == 9 ? launch_adjoint_t<D2Q9, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s)
-                            : launch_adjoint_t<D3Q19, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s);
+        return lattice == 9 ? launch_adjoint_t<D2Q9, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dFpart, s)
+                            : launch_adjoint_t<D3Q19, double>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dFpart, s);
     }
-    return lattice == 9 ? launch_adjoint_t<D2Q9, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s)
-                        : launch_adjoint_t<D3Q19, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dJdF, s);
+    return lattice == 9 ? launch_adjoint_t<D2Q9, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dFpart, s)
+                        : launch_adjoint_t<D3Q19, float>(gt, lam_in, lam_out, g, ph, tl, pd, invT, dJdX, dFpart, s);
 }
 
 }  // namespace psc
@@ -282,7 +353,9 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
     // [K], two adjoint fields, gradients + J, scratch forces and torques
     const size_t v3a = (v3 + 255) & ~(size_t)255;
     const size_t popa = (pop + 255) & ~(size_t)255;      // buffer stride, 256-byte aligned
-    const size_t need = popa * ((size_t)nseg + (size_t)K + 2) + 3 * v3a + 256;
+    const long long nblk = (long long)ctx->g.nt[0] * ctx->g.nt[1] * ctx->g.nt[2];
+    const size_t fpa = ((size_t)nblk * 3 * sizeof(double) + 255) & ~(size_t)255;
+    const size_t need = popa * ((size_t)nseg + (size_t)K + 2) + 3 * v3a + 256 + fpa;
     if (ctx->adj_cap < need) {
         if (ctx->adj) cudaFree(ctx->adj);
         ctx->adj = NULL;
@@ -297,7 +370,9 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
     double *dacc = (double *)(lam[1] + popa);
     double *sF = (double *)((char *)dacc + v3a + 256);
     double *sT = (double *)((char *)sF + v3a);
+    double *dFpart = (double *)((char *)sT + v3a);       // [blocks][3] partials of dJ/dF
     ACK(cudaMemsetAsync(dacc, 0, v3 + 4 * sizeof(double), ctx->stream), "memset gradients");
+    ACK(cudaMemsetAsync(dFpart, 0, fpa, ctx->stream), "memset gradient partials");
     ACK(cudaMemsetAsync(lam[0], 0, pop, ctx->stream), "memset adjoint");
     {
         double *dJX = dacc, *dJF = dacc + 3 * (size_t)(n > 0 ? n : 1), *dJ = dJF + 3;
@@ -324,7 +399,7 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
             }
         }
         tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap;
-        tl.stats = ctx->tile_stats; tl.blocks = ctx->tile_blocks;
+        tl.stats = ctx->tile_stats; tl.blocks = ctx->tile_blocks; tl.order = ctx->tile_order;
         scratch_parts = ctx_parts(ctx);
         scratch_parts.F = sF;
         scratch_parts.T = sT;
@@ -342,11 +417,13 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
             }
             for (int t = t1 - 1; t >= t0; --t) {
                 ACK(launch_adjoint(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - t0), lam[cur], lam[cur ^ 1],
-                                   ctx->g, ctx->ph, tl, ctx_parts(ctx), invT, dJX, dJF, ctx->stream),
+                                   ctx->g, ctx->ph, tl, ctx_parts(ctx), invT, dJX, dFpart, ctx->stream),
                     "adjoint kernel");
                 cur ^= 1;
             }
         }
+        k_sum_parts<<<1, 256, 0, ctx->stream>>>(dFpart, nblk, dJF);
+        ACK(cudaGetLastError(), "dJ/dF sum");
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
         if (J) ACK(cudaMemcpyAsync(J, dJ, sizeof(double), kind, ctx->stream), "copy J");
         if (dJdF) ACK(cudaMemcpyAsync(dJdF, dJF, 3 * sizeof(double), kind, ctx->stream), "copy dJ/dF");

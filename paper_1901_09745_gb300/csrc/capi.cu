@@ -150,6 +150,9 @@ static lbm_status validate(const lbm_params *p) {
         ctx_error(NULL, "ny or nz too large for the tile grid (at most 65535 tiles per axis)");
         return LBM_ERR_ARG;
     }
+    const int tx = (p->lattice == LBM_D2Q9) ? D2Q9::TX : D3Q19::TX;
+    const double ntiles = (double)((p->nx + tx - 1) / tx) * ((p->ny + ty - 1) / ty) * ((p->nz + tz - 1) / tz);
+    if (ntiles > 2147483647.0) { ctx_error(NULL, "too many lattice tiles (at most 2^31 - 1)"); return LBM_ERR_ARG; }
     return LBM_OK;
 }
 
@@ -222,6 +225,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     free_dev((void **)&ctx->flags);
     free_particles(ctx);
     free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
+    free_dev((void **)&ctx->tile_order);
     free_dev(&ctx->tile_blocks);
     free_dev((void **)&ctx->diag);
     free_dev(&ctx->adj);
@@ -242,6 +246,7 @@ Parts ctx_parts(lbm_ctx *ctx) {
 static Tiles ctx_tiles(lbm_ctx *ctx) {
     Tiles tl;
     tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap; tl.stats = ctx->tile_stats;
+    tl.order = ctx->tile_order;
     tl.blocks = ctx->tile_blocks;
     return tl;
 }
@@ -297,10 +302,11 @@ static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
     if (ctx->tile_count) return LBM_OK;
     CK(cudaMalloc(&ctx->tile_count, (size_t)ctx->ntiles * sizeof(int)), "cudaMalloc(tile counts)");
     CK(cudaMalloc(&ctx->tile_list, (size_t)ctx->ntiles * ctx->p.tile_cap * sizeof(int)), "cudaMalloc(tile lists)");
-    CK(cudaMalloc(&ctx->tile_stats, 4 * sizeof(int)), "cudaMalloc(tile stats)");
+    CK(cudaMalloc(&ctx->tile_stats, kTileStats * sizeof(int)), "cudaMalloc(tile stats)");
+    CK(cudaMalloc(&ctx->tile_order, (size_t)ctx->ntiles * 3 * sizeof(uint2)), "cudaMalloc(tile order)");
     CK(cudaMalloc(&ctx->tile_blocks, (size_t)ctx->ntiles * pack_block_bytes(ctx->p.storage == LBM_F64, ctx->p.tile_cap)),
        "cudaMalloc(tile candidate blocks)");
-    CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
+    CK(cudaMemsetAsync(ctx->tile_stats, 0, kTileStats * sizeof(int), ctx->stream), "memset tile stats");
     return LBM_OK;
 }
 
@@ -356,7 +362,7 @@ lbm_status ctx_bin(lbm_ctx *ctx) {
     if (ctx->np <= 0) return LBM_OK;
     Tiles tl = ctx_tiles(ctx);
     CK(cudaMemsetAsync(ctx->tile_count, 0, (size_t)ctx->ntiles * sizeof(int), ctx->stream), "memset tile counts");
-    CK(cudaMemsetAsync(ctx->tile_stats, 0, 4 * sizeof(int), ctx->stream), "memset tile stats");
+    CK(cudaMemsetAsync(ctx->tile_stats, 0, kTileStats * sizeof(int), ctx->stream), "memset tile stats");
     CK(launch_bin(ctx->dim, ctx->g, ctx->ph, tl, ctx_parts(ctx), ctx->stream), "bin kernel");
     CK(launch_pack(ctx->q, ctx->p.storage == LBM_F64, ctx->g, tl, ctx_parts(ctx), ctx->ntiles, ctx->stream), "pack kernel");
     ctx->launches += 2;
@@ -393,7 +399,7 @@ lbm_status ctx_step_once(lbm_ctx *ctx) {
                              ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream),
        "collide-stream kernel");
     if (ev) CK(cudaEventRecord(ev[1], ctx->stream), "cudaEventRecord");
-    ctx->launches += 1;
+    ctx->launches += (ctx->np > 0) ? 3 : 1;   // fluid tiles, particle tiles, overflow tiles
     ctx->cs_launches += 1;
     ctx->cur ^= 1;
     ctx->steps += 1;

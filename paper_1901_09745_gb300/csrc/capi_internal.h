@@ -28,6 +28,7 @@ struct lbm_ctx {
     // tile candidate lists
     long long ntiles;
     int *tile_count, *tile_list, *tile_stats;
+    uint2 *tile_order;
     void *tile_blocks;         // packed candidate records per tile
     int bins_valid;
 

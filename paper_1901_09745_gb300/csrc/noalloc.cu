@@ -87,14 +87,16 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
              : (p->storage == LBM_BF16_DEV && p->dev_scale > 0.0) ? p->dev_scale : 1.0;
     ph.psc = p->psc;
 
-    // carve the fixed array: counts | stats | flags | lists | f(r) | packed tile blocks
+    // carve the fixed array: counts | stats | flags | lists | tile order | f(r) | packed tile blocks
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     const int rec_double = (p->storage == LBM_F64);
     size_t off = 0;
     const size_t o_count = off; off += (size_t)ntiles * sizeof(int);
-    const size_t o_stats = off; off += 4 * sizeof(int);
+    const size_t o_stats = off; off += kTileStats * sizeof(int);
     const size_t o_flags = off; off += 4 * sizeof(int);
     const size_t o_list = off; off += (size_t)ntiles * kNoAllocCap * sizeof(int);
+    off = align_up(off, 16);
+    const size_t o_order = off; off += (size_t)ntiles * 3 * sizeof(uint2);
     off = align_up(off, 16);
     const size_t o_fr = off; off += (size_t)n * sizeof(double);
     off = align_up(off, 256);
@@ -130,6 +132,7 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     tl.list = (int *)(base + o_list);
     tl.cap = kNoAllocCap;
     tl.blocks = base + o_blocks;
+    tl.order = (uint2 *)(base + o_order);
     int *flags = (int *)(base + o_flags);
     Parts pd;
     pd.n = n; pd.X = X; pd.U = U; pd.Om = Omega; pd.R = radius; pd.Fr = (double *)(base + o_fr);

@@ -33,9 +33,16 @@ struct Tiles {
     int *count;
     int *list;
     int cap;
-    int *stats;          // [0] tiles that overflowed cap, [1] largest count
+    int *stats;          // [0] tiles that overflowed cap, [1] largest count, [2] length of
+                         // the overflow list, [4] tiles with candidates, [5] tiles without,
+                         // [6] [7] work counters of the persistent particle-tile kernel
+                         // (zero between launches)
     void *blocks;        // per-tile packed candidate records (compute type), see psc_kernels.cuh
+    uint2 *order;        // [3 * ntiles] {tile id, ty | tz << 16}: tiles with candidates, then
+                         // (from ntiles on) tiles without, then (from 2 ntiles on) tiles with
+                         // more than cap; each list in rising id order within a block of 8
 };
+constexpr int kTileStats = 8;
 
 // Particle state on the device (FP64), and the force/torque accumulators (Eq. 14).
 struct Parts {
@@ -66,10 +73,11 @@ cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles 
 // Bytes of one tile's packed block for the given candidate capacity.
 long long pack_block_bytes(int rec_double, int cap);
 // One reverse step of the collide-stream step (static particles): lam_out = S^T (dC/dp)^T
-// lam_in + drag terms; accumulates dJ/dX (n x 3) and dJ/dF (3).
+// lam_in + drag terms; accumulates dJ/dX (n x 3, atomics) and per-block partials of dJ/dF
+// (blocks x 3, each block adds to its own slot).
 cudaError_t launch_adjoint(int storage, int lattice, const void *gt, const void *lam_in, void *lam_out,
                            const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd, double invT,
-                           double *dJdX, double *dJdF, cudaStream_t s);
+                           double *dJdX, double *dFpart, cudaStream_t s);
 // f(r) of Eq. 18 (Eq. 17 in 3D, Eq. 19 in 2D) for every particle.
 cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s);
 
