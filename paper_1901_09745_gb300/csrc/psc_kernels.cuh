@@ -36,6 +36,7 @@ namespace psc {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPairCap = 32;     // candidates a tile may have to take the two-cells-per-thread path
 
 template <typename T> struct PhysT {
     T omega;        // 1/tau
@@ -239,8 +240,9 @@ __device__ __forceinline__ void write_record(T *rec, const Geom &g, const Parts 
 // Packing kernel: one warp per tile sorts the tile's candidate list and writes its block.
 // Each block of 8 tiles then appends its tiles to the list of tiles with candidates or to
 // the list of tiles without, and tiles with more candidates than `cap` also to the overflow
-// list (one atomic per list and block), so the collide-stream kernels run over compact lists
-// and launch no block for a tile that is not theirs.
+// list (tiles with more than min(cap, kPairCap) candidates; one atomic per list and block), so
+// the collide-stream kernels run over compact lists and launch no block for a tile that is
+// not theirs.
 template <class L, typename T>
 __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
     __shared__ int s_id[kWarps][64];
@@ -274,7 +276,8 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
         int np = 0, nf = 0;
         for (int w = 0; w < kWarps; ++w) { np += (s_cnt[w] > 0); nf += (s_cnt[w] == 0); }
         int no = 0;
-        for (int w = 0; w < kWarps; ++w) no += (s_cnt[w] > tl.cap);
+        const int lim = min(tl.cap, kPairCap);
+        for (int w = 0; w < kWarps; ++w) no += (s_cnt[w] > lim);
         int bp = np ? atomicAdd(&tl.stats[4], np) : 0;
         int bf = nf ? atomicAdd(&tl.stats[5], nf) : 0;
         int bo = no ? atomicAdd(&tl.stats[2], no) : 0;
@@ -285,7 +288,7 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
             const uint2 ent = make_uint2(t, (txy % (unsigned)g.nt[1]) | ((txy / (unsigned)g.nt[1]) << 16));
             if (s_cnt[w] > 0) tl.order[bp++] = ent;
             else tl.order[ntiles + bf++] = ent;
-            if (s_cnt[w] > tl.cap) tl.order[2 * ntiles + bo++] = ent;
+            if (s_cnt[w] > lim) tl.order[2 * ntiles + bo++] = ent;
         }
     }
 }
@@ -331,9 +334,9 @@ __device__ __forceinline__ T cand_eps(const T *rec, const Geom &g, T cx, T cy, T
 }
 
 // Plain-fluid tiles (no candidate particle): BGK + Guo collision and pull streaming only
-// (Eq. 1-6). A persistent grid (a few blocks per SM) walks the list of tiles without
-// candidates (all tiles when there are no particles), so no block is spent on a tile that is
-// not its own. No shared memory and no barrier: each warp's loads overlap freely with other
+// (Eq. 1-6). With particles a persistent grid (a few blocks per SM) walks the list of tiles
+// without candidates, so no block is spent on a tile that is not its own; without particles
+// every tile gets its own block. No shared memory and no barrier: each warp's loads overlap freely with other
 // warps' arithmetic, and the small register footprint keeps six blocks per SM resident.
 template <class L, typename S, bool HASF>
 __global__ void __launch_bounds__(kThreads, (L::Q == 9) ? 6 : 4)
@@ -342,22 +345,22 @@ k_fluid(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename 
     using T = typename Store<S>::T;
     constexpr int Q = L::Q;
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    const int nf = (np > 0) ? tl.stats[5] : (int)ntiles;
+    // with particles: a persistent grid over the list of tiles without candidates; without:
+    // one block per tile of the (nt0, nt1, nt2) grid
+    const int nf = (np > 0) ? tl.stats[5] : 1;
     const uint2 *list = (np > 0) ? tl.order + ntiles : nullptr;
     const long long N = g.ncell;
-    for (int it = blockIdx.x; it < nf; it += gridDim.x) {
-        unsigned tile, ty, tz;
+    for (int it = (np > 0) ? (int)blockIdx.x : 0; it < nf; it += gridDim.x) {
+        int x0, y0, z0;
         if (list) {
             const uint2 ent = list[it];
-            tile = ent.x; ty = ent.y & 0xffffu; tz = ent.y >> 16;
+            const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
+            x0 = (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
+            y0 = (int)ty * L::TY;
+            z0 = (int)tz * L::TZ;
         } else {
-            tile = (unsigned)it;
-            const unsigned txy = tile / (unsigned)g.nt[0];
-            ty = txy % (unsigned)g.nt[1]; tz = txy / (unsigned)g.nt[1];
+            x0 = blockIdx.x * L::TX; y0 = blockIdx.y * L::TY; z0 = blockIdx.z * L::TZ;
         }
-        const int x0 = (int)(tile - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
-        const int y0 = (int)ty * L::TY;
-        const int z0 = (int)tz * L::TZ;
         const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
         if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) continue;
         const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
@@ -449,9 +452,6 @@ __device__ __forceinline__ bool row_hits(const Geom &g, T px, T py, T pz, T R, T
     const T hw = dist_t(rem);
     return (px - hw <= xmax + (T)1) && (px + hw >= (T)-1);
 }
-
-// Candidates per row whose brackets are kept for the force step (further ones are redone).
-template <class L> constexpr int psc_nslot() { return (L::D == 2) ? 4 : 2; }
 
 template <class L, typename T> constexpr int psc_min_blocks() {
     return sizeof(T) == 8 ? 1 : (L::Q == 9 ? 4 : 3);
@@ -779,371 +779,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
     }
 }
 
-// Tile totals of the per-warp partial forces in a fixed warp order, one FP64 atomic per
-// particle and component (Eq. 14: the force on the particle is minus the exchange sum).
-// The particle indices come from the tile's records in global memory: by the time of the
-// flush the shared copy may already hold the next tile's records.
-template <class L, typename T>
-__device__ __forceinline__ void psc_flush(const int cnt, const T *recs, const T *part,
-                                          const unsigned long long *mask, const int cap, const Parts &pd,
-                                          const int tid) {
-    constexpr int NC = (L::D == 2) ? 3 : 6;
-    for (int idx = tid; idx < cnt * NC; idx += kThreads) {
-        const int k = idx / NC, q = idx - k * NC;
-        T sum = 0;
-        bool any = false;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            if ((mask[w] >> k) & 1ull) { sum += part[((size_t)w * cap + k) * NC + q]; any = true; }
-        }
-        if (any && sum != (T)0) {
-            const int pid = bits_id(recs[k * RW + R_ID]);
-            double *dst;
-            if (L::D == 2) dst = (q < 2) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + 2];
-            else dst = (q < 3) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + q - 3];
-            atomicAdd(dst, -(double)sum);
-        }
-    }
-}
-
-// One tile whose candidates fit the block (count <= cap): a single pass over each row's
-// candidates. Per relevant candidate it forms eps_s (Table 1), the u_s moments of the
-// collision, and the candidate's momentum-exchange "bracket" per cell,
-//     b_s = eps_s (rho u_s + F/2 - j)        (modified scheme; (rho u_s + F/2 - j) original),
-// with its torque arm. Once sum eps, B_n and the normalisation c_B (Eq. 9, 13) are known,
-// the force of Eq. 14 (Eq. 11) on candidate s is -sum over cells of c_B b_s (B_n b_s), so the
-// candidates are not evaluated a second time. The first NSLOT candidates of a row keep their
-// brackets in shared memory (one word per lane, conflict-free); further ones (rare) are
-// re-evaluated in the force step. The block meets at one barrier per tile: partial forces are
-// double-buffered and the previous tile's are added up after that barrier.
-template <class L, typename S, int PSC>
-__device__ __forceinline__ void psc_tile_fast(const uint2 ent, const int cnt, const S *__restrict__ fin,
-                                              S *__restrict__ fout, const Geom &g,
-                                              const PhysT<typename Store<S>::T> &ph, const Tiles &tl,
-                                              const Parts &pd, int *flags, typename Store<S>::T *srec,
-                                              typename Store<S>::T *part, unsigned long long *s_mask,
-                                              const int prev_cnt, const typename Store<S>::T *prev_recs,
-                                              const typename Store<S>::T *prev_part,
-                                              const unsigned long long *prev_mask,
-                                              typename Store<S>::T *sbr) {
-    using T = typename Store<S>::T;
-    constexpr int Q = L::Q;
-    constexpr int NC = (L::D == 2) ? 3 : 6;
-    constexpr int NSLOT = psc_nslot<L>();
-    const int cap = tl.cap;
-
-    const unsigned tile = ent.x, ty = ent.y & 0xffffu, tz = ent.y >> 16;
-    const int x0 = (int)(tile - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
-    const int y0 = (int)ty * L::TY;
-    const int z0 = (int)tz * L::TZ;
-    const int tid = threadIdx.x + L::TX * (threadIdx.y + L::TY * threadIdx.z);
-    const int lane = tid & 31, warp = tid >> 5;
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    const bool active = x < g.n[0] && y < g.n[1] && z < g.n[2];
-    const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-    const long long N = g.ncell;
-    const T *recs = reinterpret_cast<const T *>(tl.blocks) + (size_t)tile * block_elems<T>(cap) + head_elems<T>();
-
-    // ---- records: this thread's share, loaded before the pull, stored to shared memory after
-    constexpr int kRecWords = (64 * RW + kThreads - 1) / kThreads;
-    T rw[kRecWords];
-    const int nwords = cnt * RW;
-#pragma unroll
-    for (int j = 0; j < kRecWords; ++j) {
-        const int w = tid + j * kThreads;
-        rw[j] = (w < nwords) ? recs[w] : (T)0;
-    }
-
-    // ---- pull and moments (Eq. 1, 5, 6)
-    const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
-                          (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
-    T df[Q];
-    pull_q<L, S>(fin, g, x, y, z, cell, interior, active, ph.sc, df);
-    T drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        drho += df[i];
-        if (L::ex(i)) jx += L::ex(i) * df[i];
-        if (L::ey(i)) jy += L::ey(i) * df[i];
-        if (L::ez(i)) jz += L::ez(i) * df[i];
-    }
-    const T rho = (T)1 + drho;
-    const T irho = (T)1 / rho;
-    const T ux = (jx + (T)0.5 * ph.F[0]) * irho;
-    const T uy = (jy + (T)0.5 * ph.F[1]) * irho;
-    const T uz = (jz + (T)0.5 * ph.F[2]) * irho;
-    if (active && !(rho > (T)0)) atomicOr(flags, 1);
-    // p = F/2 - j: the fluid part of the per-cell momentum exchange (Eq. 14)
-    const T px = (T)0.5 * ph.F[0] - jx, py = (T)0.5 * ph.F[1] - jy, pz = (T)0.5 * ph.F[2] - jz;
-
-#pragma unroll
-    for (int j = 0; j < kRecWords; ++j) {
-        const int w = tid + j * kThreads;
-        if (w < nwords) srec[w] = rw[j];
-    }
-    // the block's one barrier per tile: records staged, and every warp is done with the
-    // previous tile, whose partial forces can now be added up
-    __syncthreads();
-    psc_flush<L, T>(prev_cnt, prev_recs, prev_part, prev_mask, cap, pd, tid);
-
-    // ---- candidates that can reach this warp's row (one lane per candidate, ballot)
-    const T cx = (T)threadIdx.x, cy = (T)threadIdx.y, cz = (T)threadIdx.z;
-    const T xmax = (T)(min(L::TX, g.n[0] - x0) - 1);
-    unsigned long long wmask = 0ull;
-    for (int kb = 0; kb < cnt; kb += 32) {
-        const int k = kb + lane;
-        bool rel = false;
-        if (k < cnt) {
-            const Vec4<T> a = ld4<T>(srec + k * RW);
-            rel = row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, cy, cz, xmax);
-        }
-        wmask |= (unsigned long long)__ballot_sync(kFull, rel) << kb;
-    }
-
-    // ---- one pass over the row's candidates: eps_s, u_s moments, brackets
-    T seps = 0, mx = 0, my = 0, mz = 0, Mxx = 0, Myy = 0, Mzz = 0, Mxy = 0, Mxz = 0, Myz = 0;
-    // brackets of the first NSLOT candidates: [NSLOT][NC][32 lanes] per warp in shared memory
-    T *const wbr = sbr + (size_t)warp * NSLOT * NC * 32 + lane;
-    unsigned long long mk = wmask;
-    auto visit = [&](const int k, T *b) {
-        const T *rk = srec + k * RW;
-        const Vec4<T> a = ld4<T>(rk);           // px, py, pz, r
-        const Vec4<T> f = ld4<T>(rk + 4);       // f(r), Ux, Uy, Uz
-        T dx, dy, dz;
-        cand_arm<L, T>(g, cx, cy, cz, a.x, a.y, a.z, dx, dy, dz);
-        const T e = active ? shell_eps<T>(dx * dx + dy * dy + dz * dz, a.w, f.x, ph.h) : (T)0;
-        if (e > (T)0) {
-            const Vec4<T> o = ld4<T>(rk + 8);   // Ox, Oy, Oz, id
-            // u_s = U + Omega x (x_n - X_p)
-            const T usx = f.y + o.y * dz - o.z * dy;
-            const T usy = f.z + o.z * dx - o.x * dz;
-            const T usz = (L::D == 3) ? f.w + o.x * dy - o.y * dx : (T)0;
-            // modified scheme weights by eps_s (normalised below); original by B(eps_s)
-            const T wgt = (PSC == 0) ? e : e * ph.tmh / (((T)1 - e) + ph.tmh);
-            seps += wgt;
-            mx += wgt * usx; my += wgt * usy; mz += wgt * usz;
-            Mxx += wgt * usx * usx; Myy += wgt * usy * usy; Mxy += wgt * usx * usy;
-            if (L::D == 3) { Mzz += wgt * usz * usz; Mxz += wgt * usx * usz; Myz += wgt * usy * usz; }
-            if (b) {
-                const T s = (PSC == 0) ? e : (T)1;
-                const T bx = s * (rho * usx + px), by = s * (rho * usy + py);
-                if (L::D == 2) {
-                    b[0] = bx; b[32] = by; b[64] = dx * by - dy * bx;
-                } else {
-                    const T bz = s * (rho * usz + pz);
-                    b[0] = bx; b[32] = by; b[64] = bz;
-                    b[96] = dy * bz - dz * by; b[128] = dz * bx - dx * bz; b[160] = dx * by - dy * bx;
-                }
-            }
-        } else if (b) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) b[32 * c] = (T)0;
-        }
-    };
-    for (int js = 0; js < NSLOT && mk != 0ull; ++js) {
-        const int k = __ffsll((long long)mk) - 1;
-        mk &= mk - 1ull;
-        visit(k, wbr + js * NC * 32);
-    }
-    const unsigned long long rest = mk;           // relevant candidates beyond the slots
-    while (mk) {
-        const int k = __ffsll((long long)mk) - 1;
-        mk &= mk - 1ull;
-        visit(k, nullptr);
-    }
-
-    // ---- weights: eps_n = min(1, sum eps) (Table 1 Step 5), B_n by Eq. 9 at eps_n,
-    //      B_{n,s} = B_n eps_s / sum eps = cB eps_s (Eq. 13). Original: B_n = sum_s B(eps_s) (Eq. 8)
-    const bool any_solid = __any_sync(kFull, seps > (T)0);
-    T Bn = 0, cB = 0;
-    if (seps > (T)0) {
-        if (PSC == 0) {
-            if (seps < (T)1) {
-                cB = ph.tmh / (((T)1 - seps) + ph.tmh);
-                Bn = seps * cB;
-            } else {
-                Bn = (T)1;
-                cB = (T)1 / seps;
-            }
-        } else {
-            Bn = seps;
-            cB = (T)1;
-        }
-        mx *= cB; my *= cB; mz *= cB;
-        Mxx *= cB; Myy *= cB; Mzz *= cB; Mxy *= cB; Mxz *= cB; Myz *= cB;
-    }
-
-    // ---- collision (Eq. 2-4, 10, 12) in deviation form, then store. Collected per cell so
-    //      each direction costs a handful of operations:
-    //      out_i = a1 d_i + B_n d_-i + w_i X_i with
-    //      X_i = K0 + (e.u)(c2 + c4 e.u) + 3 rho e.m + 4.5 rho e.M.e + (1-B) guo (e.F)(3 + 9 e.u)
-    //      (the expansion of the BGK, Eq. 10 solid and Guo terms with B_n, m, M of above)
-    const T uu = ux * ux + uy * uy + uz * uz;
-    const T uF = ux * ph.F[0] + uy * ph.F[1] + uz * ph.F[2];
-    if (!any_solid) {
-        const T base_eq = drho - (T)1.5 * rho * uu;
-        const T om1 = (T)1 - ph.omega;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const T w = (T)weight<L>(i);
-            const T eu = edot<L, T>(i, ux, uy, uz);
-            const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
-            const T dfeq = w * (base_eq + rho * eu * ((T)3 + (T)4.5 * eu));
-            const T fi = ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
-            const T out = om1 * df[i] + ph.omega * dfeq + fi;
-            if (active) Store<S>::st(fout, (long long)i * N + cell, out, ph.sc);
-        }
-    } else {
-        const T omB = (T)1 - Bn;
-        const T oo = omB * ph.omega;
-        const T a1 = (T)1 - oo - Bn;
-        const T c1 = oo - Bn;
-        const T r3 = (T)3 * rho, r45 = (T)4.5 * rho;
-        const T c2 = r3 * (oo + Bn);
-        const T c4 = r45 * c1;
-        const T cg = omB * ph.guo;
-        const T trM = Mxx + Myy + Mzz;
-        const T K0 = c1 * (drho - (T)1.5 * rho * uu) + Bn * drho - (T)1.5 * rho * trM - (T)3 * cg * uF;
-        const T m3x = r3 * mx, m3y = r3 * my, m3z = r3 * mz;
-        const T Axx = r45 * Mxx, Ayy = r45 * Myy, Azz = r45 * Mzz;
-        const T Axy = (T)9 * rho * Mxy, Axz = (T)9 * rho * Mxz, Ayz = (T)9 * rho * Myz;   // 2 x 4.5 rho M_ab
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int o = opp<L>(i);
-            const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-            const T w = (T)weight<L>(i);
-            T X = K0;
-            if (ex || ey || ez) {
-                const T eu = edot<L, T>(i, ux, uy, uz);
-                const T em = edot<L, T>(i, m3x, m3y, m3z);
-                const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
-                // e.M.e: the diagonal entries of the axes e uses, plus 2 e_a e_b M_ab for the pair
-                T eMe = (ex ? Axx : (T)0) + (ey ? Ayy : (T)0);
-                if (L::D == 3) eMe += (ez ? Azz : (T)0);
-                if (ex && ey) eMe += (ex == ey) ? Axy : -Axy;
-                if (ex && ez) eMe += (ex == ez) ? Axz : -Axz;
-                if (ey && ez) eMe += (ey == ez) ? Ayz : -Ayz;
-                X += eu * (c2 + c4 * eu) + em + eMe + cg * eF * ((T)3 + (T)9 * eu);
-            }
-            const T out = a1 * df[i] + Bn * df[o] + w * X;
-            if (active) Store<S>::st(fout, (long long)i * N + cell, out, ph.sc);
-        }
-    }
-
-    // ---- force and torque (Eq. 14; Eq. 11 original): per candidate, the warp's sum of
-    //      mult * bracket with mult = c_B (B_n), one shared-memory partial per warp
-    if (lane == 0) s_mask[warp] = any_solid ? wmask : 0ull;
-    if (any_solid) {
-        const T mult = (PSC == 0) ? cB : Bn;
-        constexpr int NCP = (NC <= 4) ? 4 : 8;             // values per reduction, padded
-        const int cs = lane >> ((NCP == 4) ? 3 : 2);        // the value this lane ends with
-        unsigned long long mf = wmask;
-#pragma unroll
-        for (int js = 0; js < NSLOT; ++js) {
-            if (mf == 0ull || mf == rest) break;
-            const int k = __ffsll((long long)mf) - 1;
-            mf &= mf - 1ull;
-            T v[NCP];
-#pragma unroll
-            for (int c = 0; c < NCP; ++c) v[c] = (c < NC) ? mult * wbr[(js * NC + c) * 32] : (T)0;
-            const T tot = warp_sum_spread<NCP>(v, lane);
-            if ((lane & (32 / NCP - 1)) == 0 && cs < NC) part[((size_t)warp * cap + k) * NC + cs] = tot;
-        }
-        while (mf) {
-            const int k = __ffsll((long long)mf) - 1;
-            mf &= mf - 1ull;
-            T b[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) b[c] = (T)0;
-            // re-evaluate eps_s, u_s and the bracket of this candidate (moments untouched)
-            {
-                const T *rk = srec + k * RW;
-                const Vec4<T> a = ld4<T>(rk);
-                const Vec4<T> f = ld4<T>(rk + 4);
-                T dx, dy, dz;
-                cand_arm<L, T>(g, cx, cy, cz, a.x, a.y, a.z, dx, dy, dz);
-                const T e = active ? shell_eps<T>(dx * dx + dy * dy + dz * dz, a.w, f.x, ph.h) : (T)0;
-                if (e > (T)0) {
-                    const Vec4<T> o = ld4<T>(rk + 8);
-                    const T usx = f.y + o.y * dz - o.z * dy;
-                    const T usy = f.z + o.z * dx - o.x * dz;
-                    const T usz = (L::D == 3) ? f.w + o.x * dy - o.y * dx : (T)0;
-                    const T s = (PSC == 0) ? e : (T)1;
-                    const T bx = s * (rho * usx + px), by = s * (rho * usy + py);
-                    if (L::D == 2) {
-                        b[0] = bx; b[1] = by; b[2] = dx * by - dy * bx;
-                    } else {
-                        const T bz = s * (rho * usz + pz);
-                        b[0] = bx; b[1] = by; b[2] = bz;
-                        b[3] = dy * bz - dz * by; b[4] = dz * bx - dx * bz; b[5] = dx * by - dy * bx;
-                    }
-                }
-            }
-            T v[NCP];
-#pragma unroll
-            for (int c = 0; c < NCP; ++c) v[c] = (c < NC) ? mult * b[c] : (T)0;
-            const T tot = warp_sum_spread<NCP>(v, lane);
-            if ((lane & (32 / NCP - 1)) == 0 && cs < NC) part[((size_t)warp * cap + k) * NC + cs] = tot;
-        }
-    }
-}
-
-// The particle-tile kernel: a persistent grid takes tiles with candidates from the compact
-// list through a work counter (tiles differ in cost, so the counter balances the SMs); the
-// last block to finish resets the counters for the next launch.
-template <class L, typename S, int PSC>
-__global__ void __launch_bounds__(kThreads, (psc_min_blocks<L, typename Store<S>::T>()))
-k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
-                 PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
-    using T = typename Store<S>::T;
-    constexpr int NC = (L::D == 2) ? 3 : 6;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_mask[2][kWarps];
-    __shared__ int s_next[2];
-    const int cap = tl.cap;
-    // double-buffered per tile: records [cap][RW], warp partials [kWarps][cap][NC]
-    T *const sm = reinterpret_cast<T *>(smem);
-    const int rsz = cap * RW, psz = kWarps * cap * NC;
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int npsc = tl.stats[4];
-    if (tid == 0) s_next[0] = atomicAdd(&tl.stats[6], 1);
-    __syncthreads();
-    const T *blocks = reinterpret_cast<const T *>(tl.blocks);
-    int buf = 0, prev_cnt = 0;
-    const T *prev_recs = blocks;
-    for (;;) {
-        const int it = s_next[buf];
-        if (it >= npsc) break;
-        // the following tile's index, fetched now so its latency hides behind this tile
-        if (tid == 0) s_next[buf ^ 1] = atomicAdd(&tl.stats[6], 1);
-        const uint2 ent = tl.order[it];
-        const int cnt = tl.count[ent.x];
-        const T *recs = blocks + (size_t)ent.x * block_elems<T>(cap) + head_elems<T>();
-        T *const cur_part = sm + 2 * rsz + buf * psz;
-        T *const prv_part = sm + 2 * rsz + (buf ^ 1) * psz;
-        if (cnt <= cap) {
-            psc_tile_fast<L, S, PSC>(ent, cnt, fin, fout, g, ph, tl, pd, flags, sm + buf * rsz, cur_part,
-                                     s_mask[buf], prev_cnt, prev_recs, prv_part, s_mask[buf ^ 1],
-                                     sm + 2 * (rsz + psz));
-            prev_cnt = cnt;
-        } else {               // overflowing tiles are left to k_collide_overflow
-            __syncthreads();
-            psc_flush<L, T>(prev_cnt, prev_recs, prv_part, s_mask[buf ^ 1], cap, pd, tid);
-            prev_cnt = 0;
-        }
-        prev_recs = recs;
-        buf ^= 1;
-    }
-    __syncthreads();
-    psc_flush<L, T>(prev_cnt, prev_recs, sm + 2 * rsz + (buf ^ 1) * psz, s_mask[buf ^ 1], cap, pd, tid);
-    if (tid == 0) {
-        __threadfence();
-        if (atomicAdd(&tl.stats[7], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1) {
-            tl.stats[6] = 0;
-            tl.stats[7] = 0;
-        }
-    }
-}
+#include "psc_pair.cuh"
 
 // Tiles with more candidates than the block holds (rare): the exact chunked path over all
 // particles, one block per tile of the overflow list. With no such tile every block returns
@@ -1219,7 +855,7 @@ __global__ void k_set(const double *__restrict__ f, S *__restrict__ fout, Geom g
 // Blocks of a persistent grid: as many as stay resident on all SMs (never more than the
 // work items). The occupancy query is cached per kernel and shared-memory size.
 template <typename K>
-inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsigned &blocks) {
+inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsigned &blocks, int threads = kThreads) {
     static thread_local const void *c_kern = nullptr;
     static thread_local size_t c_smem = (size_t)-1;
     static thread_local int c_per = 0;
@@ -1229,7 +865,7 @@ inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsign
     if (e != cudaSuccess) return e;
     if (c_smem != smem || c_kern != (const void *)kern) {
         int per = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
         if (e != cudaSuccess) return e;
         c_per = per > 0 ? per : 1;
         c_smem = smem;
@@ -1245,8 +881,7 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
                                     const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s) {
     using T = typename Store<S>::T;
     constexpr int NC = (L::D == 2) ? 3 : 6;
-    // double-buffered records and partials, plus the per-warp candidate brackets
-    const size_t smem = 2 * cs_smem_bytes<T>(tl.cap, NC) + (size_t)kWarps * psc_nslot<L>() * NC * 32 * sizeof(T);
+    const size_t smem = pair_smem_bytes<L, T>();
     const size_t osmem = cs_smem_bytes<T>(tl.cap, NC);
     auto kern = k_collide_stream<L, S, PSC>;
     if (smem > 48 * 1024) {
@@ -1259,20 +894,23 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
     unsigned nb = 0;
     cudaError_t e;
+    const dim3 full(g.nt[0], g.nt[1], g.nt[2]);
     if (hasF) {
         e = persistent_blocks(k_fluid<L, S, true>, 0, ntiles, nb);
         if (e != cudaSuccess) return e;
-        k_fluid<L, S, true><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        if (pd.n > 0) k_fluid<L, S, true><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        else k_fluid<L, S, true><<<full, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
     } else {
         e = persistent_blocks(k_fluid<L, S, false>, 0, ntiles, nb);
         if (e != cudaSuccess) return e;
-        k_fluid<L, S, false><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        if (pd.n > 0) k_fluid<L, S, false><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        else k_fluid<L, S, false><<<full, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || pd.n == 0) return e;
-    e = persistent_blocks(kern, smem, ntiles, nb);
+    e = persistent_blocks(kern, smem, ntiles, nb, kPThreads);
     if (e != cudaSuccess) return e;
-    kern<<<nb, block, smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+    kern<<<nb, dim3(32, kPWarps), smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto okern = k_collide_overflow<L, S, PSC>;
