@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_FILES = ["psc_kernels.cuh", "lattice.cuh", "psc_internal.h", "psc_f32.cu"]
+KERNEL_FILES = ["psc_kernels.cuh", "psc_pair.cuh", "lattice.cuh", "psc_internal.h", "psc_f32.cu"]
 
 
 def parse_args(argv=None):
@@ -213,7 +213,9 @@ def run_ours(args, rank, local_rank, world):
     nx, ny, nz = w["n"]
     ncell = nx * ny * nz
     use_dem = (w.get("dem") is not None) and (not args.no_dem) and hasattr(P.lib(), "dem_create")
-    stream = torch.cuda.current_stream(dev)
+    # a stream of our own: the library queues on it and the timing events are recorded on it
+    # (events on the legacy default stream would not order with a non-blocking context stream)
+    stream = torch.cuda.Stream(device=dev)
 
     ctx = P.lbm_create(w["lattice"], nx, ny, nz, bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
                        storage=storage, stream=stream.cuda_stream)

@@ -106,7 +106,9 @@ def test_checkpoint_interval_does_not_change_the_gradient(P):
     ref = _gpu_adjoint(P, case, f0, 12, 12)
     for K in (1, 5, 7):
         J, dX, dF = _gpu_adjoint(P, case, f0, 12, K)
-        assert J == ref[0]
+        # the forward state is re-run exactly; J sums forces through FP64 atomics whose
+        # order varies between launches, so it agrees to FP64 rounding
+        assert J == pytest.approx(ref[0], rel=1e-14, abs=0)
         assert np.allclose(dX, ref[1], rtol=1e-13, atol=1e-18)
         assert np.allclose(dF, ref[2], rtol=1e-13, atol=1e-18)
 
