@@ -1,9 +1,11 @@
 // psc_kernels.cuh -- sm_103a kernels of one lattice-Boltzmann step with the modified
 // partially-saturated-cell (PSC) immersed moving boundary (Liu & Wu, arXiv 1901.09745).
 //
-// One thread block owns one lattice tile (32 x 8 cells in 2D, 32 x 4 x 2 in 3D), one thread
-// per cell, x fastest so a warp reads 32 consecutive populations of one direction.
-// Per step and cell the fused kernel
+// The lattice is cut into tiles (32 x 8 cells in 2D, 32 x 4 x 2 in 3D). After binning,
+// k_pack_tiles writes each tile's candidate particles as packed records and sorts the
+// tiles into three lists: tiles without candidates (k_fluid_pair: BGK + Guo + pull only),
+// tiles with at most 32 (k_collide_stream, psc_pair.cuh), tiles with more (the exact
+// chunked path of k_collide_overflow, psc_tile below). Per cell every path
 //   1. pulls the Q post-collision populations of the previous step from the neighbours
 //      x - e_i (Eq. 1; periodic wrap; halfway bounce-back at walls, Eq. 6),
 //   2. forms rho and the force-shifted u (Eq. 5),
@@ -333,84 +335,6 @@ __device__ __forceinline__ T cand_eps(const T *rec, const Geom &g, T cx, T cy, T
     return e;
 }
 
-// Plain-fluid tiles (no candidate particle): BGK + Guo collision and pull streaming only
-// (Eq. 1-6). With particles a persistent grid (a few blocks per SM) walks the list of tiles
-// without candidates, so no block is spent on a tile that is not its own; without particles
-// every tile gets its own block. No shared memory and no barrier: each warp's loads overlap freely with other
-// warps' arithmetic, and the small register footprint keeps six blocks per SM resident.
-template <class L, typename S, bool HASF>
-__global__ void __launch_bounds__(kThreads, (L::Q == 9) ? 6 : 4)
-k_fluid(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph,
-        Tiles tl, int np, int *flags) {
-    using T = typename Store<S>::T;
-    constexpr int Q = L::Q;
-    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    // with particles: a persistent grid over the list of tiles without candidates; without:
-    // one block per tile of the (nt0, nt1, nt2) grid
-    const int nf = (np > 0) ? tl.stats[5] : 1;
-    const uint2 *list = (np > 0) ? tl.order + ntiles : nullptr;
-    const long long N = g.ncell;
-    for (int it = (np > 0) ? (int)blockIdx.x : 0; it < nf; it += gridDim.x) {
-        int x0, y0, z0;
-        if (list) {
-            const uint2 ent = list[it];
-            const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
-            x0 = (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
-            y0 = (int)ty * L::TY;
-            z0 = (int)tz * L::TZ;
-        } else {
-            x0 = blockIdx.x * L::TX; y0 = blockIdx.y * L::TY; z0 = blockIdx.z * L::TZ;
-        }
-        const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-        if (x >= g.n[0] || y >= g.n[1] || z >= g.n[2]) continue;
-        const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
-        T df[Q];
-        const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
-                              (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
-        if (interior) {
-            const S *base = fin + cell;
-            const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-#pragma unroll
-            for (int i = 0; i < Q; ++i)
-                df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
-        } else {
-#pragma unroll
-            for (int i = 0; i < Q; ++i) df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
-        }
-        T drho = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            drho += df[i];
-            if (L::ex(i)) jx += L::ex(i) * df[i];
-            if (L::ey(i)) jy += L::ey(i) * df[i];
-            if (L::ez(i)) jz += L::ez(i) * df[i];
-        }
-        const T rho = (T)1 + drho;
-        const T irho = (T)1 / rho;
-        const T ux = (HASF ? jx + (T)0.5 * ph.F[0] : jx) * irho;
-        const T uy = (HASF ? jy + (T)0.5 * ph.F[1] : jy) * irho;
-        const T uz = (HASF ? jz + (T)0.5 * ph.F[2] : jz) * irho;
-        if (!(rho > (T)0)) atomicOr(flags, 1);
-        const T uu = ux * ux + uy * uy + uz * uz;
-        const T base_eq = drho - (T)1.5 * rho * uu;
-        const T uF = HASF ? ux * ph.F[0] + uy * ph.F[1] + uz * ph.F[2] : (T)0;
-        const T om1 = (T)1 - ph.omega;
-        S *obase = fout + cell;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const T w = (T)weight<L>(i);
-            const T eu = edot<L, T>(i, ux, uy, uz);
-            const T dfeq = w * (base_eq + rho * eu * ((T)3 + (T)4.5 * eu));
-            T out = om1 * df[i] + ph.omega * dfeq;
-            if (HASF) {
-                const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
-                out += ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
-            }
-            Store<S>::st(obase, (long long)i * N, out, ph.sc);
-        }
-    }
-}
-
 // Arm x_n - X_p from the cell (cx, cy, cz) to the candidate at (px, py, pz), all relative
 // to the tile origin, with the per-cell minimum image on short periodic axes.
 template <class L, typename T>
@@ -478,7 +402,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
     T *part = srec + (size_t)cap * RW;                     // [kWarps][cap][NC] warp partials
 
     const int cnt = tl.count[tile];
-    if (cnt == 0) return;                                   // plain-fluid tile: k_fluid does it
+    if (cnt == 0) return;                                   // plain-fluid tile: k_fluid_pair does it
     const unsigned txy = tile / (unsigned)g.nt[0];          // 32-bit: tiles < 2^31 (host check)
     const int tx = (int)(tile - txy * (unsigned)g.nt[0]);
     const int ty = (int)(txy % (unsigned)g.nt[1]);
@@ -895,16 +819,17 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     unsigned nb = 0;
     cudaError_t e;
     const dim3 full(g.nt[0], g.nt[1], g.nt[2]);
+    const dim3 pblock(32, kPWarps);
     if (hasF) {
-        e = persistent_blocks(k_fluid<L, S, true>, 0, ntiles, nb);
+        e = persistent_blocks(k_fluid_pair<L, S, true>, 0, ntiles, nb, kPThreads);
         if (e != cudaSuccess) return e;
-        if (pd.n > 0) k_fluid<L, S, true><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
-        else k_fluid<L, S, true><<<full, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
+        if (pd.n > 0) k_fluid_pair<L, S, true><<<nb, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        else k_fluid_pair<L, S, true><<<full, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
     } else {
-        e = persistent_blocks(k_fluid<L, S, false>, 0, ntiles, nb);
+        e = persistent_blocks(k_fluid_pair<L, S, false>, 0, ntiles, nb, kPThreads);
         if (e != cudaSuccess) return e;
-        if (pd.n > 0) k_fluid<L, S, false><<<nb, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
-        else k_fluid<L, S, false><<<full, block, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
+        if (pd.n > 0) k_fluid_pair<L, S, false><<<nb, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        else k_fluid_pair<L, S, false><<<full, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess || pd.n == 0) return e;

@@ -487,3 +487,90 @@ k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
         }
     }
 }
+// Plain-fluid tiles with two cells per thread (rows as in the particle-tile kernel): BGK +
+// Guo + pull on FP32 pairs. With particles a persistent grid over the list of tiles without
+// candidates; without, one block per tile.
+template <class L, typename S, bool HASF>
+__global__ void __launch_bounds__(kPThreads, (L::Q == 9) ? 8 : 5)
+k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph,
+             Tiles tl, int np, int *flags) {
+    using T = typename Store<S>::T;
+    using P = Pr<T>;
+    using V = typename P::V;
+    constexpr int Q = L::Q;
+    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
+    const int nf = (np > 0) ? tl.stats[5] : 1;
+    const uint2 *list = (np > 0) ? tl.order + ntiles : nullptr;
+    const long long N = g.ncell;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const int ryA = (L::D == 2) ? 2 * warp : warp, ryB = (L::D == 2) ? 2 * warp + 1 : warp;
+    const int rzA = 0, rzB = (L::D == 2) ? 0 : 1;
+    for (int it = (np > 0) ? (int)blockIdx.x : 0; it < nf; it += gridDim.x) {
+        int x0, y0, z0;
+        if (list) {
+            const uint2 ent = list[it];
+            const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
+            x0 = (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
+            y0 = (int)ty * L::TY;
+            z0 = (int)tz * L::TZ;
+        } else {
+            x0 = blockIdx.x * L::TX; y0 = blockIdx.y * L::TY; z0 = blockIdx.z * L::TZ;
+        }
+        const int x = x0 + lane;
+        const int yA = y0 + ryA, yB = y0 + ryB, zA = z0 + rzA, zB = z0 + rzB;
+        const bool actA = x < g.n[0] && yA < g.n[1] && zA < g.n[2];
+        const bool actB = x < g.n[0] && yB < g.n[1] && zB < g.n[2];
+        const long long cellA = x + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
+        const long long cellB = x + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
+        const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
+                              (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+        T da[Q], db[Q];
+        pull_q<L, S>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
+        pull_q<L, S>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
+        V df[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
+        V drho = df[0], jx = P::sp((T)0), jy = P::sp((T)0), jz = P::sp((T)0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) drho = P::add(drho, df[i]);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (L::ex(i)) jx = L::ex(i) > 0 ? P::add(jx, df[i]) : P::sub(jx, df[i]);
+            if (L::ey(i)) jy = L::ey(i) > 0 ? P::add(jy, df[i]) : P::sub(jy, df[i]);
+            if (L::ez(i)) jz = L::ez(i) > 0 ? P::add(jz, df[i]) : P::sub(jz, df[i]);
+        }
+        const V rho = P::add(P::sp((T)1), drho);
+        const V irho = P::mk((T)1 / rho.x, (T)1 / rho.y);
+        V ux, uy, uz;
+        if (HASF) {
+            ux = P::mul(P::add(jx, P::sp((T)0.5 * ph.F[0])), irho);
+            uy = P::mul(P::add(jy, P::sp((T)0.5 * ph.F[1])), irho);
+            uz = P::mul(P::add(jz, P::sp((T)0.5 * ph.F[2])), irho);
+        } else {
+            ux = P::mul(jx, irho); uy = P::mul(jy, irho); uz = P::mul(jz, irho);
+        }
+        if ((actA && !(rho.x > (T)0)) || (actB && !(rho.y > (T)0))) atomicOr(flags, 1);
+        const V uu = P::fma(ux, ux, P::fma(uy, uy, P::mul(uz, uz)));
+        const V base_eq = P::sub(drho, P::mul(P::sp((T)1.5), P::mul(rho, uu)));
+        const V om1 = P::sp((T)1 - ph.omega), om = P::sp(ph.omega);
+        V guo3uF = P::sp((T)0);
+        if (HASF) {
+            const V uF = P::fma(ux, P::sp(ph.F[0]), P::fma(uy, P::sp(ph.F[1]), P::mul(uz, P::sp(ph.F[2]))));
+            guo3uF = P::mul(P::sp((T)3 * ph.guo), uF);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const T w = (T)weight<L>(i);
+            const V eu = edot2<L, T>(i, ux, uy, uz);
+            // w (base_eq + rho eu (3 + 4.5 eu))
+            const V dfeq = P::mul(P::sp(w), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
+            V out = P::fma(om1, df[i], P::mul(om, dfeq));
+            if (HASF) {
+                const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
+                out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
+            }
+            if (actA) Store<S>::st(fout, (long long)i * N + cellA, out.x, ph.sc);
+            if (actB) Store<S>::st(fout, (long long)i * N + cellB, out.y, ph.sc);
+        }
+    }
+}
