@@ -62,13 +62,7 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
     const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
     T d[Q];
-    if (interior) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = gt[(long long)i * N + cell - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz)];
-    } else {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) d[i] = active ? pull_one<L, T>(gt, g, x, y, z, cell, i, ph.sc) : (T)0;
-    }
+    pull_q<L, T>(gt, g, x, y, z, cell, interior, active, ph.sc, d);
     T drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -160,6 +154,7 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
     // a_k = lambda_k (1 - (1-B) omega - B) + B lambda_-k + Arho + Au.(e_k - u)/rho + (B/T) e_kx,
     // pushed back along the link it was pulled from (S^T)
     const T diag = (T)1 - oo - B;
+    const NbrIdx nb = interior ? NbrIdx{} : make_nbr_idx<L>(g, x, y, z);
     const T c0 = Arho - (Au[0] * u[0] + Au[1] * u[1] + Au[2] * u[2]) * irho;
     const T Av[3] = {Au[0] * irho + invT * B, Au[1] * irho, Au[2] * irho};
     if (active) {
@@ -171,19 +166,9 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
             if (L::ez(k)) a += L::ez(k) > 0 ? Av[2] : -Av[2];
             if (interior) {
                 lam_out[(long long)k * N + cell - (L::ex(k) + L::ey(k) * sy + L::ez(k) * sz)] = a;
-                continue;
+            } else {
+                lam_out[src_index<L>(nb, k, cell, N)] = a;   // S^T: the pull's source, written once
             }
-            int s[3] = {x - L::ex(k), y - L::ey(k), z - L::ez(k)};
-            bool bounce = false;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                if (s[q] < 0 || s[q] >= g.n[q]) {
-                    if (g.periodic[q]) s[q] += (s[q] < 0) ? g.n[q] : -g.n[q];
-                    else bounce = true;
-                }
-            }
-            if (bounce) lam_out[(long long)opp<L>(k) * N + cell] = a;
-            else lam_out[(long long)k * N + (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2])] = a;
         }
     }
 

@@ -132,10 +132,46 @@ __device__ __forceinline__ T edot(const int i, const T vx, const T vy, const T v
     return r;
 }
 
-// All Q pulled deviations of the cell (x, y, z) (Eq. 1, 6). Tiles one cell clear of every
-// face use fixed offsets; elsewhere the offsets to the -1 and +1 neighbour on each axis
-// (periodic wrap folded in) and the wall flags are formed once per cell, so each direction
-// costs an add and a select instead of three range tests.
+// Where the pull of direction i at cell x reads (Eq. 1, 6): x - e_i, or the cell itself in
+// direction -i when x - e_i lies beyond a wall (halfway bounce-back). The offsets to the -1
+// and +1 neighbour on each axis (periodic wrap folded in) and the wall flags are formed once
+// per cell, so each direction costs an add and a select instead of three range tests. The
+// adjoint pushes to the same index.
+struct NbrIdx {
+    long long oxm, oxp, oym, oyp, ozm, ozp;   // source offsets when e = +1 (m) / -1 (p)
+    unsigned wall;                            // bits 0..5: wxm wxp wym wyp wzm wzp
+};
+
+template <class L>
+__device__ __forceinline__ NbrIdx make_nbr_idx(const Geom &g, int x, int y, int z) {
+    const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+    NbrIdx nb{-1, 1, -sy, sy, -sz, sz, 0u};
+    if (x == 0) { if (g.periodic[0]) nb.oxm = g.n[0] - 1; else nb.wall |= 1u; }
+    if (x == g.n[0] - 1) { if (g.periodic[0]) nb.oxp = -(long long)(g.n[0] - 1); else nb.wall |= 2u; }
+    if (y == 0) { if (g.periodic[1]) nb.oym = (long long)(g.n[1] - 1) * sy; else nb.wall |= 4u; }
+    if (y == g.n[1] - 1) { if (g.periodic[1]) nb.oyp = -(long long)(g.n[1] - 1) * sy; else nb.wall |= 8u; }
+    if (L::D == 3) {
+        if (z == 0) { if (g.periodic[2]) nb.ozm = (long long)(g.n[2] - 1) * sz; else nb.wall |= 16u; }
+        if (z == g.n[2] - 1) { if (g.periodic[2]) nb.ozp = -(long long)(g.n[2] - 1) * sz; else nb.wall |= 32u; }
+    }
+    return nb;
+}
+
+template <class L>
+__device__ __forceinline__ long long src_index(const NbrIdx &nb, const int i, const long long cell, const long long N) {
+    long long off = 0;
+    unsigned w = 0u;
+    if (L::ex(i) == 1) { off += nb.oxm; w |= 1u; }
+    if (L::ex(i) == -1) { off += nb.oxp; w |= 2u; }
+    if (L::ey(i) == 1) { off += nb.oym; w |= 4u; }
+    if (L::ey(i) == -1) { off += nb.oyp; w |= 8u; }
+    if (L::ez(i) == 1) { off += nb.ozm; w |= 16u; }
+    if (L::ez(i) == -1) { off += nb.ozp; w |= 32u; }
+    return (nb.wall & w) ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
+}
+
+// All Q pulled deviations of the cell (x, y, z). Tiles one cell clear of every face use
+// fixed offsets; elsewhere the per-cell neighbour offsets above.
 template <class L, typename S>
 __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g, int x, int y, int z,
                                        long long cell, bool interior, bool active, float2 sc,
@@ -156,30 +192,9 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
         for (int i = 0; i < Q; ++i) df[i] = (T)0;
         return;
     }
-    // source x - e: from the -1 neighbour when e = +1 (m), from the +1 neighbour when e = -1 (p)
-    long long oxm = -1, oxp = 1, oym = -sy, oyp = sy, ozm = -sz, ozp = sz;
-    bool wxm = false, wxp = false, wym = false, wyp = false, wzm = false, wzp = false;
-    if (x == 0) { if (g.periodic[0]) oxm = g.n[0] - 1; else wxm = true; }
-    if (x == g.n[0] - 1) { if (g.periodic[0]) oxp = -(long long)(g.n[0] - 1); else wxp = true; }
-    if (y == 0) { if (g.periodic[1]) oym = (long long)(g.n[1] - 1) * sy; else wym = true; }
-    if (y == g.n[1] - 1) { if (g.periodic[1]) oyp = -(long long)(g.n[1] - 1) * sy; else wyp = true; }
-    if (L::D == 3) {
-        if (z == 0) { if (g.periodic[2]) ozm = (long long)(g.n[2] - 1) * sz; else wzm = true; }
-        if (z == g.n[2] - 1) { if (g.periodic[2]) ozp = -(long long)(g.n[2] - 1) * sz; else wzp = true; }
-    }
+    const NbrIdx nb = make_nbr_idx<L>(g, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        long long off = 0;
-        bool wall = false;
-        if (L::ex(i) == 1) { off += oxm; wall |= wxm; }
-        if (L::ex(i) == -1) { off += oxp; wall |= wxp; }
-        if (L::ey(i) == 1) { off += oym; wall |= wym; }
-        if (L::ey(i) == -1) { off += oyp; wall |= wyp; }
-        if (L::ez(i) == 1) { off += ozm; wall |= wzm; }
-        if (L::ez(i) == -1) { off += ozp; wall |= wzp; }
-        const long long idx = wall ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
-        df[i] = Store<S>::ld(fin, idx, sc);
-    }
+    for (int i = 0; i < Q; ++i) df[i] = Store<S>::ld(fin, src_index<L>(nb, i, cell, N), sc);
 }
 
 // ------------------------------------------------------------------- candidate records
