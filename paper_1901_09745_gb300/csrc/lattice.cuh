@@ -56,36 +56,50 @@ __host__ __device__ constexpr double weight(int i) {
 
 // Storage of the deviation d_i = f_i - w_i: FP64 and FP32 hold it as is; FP16 and BF16 hold
 // scale * d_i rounded to nearest and are widened to FP32 for compute. `sc` carries
-// (scale, 1/scale).
+// (scale, 1/scale). ld/st convert between d_i and the stored value; ldr/str only widen and
+// narrow (kScaled says whether the stored value carries the scale), for kernels that fold
+// the scale into their own arithmetic.
 template <typename S> struct Store;
 
 template <> struct Store<double> {
     using T = double;
+    static constexpr bool kScaled = false;
     __device__ __forceinline__ static double ld(const double *p, long long i, float2) { return p[i]; }
     __device__ __forceinline__ static void st(double *p, long long i, double v, float2) { p[i] = v; }
+    __device__ __forceinline__ static double ldr(const double *p, long long i) { return p[i]; }
+    __device__ __forceinline__ static void str(double *p, long long i, double v) { p[i] = v; }
 };
 template <> struct Store<float> {
     using T = float;
+    static constexpr bool kScaled = false;
     __device__ __forceinline__ static float ld(const float *p, long long i, float2) { return p[i]; }
     __device__ __forceinline__ static void st(float *p, long long i, float v, float2) { p[i] = v; }
+    __device__ __forceinline__ static float ldr(const float *p, long long i) { return p[i]; }
+    __device__ __forceinline__ static void str(float *p, long long i, float v) { p[i] = v; }
 };
 template <> struct Store<__half> {
     using T = float;
+    static constexpr bool kScaled = true;
     __device__ __forceinline__ static float ld(const __half *p, long long i, float2 sc) {
         return __half2float(p[i]) * sc.y;
     }
     __device__ __forceinline__ static void st(__half *p, long long i, float v, float2 sc) {
         p[i] = __float2half_rn(v * sc.x);
     }
+    __device__ __forceinline__ static float ldr(const __half *p, long long i) { return __half2float(p[i]); }
+    __device__ __forceinline__ static void str(__half *p, long long i, float v) { p[i] = __float2half_rn(v); }
 };
 template <> struct Store<__nv_bfloat16> {
     using T = float;
+    static constexpr bool kScaled = true;
     __device__ __forceinline__ static float ld(const __nv_bfloat16 *p, long long i, float2 sc) {
         return __bfloat162float(p[i]) * sc.y;
     }
     __device__ __forceinline__ static void st(__nv_bfloat16 *p, long long i, float v, float2 sc) {
         p[i] = __float2bfloat16_rn(v * sc.x);
     }
+    __device__ __forceinline__ static float ldr(const __nv_bfloat16 *p, long long i) { return __bfloat162float(p[i]); }
+    __device__ __forceinline__ static void str(__nv_bfloat16 *p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
 };
 
 }  // namespace psc

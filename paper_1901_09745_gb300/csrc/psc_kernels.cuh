@@ -173,7 +173,7 @@ __device__ __forceinline__ long long src_index(const NbrIdx &nb, const int i, co
 // All Q pulled deviations of the cell (x, y, z). Tiles one cell clear of every face use
 // fixed offsets; elsewhere the same offsets and wall flags as make_nbr_idx, held in scalars
 // (measured faster here than going through the struct).
-template <class L, typename S>
+template <class L, typename S, bool RAW = false>
 __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g, int x, int y, int z,
                                        long long cell, bool interior, bool active, float2 sc,
                                        typename Store<S>::T *df) {
@@ -184,8 +184,10 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
     if (interior) {
         const S *base = fin + cell;
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), sc);
+        for (int i = 0; i < Q; ++i) {
+            const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
+            df[i] = RAW ? Store<S>::ldr(base, o) : Store<S>::ld(base, o, sc);
+        }
         return;
     }
     if (!active) {
@@ -215,7 +217,7 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
         if (L::ez(i) == 1) { off += ozm; wall |= wzm; }
         if (L::ez(i) == -1) { off += ozp; wall |= wzp; }
         const long long idx = wall ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
-        df[i] = Store<S>::ld(fin, idx, sc);
+        df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
     }
 }
 

@@ -164,9 +164,12 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     // ---- pull and moments (Eq. 1, 5, 6)
     const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+    // 16-bit storage: the stored values carry the scale s; they are summed as stored and the
+    // sums unscaled once, and the outputs are formed scaled (s folded into the weights)
+    constexpr bool SC = Store<S>::kScaled;
     T da[Q], db[Q];
-    pull_q<L, S>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
-    pull_q<L, S>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
+    pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
+    pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
     V df[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -178,6 +181,11 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
         if (L::ex(i)) jx = L::ex(i) > 0 ? P::add(jx, df[i]) : P::sub(jx, df[i]);
         if (L::ey(i)) jy = L::ey(i) > 0 ? P::add(jy, df[i]) : P::sub(jy, df[i]);
         if (L::ez(i)) jz = L::ez(i) > 0 ? P::add(jz, df[i]) : P::sub(jz, df[i]);
+    }
+    const T ssc = SC ? (T)ph.sc.x : (T)1;           // s (the stored values are s d)
+    if (SC) {
+        const V is = P::sp((T)ph.sc.y);
+        drho = P::mul(drho, is); jx = P::mul(jx, is); jy = P::mul(jy, is); jz = P::mul(jz, is);
     }
     const V rho = P::add(P::sp((T)1), drho);
     const V irho = P::mk((T)1 / rho.x, (T)1 / rho.y);
@@ -306,12 +314,13 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
             const V eu = edot2<L, T>(i, ux, uy, uz);
             const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
             // w (base_eq + rho eu (3 + 4.5 eu))
-            const V dfeq = P::mul(P::sp(w), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
+            const T ws = w * ssc;
+            const V dfeq = P::mul(P::sp(ws), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
             // guo w (3 (eF - uF) + 9 eu eF)
-            const V fi = P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF));
+            const V fi = P::mul(P::sp(ws), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF));
             const V out = P::add(P::fma(om1, df[i], P::mul(om, dfeq)), fi);
-            if (actA) Store<S>::st(fout, (long long)i * N + cellA, out.x, ph.sc);
-            if (actB) Store<S>::st(fout, (long long)i * N + cellB, out.y, ph.sc);
+            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
+            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
         }
     } else {
         const V mxs = P::mul(cB, mx), mys = P::mul(cB, my), mzs = P::mul(cB, mz);
@@ -359,9 +368,9 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
                 t = P::fma(P::mul(cg, P::sp(eF)), P::fma(P::sp((T)9), eu, P::sp((T)3)), t);
                 X = P::add(X, t);
             }
-            const V out = P::fma(a1, df[i], P::fma(Bn, df[o], P::mul(P::sp(w), X)));
-            if (actA) Store<S>::st(fout, (long long)i * N + cellA, out.x, ph.sc);
-            if (actB) Store<S>::st(fout, (long long)i * N + cellB, out.y, ph.sc);
+            const V out = P::fma(a1, df[i], P::fma(Bn, df[o], P::mul(P::sp(w * ssc), X)));
+            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
+            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
         }
     }
 
@@ -524,9 +533,10 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
         const long long cellB = x + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
         const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
                               (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+        constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
         T da[Q], db[Q];
-        pull_q<L, S>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
-        pull_q<L, S>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
+        pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
+        pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
         V df[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -538,6 +548,11 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
             if (L::ex(i)) jx = L::ex(i) > 0 ? P::add(jx, df[i]) : P::sub(jx, df[i]);
             if (L::ey(i)) jy = L::ey(i) > 0 ? P::add(jy, df[i]) : P::sub(jy, df[i]);
             if (L::ez(i)) jz = L::ez(i) > 0 ? P::add(jz, df[i]) : P::sub(jz, df[i]);
+        }
+        const T ssc = SC ? (T)ph.sc.x : (T)1;
+        if (SC) {
+            const V is = P::sp((T)ph.sc.y);
+            drho = P::mul(drho, is); jx = P::mul(jx, is); jy = P::mul(jy, is); jz = P::mul(jz, is);
         }
         const V rho = P::add(P::sp((T)1), drho);
         const V irho = P::mk((T)1 / rho.x, (T)1 / rho.y);
@@ -560,7 +575,7 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
         }
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const T w = (T)weight<L>(i);
+            const T w = (T)weight<L>(i) * ssc;
             const V eu = edot2<L, T>(i, ux, uy, uz);
             // w (base_eq + rho eu (3 + 4.5 eu))
             const V dfeq = P::mul(P::sp(w), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
@@ -569,8 +584,8 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
                 const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
                 out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
             }
-            if (actA) Store<S>::st(fout, (long long)i * N + cellA, out.x, ph.sc);
-            if (actB) Store<S>::st(fout, (long long)i * N + cellB, out.y, ph.sc);
+            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
+            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
         }
     }
 }
