@@ -111,9 +111,9 @@ template <class L> constexpr int pair_nslot() { return (L::D == 2) ? 4 : 2; }
 
 template <class L, typename T> __host__ __device__ constexpr size_t pair_smem_bytes() {
     // records [2][kPairCap][RW] | partials [2][kPWarps][kPairCap][NC] | brackets
-    // [kPWarps][NSLOT][NC][32] pairs
+    // [kPWarps][NSLOT + 1][NC][32] pairs (the last slot is scratch for further candidates)
     return (size_t)2 * kPairCap * RW * sizeof(T) + (size_t)2 * kPWarps * kPairCap * ((L::D == 2) ? 3 : 6) * sizeof(T) +
-           (size_t)kPWarps * pair_nslot<L>() * ((L::D == 2) ? 3 : 6) * 32 * 2 * sizeof(T);
+           (size_t)kPWarps * (pair_nslot<L>() + 1) * ((L::D == 2) ? 3 : 6) * 32 * 2 * sizeof(T);
 }
 
 template <class L, typename S, int PSC>
@@ -168,8 +168,19 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     // sums unscaled once, and the outputs are formed scaled (s folded into the weights)
     constexpr bool SC = Store<S>::kScaled;
     T da[Q], db[Q];
-    pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
-    pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
+    if (interior) {     // both cells with the same fixed offsets (one copy of the load code)
+        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+        const S *ba = fin + cellA, *bb = fin + cellB;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
+            da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
+            db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
+        }
+    } else {
+        pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, false, actA, ph.sc, da);
+        pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, false, actB, ph.sc, db);
+    }
     V df[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -225,8 +236,9 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     // ---- one pass over the candidates: eps_s, u_s moments, brackets
     V seps = P::sp((T)0), mx = seps, my = seps, mz = seps;
     V Mxx = seps, Myy = seps, Mzz = seps, Mxy = seps, Mxz = seps, Myz = seps;
-    V *const wbr = sbr + (size_t)warp * NSLOT * NC * 32 + lane;   // [NSLOT][NC][32]
-    auto visit = [&](const int k, V *b) {
+    V *const wbr = sbr + (size_t)warp * (NSLOT + 1) * NC * 32 + lane;   // [NSLOT + 1][NC][32]
+    // one candidate at both cells: eps, and (acc) the u_s moments, and (b) the bracket
+    auto visit = [&](const int k, V *b, const bool acc) {
         const T *rk = srec + k * RW;
         const Vec4<T> a = ld4<T>(rk);           // px, py, pz, r
         const Vec4<T> f = ld4<T>(rk + 4);       // f(r), Ux, Uy, Uz
@@ -246,18 +258,20 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
             const V e = P::mk(ea, eb);
             const V wgt = (PSC == 0) ? e
                                      : P::mk(ea * ph.tmh / (((T)1 - ea) + ph.tmh), eb * ph.tmh / (((T)1 - eb) + ph.tmh));
-            seps = P::add(seps, wgt);
-            mx = P::fma(wgt, usx, mx);
-            my = P::fma(wgt, usy, my);
-            const V wx = P::mul(wgt, usx), wy = P::mul(wgt, usy);
-            Mxx = P::fma(wx, usx, Mxx);
-            Myy = P::fma(wy, usy, Myy);
-            Mxy = P::fma(wx, usy, Mxy);
-            if (L::D == 3) {
-                mz = P::fma(wgt, usz, mz);
-                Mzz = P::fma(P::mul(wgt, usz), usz, Mzz);
-                Mxz = P::fma(wx, usz, Mxz);
-                Myz = P::fma(wy, usz, Myz);
+            if (acc) {
+                seps = P::add(seps, wgt);
+                mx = P::fma(wgt, usx, mx);
+                my = P::fma(wgt, usy, my);
+                const V wx = P::mul(wgt, usx), wy = P::mul(wgt, usy);
+                Mxx = P::fma(wx, usx, Mxx);
+                Myy = P::fma(wy, usy, Myy);
+                Mxy = P::fma(wx, usy, Mxy);
+                if (L::D == 3) {
+                    mz = P::fma(wgt, usz, mz);
+                    Mzz = P::fma(P::mul(wgt, usz), usz, Mzz);
+                    Mxz = P::fma(wx, usz, Mxz);
+                    Myz = P::fma(wy, usz, Myz);
+                }
             }
             if (b) {
                 const V s = (PSC == 0) ? e : P::mk(ea > (T)0 ? (T)1 : (T)0, eb > (T)0 ? (T)1 : (T)0);
@@ -278,17 +292,13 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
             for (int c = 0; c < NC; ++c) b[32 * c] = P::sp((T)0);
         }
     };
-    unsigned mk = wmask;
-    for (int js = 0; js < NSLOT && mk != 0u; ++js) {
-        const int k = __ffs(mk) - 1;
-        mk &= mk - 1u;
-        visit(k, wbr + js * NC * 32);
-    }
-    const unsigned rest = mk;               // candidates beyond the slots (rare)
-    while (mk) {
-        const int k = __ffs(mk) - 1;
-        mk &= mk - 1u;
-        visit(k, nullptr);
+    {
+        unsigned mk = wmask;
+        for (int js = 0; mk != 0u; ++js) {
+            const int k = __ffs(mk) - 1;
+            mk &= mk - 1u;
+            visit(k, js < NSLOT ? wbr + js * NC * 32 : nullptr, true);
+        }
     }
 
     // ---- weights (Eq. 8, 9, 13; Table 1 Step 5)
@@ -298,31 +308,16 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     psc_weights<PSC, T>(seps.y, ph.tmh, BnB, cBB);
     const V Bn = P::mk(BnA, BnB), cB = P::mk(cBA, cBB);
 
-    // ---- collision (Eq. 2-4, 10, 12), collected per cell as in the one-cell path:
+    // ---- collision (Eq. 2-4, 10, 12), collected per cell:
     //      out_i = a1 d_i + B_n d_-i + w_i X_i,
-    //      X_i = K0 + (e.u)(c2 + c4 e.u) + 3 rho e.m + 4.5 rho e.M.e + (1-B) guo (e.F)(3 + 9 e.u)
+    //      X_i = K0 + (e.u)(c2 + c4 e.u) + 3 rho e.m + 4.5 rho e.M.e + (1-B) guo (e.F)(3 + 9 e.u).
+    //      Rows with no solid cell take the same code (B_n = 0 reduces it to BGK + Guo
+    //      exactly): one copy of the collision keeps the kernel small enough for the
+    //      instruction cache, which measured faster than a separate fluid branch.
     const V uu = P::fma(ux, ux, P::fma(uy, uy, P::mul(uz, uz)));
     const V uF = P::fma(ux, P::sp(ph.F[0]), P::fma(uy, P::sp(ph.F[1]), P::mul(uz, P::sp(ph.F[2]))));
     const V one = P::sp((T)1);
-    if (!any_solid) {
-        const V base_eq = P::sub(drho, P::mul(P::sp((T)1.5), P::mul(rho, uu)));
-        const V om1 = P::sp((T)1 - ph.omega), om = P::sp(ph.omega);
-        const V guo3uF = P::mul(P::sp((T)3 * ph.guo), uF);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const T w = (T)weight<L>(i);
-            const V eu = edot2<L, T>(i, ux, uy, uz);
-            const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
-            // w (base_eq + rho eu (3 + 4.5 eu))
-            const T ws = w * ssc;
-            const V dfeq = P::mul(P::sp(ws), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
-            // guo w (3 (eF - uF) + 9 eu eF)
-            const V fi = P::mul(P::sp(ws), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF));
-            const V out = P::add(P::fma(om1, df[i], P::mul(om, dfeq)), fi);
-            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
-            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
-        }
-    } else {
+    {
         const V mxs = P::mul(cB, mx), mys = P::mul(cB, my), mzs = P::mul(cB, mz);
         const V omB = P::sub(one, Bn);
         const V oo = P::mul(omB, P::sp(ph.omega));
@@ -396,44 +391,14 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
             const T tot = warp_sum_spread<NCP>(v, lane);
             if ((lane & (32 / NCP - 1)) == 0 && cs < NC) part[(warp * kPairCap + k) * NC + cs] = tot;
         };
-        for (int js = 0; js < NSLOT && mf != 0u && mf != rest; ++js) {
+        // the first NSLOT candidates' brackets are kept; further ones are evaluated again
+        // (brackets only) into the scratch slot
+        V *const scratch = wbr + NSLOT * NC * 32;
+        for (int js = 0; mf != 0u; ++js) {
             const int k = __ffs(mf) - 1;
             mf &= mf - 1u;
-            reduce_store(k, wbr + js * NC * 32, 32);
-        }
-        while (mf) {
-            const int k = __ffs(mf) - 1;
-            mf &= mf - 1u;
-            // re-evaluate this candidate's bracket (moments are not touched again)
-            V b[NC];
-            {
-                const T *rk = srec + k * RW;
-                const Vec4<T> a = ld4<T>(rk);
-                const Vec4<T> f = ld4<T>(rk + 4);
-                T dxa, dya, dza, dxb, dyb, dzb;
-                cand_arm<L, T>(g, cx, cyA, czA, a.x, a.y, a.z, dxa, dya, dza);
-                cand_arm<L, T>(g, cx, cyB, czB, a.x, a.y, a.z, dxb, dyb, dzb);
-                const T ea = actA ? shell_eps<T>(dxa * dxa + dya * dya + dza * dza, a.w, f.x, ph.h) : (T)0;
-                const T eb = actB ? shell_eps<T>(dxb * dxb + dyb * dyb + dzb * dzb, a.w, f.x, ph.h) : (T)0;
-                const Vec4<T> o = ld4<T>(rk + 8);
-                const V dx = P::mk(dxa, dxb), dy = P::mk(dya, dyb), dz = P::mk(dza, dzb);
-                const V usx = P::fma(P::sp(o.y), dz, P::fma(P::sp(-o.z), dy, P::sp(f.y)));
-                const V usy = P::fma(P::sp(o.z), dx, P::fma(P::sp(-o.x), dz, P::sp(f.z)));
-                const V usz = (L::D == 3) ? P::fma(P::sp(o.x), dy, P::fma(P::sp(-o.y), dx, P::sp(f.w))) : P::sp((T)0);
-                const V s = (PSC == 0) ? P::mk(ea, eb) : P::mk(ea > (T)0 ? (T)1 : (T)0, eb > (T)0 ? (T)1 : (T)0);
-                const V bx = P::mul(s, P::fma(rho, usx, px));
-                const V by = P::mul(s, P::fma(rho, usy, py));
-                if (L::D == 2) {
-                    b[0] = bx; b[1] = by; b[2] = P::sub(P::mul(dx, by), P::mul(dy, bx));
-                } else {
-                    const V bz = P::mul(s, P::fma(rho, usz, pz));
-                    b[0] = bx; b[1] = by; b[2] = bz;
-                    b[3] = P::sub(P::mul(dy, bz), P::mul(dz, by));
-                    b[4] = P::sub(P::mul(dz, bx), P::mul(dx, bz));
-                    b[5] = P::sub(P::mul(dx, by), P::mul(dy, bx));
-                }
-            }
-            reduce_store(k, b, 1);
+            if (js >= NSLOT) visit(k, scratch, false);
+            reduce_store(k, js < NSLOT ? wbr + js * NC * 32 : scratch, 32);
         }
     }
 }
