@@ -500,8 +500,19 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
                               (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
         constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
         T da[Q], db[Q];
-        pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, interior, actA, ph.sc, da);
-        pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, interior, actB, ph.sc, db);
+        if (interior) {     // both cells with the same fixed offsets (one copy of the load code)
+            const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+            const S *ba = fin + cellA, *bb = fin + cellB;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
+                da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
+                db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
+            }
+        } else {
+            pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, false, actA, ph.sc, da);
+            pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, false, actB, ph.sc, db);
+        }
         V df[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
