@@ -39,6 +39,7 @@ struct DemGeom {
     int bin_cap;
     double skin;
     float margin;       // slack for FP32 position copies (>> their rounding error)
+    double inv_n[3];    // 1 / n per axis (no FP64 division on the device)
 };
 
 struct DemPhys {
@@ -262,7 +263,10 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, doub
                              double ri, double rj, float imi, float imj, const double *Ui,
                              const double *Uj, const double *Omi, const double *Omj, float *h,
                              float *fo, float *to, int *fail) {
-    const float Rf = (float)(ri * rj / (ri + rj));
+    // the contact law runs in FP32; only the contact decisions below use FP64 (GB300 executes
+    // FP64, and FP64 division in particular, at a small fraction of the FP32 rate)
+    const float rif = (float)ri, rjf = (float)rj;
+    const float Rf = rif * rjf / (rif + rjf);
     const float Es = ph.Es;
     float FC = 0.0f, a0 = 0.0f;
     const bool was = h[7] != 0.0f;
@@ -289,10 +293,9 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, doub
         for (int a = 0; a < 3; ++a) { fo[a] = 0.0f; to[a] = 0.0f; }
         return false;
     }
-    const double inv = 1.0 / dist;
-    const float n[3] = {(float)(d64[0] * inv), (float)(d64[1] * inv), (float)(d64[2] * inv)};
+    const float inv = 1.0f / (float)dist;
+    const float n[3] = {(float)d64[0] * inv, (float)d64[1] * inv, (float)d64[2] * inv};
     const float dnf = (float)dn;
-    const float rif = (float)ri, rjf = (float)rj;
     float ac, Fne, kr = 0.0f;
     if (ph.adhesive) {
         const float s = jkr_s(dnf * Rf / (a0 * a0), fail);
@@ -470,7 +473,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         if (a < dim) {
             un[a] = ui[a] + ph.dt * ((b.Ff[3 * i + a] + acc[a]) * im + ph.g[a]);
             xn[a] = xi[a] + ph.dt * un[a];
-            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] * (1.0 / g.n[a]));
+            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] * g.inv_n[a]);
         } else {
             un[a] = ui[a];
             xn[a] = xi[a];
@@ -613,7 +616,11 @@ extern "C" lbm_status dem_create(const dem_params *p, lbm_ctx *fluid, dem_ctx **
     d->p = *p;
     d->fl = fluid;
     d->g.dim = fluid->dim;
-    for (int a = 0; a < 3; ++a) { d->g.n[a] = fluid->g.n[a]; d->g.periodic[a] = fluid->g.periodic[a]; }
+    for (int a = 0; a < 3; ++a) {
+        d->g.n[a] = fluid->g.n[a];
+        d->g.periodic[a] = fluid->g.periodic[a];
+        d->g.inv_n[a] = 1.0 / fluid->g.n[a];
+    }
     d->g.skin = p->skin > 0 ? p->skin : 0.5;
     d->ph.Es = (float)(p->E / (2.0 * (1.0 - p->poisson * p->poisson)));
     d->ph.Gs = (float)(p->E / (4.0 * (2.0 - p->poisson) * (1.0 + p->poisson)));
