@@ -97,7 +97,7 @@ static void free_dev(void **p) {
 static void free_particles(lbm_ctx *ctx) {
     free_dev((void **)&ctx->dX); free_dev((void **)&ctx->dU); free_dev((void **)&ctx->dOm);
     free_dev((void **)&ctx->dR); free_dev((void **)&ctx->dFr); free_dev((void **)&ctx->dF);
-    free_dev((void **)&ctx->dT);
+    free_dev((void **)&ctx->dT); free_dev((void **)&ctx->dPf);
     ctx->np_cap = 0;
 }
 
@@ -240,6 +240,7 @@ Parts ctx_parts(lbm_ctx *ctx) {
     Parts pd;
     pd.n = ctx->np; pd.X = ctx->dX; pd.U = ctx->dU; pd.Om = ctx->dOm; pd.R = ctx->dR; pd.Fr = ctx->dFr;
     pd.F = ctx->dF; pd.T = ctx->dT;
+    pd.Pf = ctx->dPf;
     return pd;
 }
 
@@ -292,6 +293,7 @@ lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n) {
     CK(cudaMalloc(&ctx->dFr, s), "cudaMalloc(f(r))");
     CK(cudaMalloc(&ctx->dF, v), "cudaMalloc(F)");
     CK(cudaMalloc(&ctx->dT, v), "cudaMalloc(T)");
+    CK(cudaMalloc(&ctx->dPf, (size_t)n * 2 * sizeof(float4)), "cudaMalloc(FP32 record data)");
     CK(cudaMemsetAsync(ctx->dF, 0, v, ctx->stream), "memset F");
     CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
     ctx->np_cap = n;

@@ -23,6 +23,7 @@ struct lbm_ctx {
     // particles (FP64, device)
     int np, np_cap;
     double *dX, *dU, *dOm, *dR, *dFr, *dF, *dT;
+    float4 *dPf;               // FP32 record data per particle (binning kernel)
     double rmax;
 
     // tile candidate lists

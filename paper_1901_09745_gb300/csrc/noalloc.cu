@@ -137,6 +137,7 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     Parts pd;
     pd.n = n; pd.X = X; pd.U = U; pd.Om = Omega; pd.R = radius; pd.Fr = (double *)(base + o_fr);
     pd.F = F; pd.T = T;
+    pd.Pf = nullptr;
 
     // what must start at zero: tile counts, stats, flags (the rest is fully rewritten)
     e = cudaMemsetAsync(base, 0, o_list, s);

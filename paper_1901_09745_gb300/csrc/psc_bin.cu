@@ -32,28 +32,38 @@ __device__ __forceinline__ int axis_tile_ranges(long long lo, long long hi, int 
 
 __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= pd.n) return;
-    for (int c = 0; c < 3; ++c) { pd.F[3 * p + c] = 0.0; pd.T[3 * p + c] = 0.0; }
-    int ra[3][2], rb[3][2], nr[3];
-    const double r = pd.R[p];
-    for (int ax = 0; ax < 3; ++ax) {
-        if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; continue; }
-        const double X = pd.X[3 * p + ax];
-        const long long lo = (long long)ceil(X - r - h), hi = (long long)floor(X + r + h);
-        nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
+    int mx = 0;   // largest slot taken by this thread
+    if (p < pd.n) {
+        for (int c = 0; c < 3; ++c) { pd.F[3 * p + c] = 0.0; pd.T[3 * p + c] = 0.0; }
+        if (pd.Pf) {   // FP32 record data, converted once per particle
+            pd.Pf[2 * p] = make_float4((float)pd.R[p], (float)pd.Fr[p], (float)pd.U[3 * p], (float)pd.U[3 * p + 1]);
+            pd.Pf[2 * p + 1] = make_float4((float)pd.U[3 * p + 2], (float)pd.Om[3 * p], (float)pd.Om[3 * p + 1],
+                                           (float)pd.Om[3 * p + 2]);
+        }
+        int ra[3][2], rb[3][2], nr[3];
+        const double r = pd.R[p];
+        for (int ax = 0; ax < 3; ++ax) {
+            if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; continue; }
+            const double X = pd.X[3 * p + ax];
+            const long long lo = (long long)ceil(X - r - h), hi = (long long)floor(X + r + h);
+            nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
+        }
+        for (int iz = 0; iz < nr[2]; ++iz)
+        for (int tz = ra[2][iz]; tz <= rb[2][iz]; ++tz)
+        for (int iy = 0; iy < nr[1]; ++iy)
+        for (int ty = ra[1][iy]; ty <= rb[1][iy]; ++ty)
+        for (int ix = 0; ix < nr[0]; ++ix)
+        for (int tx = ra[0][ix]; tx <= rb[0][ix]; ++tx) {
+            const long long tile = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+            const int slot = atomicAdd(&tl.count[tile], 1);
+            if (slot < tl.cap) tl.list[tile * tl.cap + slot] = p;
+            else if (slot == tl.cap) atomicAdd(&tl.stats[0], 1);
+            mx = max(mx, slot + 1);
+        }
     }
-    for (int iz = 0; iz < nr[2]; ++iz)
-    for (int tz = ra[2][iz]; tz <= rb[2][iz]; ++tz)
-    for (int iy = 0; iy < nr[1]; ++iy)
-    for (int ty = ra[1][iy]; ty <= rb[1][iy]; ++ty)
-    for (int ix = 0; ix < nr[0]; ++ix)
-    for (int tx = ra[0][ix]; tx <= rb[0][ix]; ++tx) {
-        const long long tile = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
-        const int slot = atomicAdd(&tl.count[tile], 1);
-        if (slot < tl.cap) tl.list[tile * tl.cap + slot] = p;
-        else if (slot == tl.cap) atomicAdd(&tl.stats[0], 1);
-        atomicMax(&tl.stats[1], slot + 1);
-    }
+    // the largest count: one atomic per warp, not per (particle, tile)
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&tl.stats[1], mx);
 }
 
 // Eq. 18 with V_a of Eq. 17 (3D) or Eq. 19 (2D), the integrand read as the sphere (disc)

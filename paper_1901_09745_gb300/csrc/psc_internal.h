@@ -49,6 +49,8 @@ struct Parts {
     int n;
     const double *X, *U, *Om, *R, *Fr;   // n x 3, n x 3, n x 3, n, n (f(r) of Eq. 18)
     double *F, *T;                       // n x 3 each
+    float4 *Pf;                          // optional [n][2]: {r, f(r), Ux, Uy}, {Uz, Ox, Oy, Oz} in
+                                         // FP32, written by the binning kernel for the records
 };
 
 enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };

@@ -271,10 +271,17 @@ __device__ __forceinline__ void write_record(T *rec, const Geom &g, const Parts 
         }
         rec[R_PX + a] = rel;
     }
-    rec[R_R] = (T)pd.R[id];
-    rec[R_FR] = (T)pd.Fr[id];
-    rec[R_UX] = (T)pd.U[3 * id + 0]; rec[R_UY] = (T)pd.U[3 * id + 1]; rec[R_UZ] = (T)pd.U[3 * id + 2];
-    rec[R_OX] = (T)pd.Om[3 * id + 0]; rec[R_OY] = (T)pd.Om[3 * id + 1]; rec[R_OZ] = (T)pd.Om[3 * id + 2];
+    if (sizeof(T) == 4 && pd.Pf) {   // FP32 records: the per-particle copy, no conversions here
+        const float4 a = pd.Pf[2 * id], b = pd.Pf[2 * id + 1];
+        rec[R_R] = (T)a.x; rec[R_FR] = (T)a.y;
+        rec[R_UX] = (T)a.z; rec[R_UY] = (T)a.w; rec[R_UZ] = (T)b.x;
+        rec[R_OX] = (T)b.y; rec[R_OY] = (T)b.z; rec[R_OZ] = (T)b.w;
+    } else {
+        rec[R_R] = (T)pd.R[id];
+        rec[R_FR] = (T)pd.Fr[id];
+        rec[R_UX] = (T)pd.U[3 * id + 0]; rec[R_UY] = (T)pd.U[3 * id + 1]; rec[R_UZ] = (T)pd.U[3 * id + 2];
+        rec[R_OX] = (T)pd.Om[3 * id + 0]; rec[R_OY] = (T)pd.Om[3 * id + 1]; rec[R_OZ] = (T)pd.Om[3 * id + 2];
+    }
     rec[R_ID] = id_bits<T>(id);
 }
 
