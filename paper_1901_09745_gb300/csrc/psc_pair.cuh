@@ -409,7 +409,7 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
 // the counters for the next launch. Tiles with more than kPairCap candidates are left to
 // k_collide_overflow.
 template <class L, typename S, int PSC>
-__global__ void __launch_bounds__(kPThreads, (sizeof(typename Store<S>::T) == 8) ? 2 : ((L::Q == 9) ? 6 : 4))
+__global__ void __launch_bounds__(kPThreads, (sizeof(typename Store<S>::T) == 8) ? 2 : ((L::Q == 9) ? 7 : 4))
 k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
                  PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
     using T = typename Store<S>::T;
