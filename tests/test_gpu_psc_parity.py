@@ -220,6 +220,31 @@ def test_c3_dense_subrun_64cube_200_steps(P):
     _check(compare(g, o, 3), TOL32)
 
 
+def test_c5_channel_subbox_20_steps(P):
+    """D3Q19 64^3 channel sub-box of the 512^3 workload (walls in z, tau 0.55, polydisperse
+    spheres r ~ U(3, 8) at the same solid fraction, velocities N(0, 1e-3)), 20 steps from a
+    perturbed state, FP32: the mobile-particle protocol of the 3D channel."""
+    w = synth.workload("c5", scale=0.125)
+    case = dict(lattice=19, n=w["n"], bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                X=w["X"], U=w["U"], Om=w["Om"], r=w["r"])
+    f0 = perturbed_state(case, 10)
+    o = run_oracle(case, f0, 20)
+    g = run_gpu(P, case, f0, 20, storage="f32")
+    assert g["info"]["overflow_tiles"] == 0
+    _check(compare(g, o, 3), TOL32)
+
+
+def test_c4_subrun_64cube_100_steps(P):
+    """D3Q19 64^3 periodic sub-run of the 128^3 adjoint workload (static spheres r = 5 at
+    the same solid fraction, tau 0.7, body force 1e-6), 100 steps from rest, FP32."""
+    w = synth.workload("c4", scale=0.5)
+    case = dict(lattice=19, n=w["n"], bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                X=w["X"], U=w["U"], Om=w["Om"], r=w["r"])
+    o = run_oracle(case, perturbed_state(case, 0, amp=0.0), 100)
+    g = run_gpu(P, case, None, 100, storage="f32")
+    _check(compare(g, o, 3), TOL32)
+
+
 def test_c2_full_size_one_step(P):
     """The 2048^2 channel with 5000 discs in the launch configuration the benchmark times:
     one step from a seeded perturbed state, every cell and every particle compared."""

@@ -79,3 +79,22 @@ def test_c2_subbox_reduced_storage(P):
     for st in ("f16", "bf16"):
         for k, b in BOUND[st].items():
             assert errs[st][k] < b, (st, k, errs[st][k])
+
+
+def test_c5_channel_subbox_reduced_storage(P):
+    """The 512^3 channel's own storage form (FP16 deviations) on its 64^3 sub-box: walls in
+    z, polydisperse moving spheres, 20 steps from a perturbed state; FP32, FP16 and BF16
+    against FP64."""
+    w = synth.workload("c5", scale=0.125)
+    case = dict(lattice=19, n=w["n"], bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                X=w["X"], U=w["U"], Om=w["Om"], r=w["r"])
+    f0 = perturbed_state(case, 11)
+    o = run_oracle(case, f0, 20)
+    errs = {}
+    for st in ("f32", "f16", "bf16"):
+        g = run_gpu(P, case, f0, 20, storage=st)
+        errs[st] = compare(g, o, 3)
+    _report("c5 64^3 channel 20 steps", errs)
+    for st in ("f16", "bf16"):
+        for k, b in BOUND[st].items():
+            assert errs[st][k] < b, (st, k, errs[st][k])
