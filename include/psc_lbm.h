@@ -220,7 +220,7 @@ lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
  *           double / float / half / bfloat16 (FP16 scaled by dev_scale, default 4096), the
  *           bytes lbm_save_state writes after its 64-byte header.
  *   f_out   device buffer of the same size receiving the state after the step (must not
- *           alias f_in).
+ *           alias f_in). Each buffer must be aligned to its element size.
  *   n, X, U, Omega, radius   particles as for lbm_set_particles, but device pointers; the
  *           caller guarantees the radius and box-size conditions stated there (the device
  *           data is not inspected on the host).

@@ -107,6 +107,51 @@ __device__ __forceinline__ void pair_flush(const int cnt, const T *recs, const T
     }
 }
 
+// The lane's two cells, tile-relative: one column (the lane), both of the warp's rows.
+template <class L>
+struct PairCells {
+    int xA, xB, yA, yB, zA, zB;
+    __device__ __forceinline__ PairCells(const int lane, const int warp) {
+        xA = xB = lane;
+        yA = (L::D == 2) ? 2 * warp : warp;
+        yB = (L::D == 2) ? 2 * warp + 1 : warp;
+        zA = 0;
+        zB = (L::D == 2) ? 0 : 1;
+    }
+};
+
+// Pull of the lane's two cells (raw values for 16-bit storage, which folds its scale).
+template <class L, typename S>
+__device__ __forceinline__ void pull_pair(const S *__restrict__ fin, const Geom &g, const PhysT<typename Store<S>::T> &ph,
+                                          const bool interior, const int xA, const int xB, const int yA,
+                                          const int yB, const int zA, const int zB, const long long cellA,
+                                          const long long cellB, const bool actA, const bool actB,
+                                          typename Store<S>::T *da, typename Store<S>::T *db) {
+    constexpr bool SC = Store<S>::kScaled;
+    if (interior) {     // both cells with the same fixed offsets (one copy of the load code)
+        const long long N = g.ncell, sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
+        const S *ba = fin + cellA, *bb = fin + cellB;
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
+            da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
+            db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
+        }
+        return;
+    }
+    pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da);
+    pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db);
+}
+
+// Store of velocity i at the lane's two cells (values already scaled for 16-bit storage).
+template <typename S>
+__device__ __forceinline__ void store_pair(S *__restrict__ fout, const long long iA, const long long iB,
+                                           const typename Store<S>::T a, const typename Store<S>::T b,
+                                           const bool actA, const bool actB) {
+    if (actA) Store<S>::str(fout, iA, a);
+    if (actB) Store<S>::str(fout, iB, b);
+}
+
 template <class L> constexpr int pair_nslot() { return (L::D == 2) ? 4 : 2; }
 
 template <class L, typename T> __host__ __device__ constexpr size_t pair_smem_bytes() {
@@ -139,15 +184,16 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     const int z0 = (int)tz * L::TZ;
     const int lane = threadIdx.x, warp = threadIdx.y;
     const int tid = lane + 32 * warp;
-    // the warp's two rows, tile-relative
+    // the warp's two rows, tile-relative (the candidate row test covers both)
     const int ryA = (L::D == 2) ? 2 * warp : warp, ryB = (L::D == 2) ? 2 * warp + 1 : warp;
     const int rzA = 0, rzB = (L::D == 2) ? 0 : 1;
-    const int x = x0 + lane;
-    const int yA = y0 + ryA, yB = y0 + ryB, zA = z0 + rzA, zB = z0 + rzB;
-    const bool actA = x < g.n[0] && yA < g.n[1] && zA < g.n[2];
-    const bool actB = x < g.n[0] && yB < g.n[1] && zB < g.n[2];
-    const long long cellA = x + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
-    const long long cellB = x + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
+    const PairCells<L> pc(lane, warp);
+    const int xA = x0 + pc.xA, xB = x0 + pc.xB;
+    const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
+    const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
+    const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
+    const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
+    const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
     const long long N = g.ncell;
     const T *recs = reinterpret_cast<const T *>(tl.blocks) + (size_t)tile * block_elems<T>(cap) + head_elems<T>();
 
@@ -168,19 +214,7 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     // sums unscaled once, and the outputs are formed scaled (s folded into the weights)
     constexpr bool SC = Store<S>::kScaled;
     T da[Q], db[Q];
-    if (interior) {     // both cells with the same fixed offsets (one copy of the load code)
-        const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-        const S *ba = fin + cellA, *bb = fin + cellB;
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
-            da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
-            db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
-        }
-    } else {
-        pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, false, actA, ph.sc, da);
-        pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, false, actB, ph.sc, db);
-    }
+    pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
     V df[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -219,16 +253,16 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     pair_flush<L, T>(prev_cnt, prev_recs, prev_part, prev_mask, pd, tid);
 
     // ---- candidates that can reach either row (one lane per candidate, ballot)
-    const T cx = (T)lane;
-    const T cyA = (T)ryA, cyB = (T)ryB, czA = (T)rzA, czB = (T)rzB;
+    const T cxA = (T)pc.xA, cxB = (T)pc.xB;
+    const T cyA = (T)pc.yA, cyB = (T)pc.yB, czA = (T)pc.zA, czB = (T)pc.zB;
     const T xmax = (T)(min(L::TX, g.n[0] - x0) - 1);
     unsigned wmask;
     {
         bool rel = false;
         if (lane < cnt) {
             const Vec4<T> a = ld4<T>(srec + lane * RW);
-            rel = row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, cyA, czA, xmax) ||
-                  row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, cyB, czB, xmax);
+            rel = row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, (T)ryA, (T)rzA, xmax) ||
+                  row_hits<L, T>(g, a.x, a.y, a.z, a.w + ph.h, (T)ryB, (T)rzB, xmax);
         }
         wmask = __ballot_sync(kFull, rel);
     }
@@ -243,8 +277,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
         const Vec4<T> a = ld4<T>(rk);           // px, py, pz, r
         const Vec4<T> f = ld4<T>(rk + 4);       // f(r), Ux, Uy, Uz
         T dxa, dya, dza, dxb, dyb, dzb;
-        cand_arm<L, T>(g, cx, cyA, czA, a.x, a.y, a.z, dxa, dya, dza);
-        cand_arm<L, T>(g, cx, cyB, czB, a.x, a.y, a.z, dxb, dyb, dzb);
+        cand_arm<L, T>(g, cxA, cyA, czA, a.x, a.y, a.z, dxa, dya, dza);
+        cand_arm<L, T>(g, cxB, cyB, czB, a.x, a.y, a.z, dxb, dyb, dzb);
         const T ea = actA ? shell_eps<T>(dxa * dxa + dya * dya + dza * dza, a.w, f.x, ph.h) : (T)0;
         const T eb = actB ? shell_eps<T>(dxb * dxb + dyb * dyb + dzb * dzb, a.w, f.x, ph.h) : (T)0;
         if (ea > (T)0 || eb > (T)0) {
@@ -364,8 +398,7 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
                 X = P::add(X, t);
             }
             const V out = P::fma(a1, df[i], P::fma(Bn, df[o], P::mul(P::sp(w * ssc), X)));
-            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
-            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
+            store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
         }
     }
 
@@ -477,8 +510,7 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
     const uint2 *list = (np > 0) ? tl.order + ntiles : nullptr;
     const long long N = g.ncell;
     const int lane = threadIdx.x, warp = threadIdx.y;
-    const int ryA = (L::D == 2) ? 2 * warp : warp, ryB = (L::D == 2) ? 2 * warp + 1 : warp;
-    const int rzA = 0, rzB = (L::D == 2) ? 0 : 1;
+    const PairCells<L> pc(lane, warp);
     for (int it = (np > 0) ? (int)blockIdx.x : 0; it < nf; it += gridDim.x) {
         int x0, y0, z0;
         if (list) {
@@ -490,29 +522,17 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
         } else {
             x0 = blockIdx.x * L::TX; y0 = blockIdx.y * L::TY; z0 = blockIdx.z * L::TZ;
         }
-        const int x = x0 + lane;
-        const int yA = y0 + ryA, yB = y0 + ryB, zA = z0 + rzA, zB = z0 + rzB;
-        const bool actA = x < g.n[0] && yA < g.n[1] && zA < g.n[2];
-        const bool actB = x < g.n[0] && yB < g.n[1] && zB < g.n[2];
-        const long long cellA = x + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
-        const long long cellB = x + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
+        const int xA = x0 + pc.xA, xB = x0 + pc.xB;
+        const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
+        const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
+        const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
+        const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
+        const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
         const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
                               (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
         constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
         T da[Q], db[Q];
-        if (interior) {     // both cells with the same fixed offsets (one copy of the load code)
-            const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
-            const S *ba = fin + cellA, *bb = fin + cellB;
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
-                da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
-                db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
-            }
-        } else {
-            pull_q<L, S, SC>(fin, g, x, yA, zA, cellA, false, actA, ph.sc, da);
-            pull_q<L, S, SC>(fin, g, x, yB, zB, cellB, false, actB, ph.sc, db);
-        }
+        pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
         V df[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -560,8 +580,7 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
                 const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
                 out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
             }
-            if (actA) Store<S>::str(fout, (long long)i * N + cellA, out.x);
-            if (actB) Store<S>::str(fout, (long long)i * N + cellB, out.y);
+            store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
         }
     }
 }

@@ -10,6 +10,7 @@ import pytest
 
 import synth
 from parity_utils import compare, perturbed_state, run_gpu, run_oracle
+from parity_utils import ragged_case2d as _case2d, ragged_case3d as _case3d
 
 pytestmark = pytest.mark.gpu
 
@@ -33,35 +34,6 @@ def _check(err, tol):
     for k, v in tol.items():
         if k in err:
             assert err[k] <= v, "%s rel L2 %.3e > %.1e (all: %s)" % (k, err[k], v, err)
-
-
-def _case2d(psc=0, bc=(0, 1, 0), n=(77, 45, 1)):
-    rng = np.random.default_rng(21)
-    X = np.array([[3.2, 20.5, 0], [75.6, 22.0, 0], [30.1, 4.3, 0], [38.9, 9.6, 0],
-                  [55.0, 38.7, 0], [61.3, 30.2, 0], [12.4, 36.1, 0]], dtype=float)
-    r = np.array([5.5, 4.2, 4.0, 5.1, 4.4, 6.0, 3.3])
-    # 0-1 overlap across the periodic x faces (fractions summing above one); 4-5 share
-    # cells 0.18 lu apart. The original scheme diverges where fractions overlap (its B_n
-    # exceeds one), so its cases move particle 1 to a 0.6 lu gap.
-    if psc == 1:
-        X[1, 0] = 70.0
-    U = np.zeros((7, 3)); U[:, :2] = rng.normal(0, 2e-3, (7, 2))
-    Om = np.zeros((7, 3)); Om[:, 2] = rng.normal(0, 5e-4, 7)
-    return dict(lattice=9, n=n, bc=bc, tau=0.7, body_force=(2e-5, -5e-6, 0.0), X=X, U=U, Om=Om,
-                r=r, psc=psc)
-
-
-def _case3d(psc=0, bc=(0, 0, 1), n=(45, 29, 23)):
-    rng = np.random.default_rng(22)
-    X = np.array([[2.1, 14.0, 11.2], [43.5, 6.2, 9.1], [20.2, 12.5, 4.6], [26.9, 14.1, 6.1],
-                  [33.3, 27.6, 15.5], [12.0, 0.4, 17.8]], dtype=float)
-    r = np.array([4.5, 3.8, 4.0, 3.9, 5.0, 4.2])   # 2-3 overlap; 0, 1, 4, 5 cross faces
-    if psc == 1:
-        X[3, 0] = 27.9    # 2-3 at a 0.1 lu gap for the original scheme
-    U = rng.normal(0, 2e-3, (6, 3))
-    Om = rng.normal(0, 5e-4, (6, 3))
-    return dict(lattice=19, n=n, bc=bc, tau=0.62, body_force=(1e-5, 2e-6, -3e-6), X=X, U=U, Om=Om,
-                r=r, psc=psc)
 
 
 def fp32_horizon_tol(o, steps, lattice):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity_utils import compare, perturbed_state, run_gpu, run_oracle
+from parity_utils import compare, perturbed_state, ragged_case2d, ragged_case3d, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -98,3 +98,21 @@ def test_c5_channel_subbox_reduced_storage(P):
     for st in ("f16", "bf16"):
         for k, b in BOUND[st].items():
             assert errs[st][k] < b, (st, k, errs[st][k])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_ragged_reduced_storage(P, storage, dim):
+    """16-bit storage on the ragged parity cases: partial tiles on every axis, walls,
+    periodic faces, moving particles that share cells; FP32 and the 16-bit form against
+    FP64."""
+    case = ragged_case2d() if dim == 2 else ragged_case3d()
+    steps = 25 if dim == 2 else 15
+    f0 = perturbed_state(case, 3)
+    o = run_oracle(case, f0, steps)
+    g32 = run_gpu(P, case, f0, steps, storage="f32")
+    g = run_gpu(P, case, f0, steps, storage=storage)
+    errs = {"f32": compare(g32, o, dim), storage: compare(g, o, dim)}
+    _report("ragged %dD %s %d steps" % (dim, "x".join(map(str, case["n"][:dim])), steps), errs)
+    for k, b in BOUND[storage].items():
+        assert errs[storage][k] < b, (storage, k, errs[storage][k])
