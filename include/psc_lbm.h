@@ -145,11 +145,14 @@ lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, doub
  * collide-stream launches. Synchronises the stream. */
 lbm_status lbm_get_info(lbm_ctx *ctx, long long *out, int n);
 
-/* Optional CUDA-event timing of every fused collide-stream launch (used by the benchmark
+/* Optional CUDA-event timing of the fused collide-stream launches (used by the benchmark
  * to measure the kernel's own duration inside a timed run). A call returns, in *ms_total
  * and *launches (either may be NULL), the summed device time and the number of launches
- * timed since the previous call, synchronising the stream, then enables (enable = 1) or
- * disables timing for the launches that follow. */
+ * timed since the previous call, synchronising the stream, then times every enable-th
+ * step that follows (enable = 1: every step; 0: none). lbm_step replays each step from a
+ * CUDA graph (captured on first use and whenever lbm_set_particles or lbm_set_body_force
+ * changed what it reads); a timed step is queued kernel by kernel instead, with an event
+ * on either side of the collide-stream kernels. */
 lbm_status lbm_kernel_timing(lbm_ctx *ctx, int enable, double *ms_total, long long *launches);
 
 /* ------------------------------------------------------------------ DEM (Sec. 2.5) --- */
@@ -227,8 +230,10 @@ lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
  *   F, T    device buffers (n x 3) receiving the force and torque of this step.
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture. The call is
- * asynchronous on p->stream; device-side instability is not reported by this entry point.
+ * and creates a second stream and two events there (a D2Q9 step runs two kernels side by
+ * side, forked from p->stream and joined back into it), with that device current; make
+ * that first call before any stream capture. The call is asynchronous on p->stream;
+ * device-side instability is not reported by this entry point.
  * Every call shares the one array and finds whatever the previous call left there: each
  * call clears what must start at zero, but calls that overlap on the GPU (different streams
  * or host threads at the same time) corrupt each other's results — serialise them. */

@@ -15,10 +15,14 @@
 #include "psc_internal.h"
 
 namespace psc {
-cudaError_t launch_collide_stream_f64(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
-cudaError_t launch_collide_stream_f32(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
-cudaError_t launch_collide_stream_f16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
-cudaError_t launch_collide_stream_bf16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t);
+cudaError_t launch_collide_stream_f64(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
+                                     const Overlap *);
+cudaError_t launch_collide_stream_f32(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
+                                     const Overlap *);
+cudaError_t launch_collide_stream_f16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
+                                     const Overlap *);
+cudaError_t launch_collide_stream_bf16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
+                                     const Overlap *);
 cudaError_t launch_gather_f64(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f32(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f16(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
@@ -30,12 +34,12 @@ cudaError_t launch_set_bf16(int, const double *, void *, const Geom &, const Phy
 
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout, const Geom &g,
                                   const Phys &ph, const Tiles &tl, const Parts &pd, int *flags,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, const Overlap *ov) {
     switch (storage) {
-    case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s);
-    case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s);
-    case ST_F16: return launch_collide_stream_f16(lattice, fin, fout, g, ph, tl, pd, flags, s);
-    default: return launch_collide_stream_bf16(lattice, fin, fout, g, ph, tl, pd, flags, s);
+    case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    case ST_F16: return launch_collide_stream_f16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    default: return launch_collide_stream_bf16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
     }
 }
 cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out, double *rho, double *u,
@@ -198,6 +202,10 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
         e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
         ctx->own_stream = 1;
     }
+    // the second stream of the 2D step (fluid and particle tiles side by side)
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->ov.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.join, cudaEventDisableTiming);
     size_t bytes = (size_t)g.ncell * ctx->q * ctx->elem;
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[1], bytes);
@@ -231,6 +239,12 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     free_dev(&ctx->adj);
     for (int i = 0; i < ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
     free(ctx->ev);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            if (ctx->sgraph[a][b]) cudaGraphExecDestroy(ctx->sgraph[a][b]);
+    if (ctx->ov.aux) cudaStreamDestroy(ctx->ov.aux);
+    if (ctx->ov.fork) cudaEventDestroy(ctx->ov.fork);
+    if (ctx->ov.join) cudaEventDestroy(ctx->ov.join);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return LBM_OK;
@@ -257,7 +271,9 @@ static Tiles ctx_tiles(lbm_ctx *ctx) {
 void ctx_update_wrap(lbm_ctx *ctx) {
     for (int a = 0; a < 3; ++a) {
         double need = ctx->g.t[a] + 2.0 * (ctx->rmax + ctx->p.shell_h) + 2.0;
-        ctx->g.wrap_img[a] = (a < ctx->dim && ctx->g.periodic[a] && ctx->g.n[a] < need) ? 1 : 0;
+        const int w = (a < ctx->dim && ctx->g.periodic[a] && ctx->g.n[a] < need) ? 1 : 0;
+        if (w != ctx->g.wrap_img[a]) ctx->gen += 1;     // the step's kernels take Geom by value
+        ctx->g.wrap_img[a] = w;
     }
 }
 
@@ -284,6 +300,7 @@ lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n) {
 
 lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n) {
     if (n <= ctx->np_cap) return LBM_OK;
+    ctx->gen += 1;      // new buffers: the step's graph is captured again
     free_particles(ctx);
     size_t v = (size_t)n * 3 * sizeof(double), s = (size_t)n * sizeof(double);
     CK(cudaMalloc(&ctx->dX, v), "cudaMalloc(X)");
@@ -302,6 +319,7 @@ lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n) {
 
 static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
     if (ctx->tile_count) return LBM_OK;
+    ctx->gen += 1;
     CK(cudaMalloc(&ctx->tile_count, (size_t)ctx->ntiles * sizeof(int)), "cudaMalloc(tile counts)");
     CK(cudaMalloc(&ctx->tile_list, (size_t)ctx->ntiles * ctx->p.tile_cap * sizeof(int)), "cudaMalloc(tile lists)");
     CK(cudaMalloc(&ctx->tile_stats, kTileStats * sizeof(int)), "cudaMalloc(tile stats)");
@@ -360,22 +378,22 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
     return LBM_OK;
 }
 
-lbm_status ctx_bin(lbm_ctx *ctx) {
-    if (ctx->np <= 0) return LBM_OK;
+// Queue the binning of the particles into the tiles' candidate lists (no host state).
+static lbm_status ctx_enqueue_bin(lbm_ctx *ctx) {
     Tiles tl = ctx_tiles(ctx);
     CK(cudaMemsetAsync(ctx->tile_count, 0, (size_t)ctx->ntiles * sizeof(int), ctx->stream), "memset tile counts");
     CK(cudaMemsetAsync(ctx->tile_stats, 0, kTileStats * sizeof(int), ctx->stream), "memset tile stats");
     CK(launch_bin(ctx->dim, ctx->g, ctx->ph, tl, ctx_parts(ctx), ctx->stream), "bin kernel");
     CK(launch_pack(ctx->q, ctx->p.storage == LBM_F64, ctx->g, tl, ctx_parts(ctx), ctx->ntiles, ctx->stream), "pack kernel");
-    ctx->launches += 2;
-    ctx->bins_valid = 1;
     return LBM_OK;
 }
 
-lbm_status ctx_step_once(lbm_ctx *ctx) {
+// Queue one step (binning or zeroed forces, then the collide-stream kernels); ev, when
+// given, brackets the collide-stream kernels.
+static lbm_status ctx_enqueue_step(lbm_ctx *ctx, bool bin, cudaEvent_t *ev) {
     if (ctx->np > 0) {
-        if (!ctx->bins_valid) {
-            lbm_status st = ctx_bin(ctx);
+        if (bin) {
+            lbm_status st = ctx_enqueue_bin(ctx);
             if (st != LBM_OK) return st;
         } else {
             size_t v = (size_t)ctx->np * 3 * sizeof(double);
@@ -383,25 +401,77 @@ lbm_status ctx_step_once(lbm_ctx *ctx) {
             CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
         }
     }
-    cudaEvent_t *ev = NULL;
-    if (ctx->timing) {
-        if (ctx->ev_used + 2 > ctx->ev_cap) {
-            int cap = ctx->ev_cap ? 2 * ctx->ev_cap : 256;
-            cudaEvent_t *nev = (cudaEvent_t *)realloc(ctx->ev, sizeof(cudaEvent_t) * cap);
-            if (!nev) { ctx_error(ctx, "host allocation failed"); return LBM_ERR_OOM; }
-            ctx->ev = nev;
-            for (int i = ctx->ev_cap; i < cap; ++i) CK(cudaEventCreate(&ctx->ev[i]), "cudaEventCreate");
-            ctx->ev_cap = cap;
-        }
-        ev = &ctx->ev[ctx->ev_used];
-        ctx->ev_used += 2;
-        CK(cudaEventRecord(ev[0], ctx->stream), "cudaEventRecord");
-    }
+    if (ev) CK(cudaEventRecord(ev[0], ctx->stream), "cudaEventRecord");
     CK(launch_collide_stream(ctx->p.storage, ctx->q, ctx->f[ctx->cur], ctx->f[ctx->cur ^ 1], ctx->g, ctx->ph,
-                             ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream),
+                             ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream, &ctx->ov),
        "collide-stream kernel");
     if (ev) CK(cudaEventRecord(ev[1], ctx->stream), "cudaEventRecord");
-    ctx->launches += (ctx->np > 0) ? 3 : 1;   // fluid tiles, particle tiles, overflow tiles
+    return LBM_OK;
+}
+
+// Replay one step from its CUDA graph, capturing it first when its key changed. Returns
+// LBM_OK with *done = false when the stream is being captured by the caller (the step is
+// then queued directly).
+static lbm_status ctx_step_graph(lbm_ctx *ctx, bool bin, bool *done) {
+    *done = false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs), "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return LBM_OK;
+    const void *key[10] = {(const void *)(size_t)ctx->gen, ctx->dX, ctx->dU, ctx->dOm, ctx->dR, ctx->dF,
+                           ctx->dT, ctx->dFr, ctx->dPf, (const void *)(size_t)ctx->np};
+    const int a = ctx->cur, b = bin ? 1 : 0;
+    bool same = ctx->sgraph[a][b] != NULL;
+    for (int k = 0; same && k < 10; ++k) same = (ctx->sgkey[a][b][k] == key[k]);
+    if (!same) {
+        if (ctx->sgraph[a][b]) { cudaGraphExecDestroy(ctx->sgraph[a][b]); ctx->sgraph[a][b] = NULL; }
+        cudaGraph_t graph = NULL;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        lbm_status st = ctx_enqueue_step(ctx, bin, NULL);
+        cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        if (st != LBM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        CK(ec, "cudaStreamEndCapture");
+        cudaError_t ei = cudaGraphInstantiate(&ctx->sgraph[a][b], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei, "cudaGraphInstantiate");
+        for (int k = 0; k < 10; ++k) ctx->sgkey[a][b][k] = key[k];
+    }
+    CK(cudaGraphLaunch(ctx->sgraph[a][b], ctx->stream), "cudaGraphLaunch");
+    *done = true;
+    return LBM_OK;
+}
+
+lbm_status ctx_step_once(lbm_ctx *ctx) {
+    const bool bin = ctx->np > 0 && !ctx->bins_valid;
+    const bool timed = ctx->timing > 0 && ctx->steps % ctx->timing == 0;
+    bool done = false;
+    if (!timed) {
+        // the usual path: one graph launch per step
+        lbm_status st = ctx_step_graph(ctx, bin, &done);
+        if (st != LBM_OK) return st;
+    }
+    if (!done) {
+        cudaEvent_t *ev = NULL;
+        if (timed) {
+            if (ctx->ev_used + 2 > ctx->ev_cap) {
+                int cap = ctx->ev_cap ? 2 * ctx->ev_cap : 256;
+                cudaEvent_t *nev = (cudaEvent_t *)realloc(ctx->ev, sizeof(cudaEvent_t) * cap);
+                if (!nev) { ctx_error(ctx, "host allocation failed"); return LBM_ERR_OOM; }
+                ctx->ev = nev;
+                for (int i = ctx->ev_cap; i < cap; ++i) CK(cudaEventCreate(&ctx->ev[i]), "cudaEventCreate");
+                ctx->ev_cap = cap;
+            }
+            ev = &ctx->ev[ctx->ev_used];
+            ctx->ev_used += 2;
+        }
+        lbm_status st = ctx_enqueue_step(ctx, bin, ev);
+        if (st != LBM_OK) return st;
+    }
+    if (bin) {
+        ctx->launches += 2;
+        ctx->bins_valid = 1;
+    }
+    // all tiles (2D: particle and fluid tiles), overflow tiles
+    ctx->launches += (ctx->np > 0) ? ((ctx->q == 9 && ctx->p.storage != LBM_F64) ? 3 : 2) : 1;
     ctx->cs_launches += 1;
     ctx->cur ^= 1;
     ctx->steps += 1;
@@ -557,6 +627,7 @@ extern "C" lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F) {
     for (int a = 0; a < 3; ++a)
         if (!isfinite(F[a])) { ctx_error(ctx, "body force must be finite"); return LBM_ERR_ARG; }
     for (int a = 0; a < 3; ++a) { ctx->p.body_force[a] = F[a]; ctx->ph.body_force[a] = F[a]; }
+    ctx->gen += 1;
     return LBM_OK;
 }
 
@@ -586,6 +657,6 @@ extern "C" lbm_status lbm_kernel_timing(lbm_ctx *ctx, int enable, double *ms_tot
         if (launches) *launches = ctx->ev_used / 2;
     }
     ctx->ev_used = 0;   // every query (or toggle) starts a new timing window
-    ctx->timing = enable ? 1 : 0;
+    ctx->timing = enable > 0 ? enable : 0;
     return LBM_OK;
 }

@@ -16,6 +16,7 @@ struct lbm_ctx {
     void *f[2];                // population buffers (post-collision state lives in f[cur])
     int cur;
     cudaStream_t stream;
+    psc::Overlap ov;           // second stream + fork/join events of the 2D step
     int own_stream;
     int device;
     int *flags;                // device flag word: [0] bit 0 unstable density, [1] DEM failures
@@ -42,6 +43,13 @@ struct lbm_ctx {
     long long steps;
     long long launches;        // kernels this context has launched
     long long cs_launches;     // of which fused collide-stream launches
+
+    // one step replayed from a CUDA graph (by population parity and whether it bins),
+    // keyed on what its kernels capture; `gen` changes with every call that changes the
+    // parameters or buffers a step reads
+    cudaGraphExec_t sgraph[2][2];
+    const void *sgkey[2][2][10];
+    long long gen;
 
     // optional CUDA-event timing of the collide-stream kernel (bench / profiling)
     int timing;

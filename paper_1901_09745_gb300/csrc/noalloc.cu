@@ -29,8 +29,10 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-// Device address of g_scratch for each device, looked up once (with that device current).
+// Device address of g_scratch for each device, looked up once (with that device current),
+// and the second stream and events of the 2D step on that device, created at the same time.
 static void *g_scratch_addr[kMaxDevices];
+static psc::Overlap g_overlap[kMaxDevices];
 static std::mutex g_setup_mutex;
 
 char g_noalloc_error[256] = "no error";
@@ -121,6 +123,11 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
             e = cudaGetSymbolAddress(&ptr, g_scratch);
             if (e != cudaSuccess || !ptr) return fail(LBM_ERR_CUDA, "cudaGetSymbolAddress of the working array failed");
             g_scratch_addr[dev] = ptr;
+            psc::Overlap ov = {nullptr, nullptr, nullptr};
+            if (cudaStreamCreateWithFlags(&ov.aux, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ov.fork, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&ov.join, cudaEventDisableTiming) == cudaSuccess)
+                g_overlap[dev] = ov;     // else the kernels of a step share one stream
         }
         base = (unsigned char *)g_scratch_addr[dev];
     }
@@ -144,7 +151,9 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     if (e == cudaSuccess && n > 0) e = launch_f_of_r(is2d ? 2 : 3, radius, (double *)(base + o_fr), n, s);
     if (e == cudaSuccess && n > 0) e = launch_bin(is2d ? 2 : 3, g, ph, tl, pd, s);
     if (e == cudaSuccess && n > 0) e = launch_pack(p->lattice, rec_double, g, tl, pd, ntiles, s);
-    if (e == cudaSuccess) e = launch_collide_stream(p->storage, p->lattice, f_in, f_out, g, ph, tl, pd, flags, s);
+    if (e == cudaSuccess)
+        e = launch_collide_stream(p->storage, p->lattice, f_in, f_out, g, ph, tl, pd, flags, s,
+                                  g_overlap[dev].join ? &g_overlap[dev] : nullptr);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
     return LBM_OK;
 }

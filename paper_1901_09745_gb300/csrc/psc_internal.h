@@ -34,9 +34,9 @@ struct Tiles {
     int *list;
     int cap;
     int *stats;          // [0] tiles that overflowed cap, [1] largest count, [2] length of
-                         // the overflow list, [4] tiles with candidates, [5] tiles without,
-                         // [6] [7] work counters of the persistent particle-tile kernel
-                         // (zero between launches)
+                         // the overflow list, [3] [6] work counters of the collide-stream
+                         // kernel over the fluid and the particle tiles (zero between
+                         // launches), [4] tiles with candidates, [5] tiles without
     void *blocks;        // per-tile packed candidate records (compute type), see psc_kernels.cuh
     uint2 *order;        // [3 * ntiles] {tile id, ty | tz << 16}: tiles with candidates, then
                          // (from ntiles on) tiles without, then (from 2 ntiles on) tiles with
@@ -55,10 +55,17 @@ struct Parts {
 
 enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 
+// A second stream and two events, for the two kernels of a step that run side by side
+// (forked from the caller's stream and joined back into it). Null: one stream.
+struct Overlap {
+    cudaStream_t aux;
+    cudaEvent_t fork, join;
+};
+
 // Fused solid-fraction + PSC collision + pull streaming + force reduction (one step).
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout,
                                   const Geom &g, const Phys &ph, const Tiles &tl,
-                                  const Parts &pd, int *flags, cudaStream_t s);
+                                  const Parts &pd, int *flags, cudaStream_t s, const Overlap *ov);
 // Pre-collision populations (full f, FP64) and/or Eq. 5 moments of the current state.
 cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out,
                           double *rho, double *u, const Geom &g, const Phys &ph,

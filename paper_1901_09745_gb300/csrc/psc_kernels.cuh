@@ -763,6 +763,11 @@ k_collide_overflow(const S *__restrict__ fin, S *__restrict__ fout, Geom g, Phys
     __shared__ unsigned long long s_mask[kWarps];
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     const int novf = tl.stats[2];
+    // the collide-stream kernel before this one has finished: clear its work counters
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+        tl.stats[3] = 0;
+        tl.stats[6] = 0;
+    }
     for (int it = blockIdx.x; it < novf; it += gridDim.x) {
         psc_tile<L, S, PSC>(tl.order[2 * ntiles + it].x, fin, fout, g, ph, tl, pd, flags,
                             reinterpret_cast<T *>(smem), s_mask);
@@ -825,7 +830,8 @@ __global__ void k_set(const double *__restrict__ f, S *__restrict__ fout, Geom g
 // Blocks of a persistent grid: as many as stay resident on all SMs (never more than the
 // work items). The occupancy query is cached per kernel and shared-memory size.
 template <typename K>
-inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsigned &blocks, int threads = kThreads) {
+inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsigned &blocks, int threads = kThreads,
+                                     int *per_sm = nullptr) {
     static thread_local const void *c_kern = nullptr;
     static thread_local size_t c_smem = (size_t)-1;
     static thread_local int c_per = 0;
@@ -843,17 +849,37 @@ inline cudaError_t persistent_blocks(K kern, size_t smem, long long work, unsign
     }
     const long long b = (long long)sms * c_per;
     blocks = (unsigned)(b < work ? b : (work > 0 ? work : 1));
+    if (per_sm) *per_sm = c_per;
     return cudaSuccess;
 }
 
+// Registers a block of `threads` holds (allocated per warp in units of 8 per thread).
+template <typename K>
+inline cudaError_t block_registers(K kern, int threads, int &regs) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    regs = (e == cudaSuccess) ? ((fa.numRegs + 7) / 8 * 8) * threads : 0;
+    return e;
+}
+
+// One collide-stream step. Without particles: the fluid kernel over every tile. With
+// particles in 2D (FP32 and 16-bit storage): the particle-tile kernel (4 blocks per SM) and
+// the fluid-tile kernel (3 blocks per SM) side by side on two streams, which together fill
+// each SM's register file, so the issue-bound particle tiles and the DRAM-bound fluid tiles
+// share every SM for the whole step; without a second stream, one after the other. In 3D
+// (and FP64) the particle-tile kernel holds all the registers an SM has, and takes the
+// fluid tiles itself once its own are done. Then the overflow kernel.
 template <class L, typename S, int PSC>
 cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, const Phys &ph,
-                                    const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s) {
+                                    const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s,
+                                    const Overlap *ov) {
     using T = typename Store<S>::T;
     constexpr int NC = (L::D == 2) ? 3 : 6;
+    constexpr bool kSteal = (L::D == 3) || sizeof(T) == 8;
+    constexpr int kSideP = 4, kSideF = 3;     // blocks per SM side by side (2D)
     const size_t smem = pair_smem_bytes<L, T>();
     const size_t osmem = cs_smem_bytes<T>(tl.cap, NC);
-    auto kern = k_collide_stream<L, S, PSC>;
+    auto kern = k_collide_stream<L, S, PSC, kSteal>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -862,28 +888,49 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     dim3 block(L::TX, L::TY, L::TZ);
     const PhysT<T> pt = make_phys<T>(ph);
     const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
-    unsigned nb = 0;
-    cudaError_t e;
-    const dim3 full(g.nt[0], g.nt[1], g.nt[2]);
+    auto fkern = hasF ? k_fluid_pair<L, S, true> : k_fluid_pair<L, S, false>;
     const dim3 pblock(32, kPWarps);
-    if (hasF) {
-        e = persistent_blocks(k_fluid_pair<L, S, true>, 0, ntiles, nb, kPThreads);
-        if (e != cudaSuccess) return e;
-        if (pd.n > 0) k_fluid_pair<L, S, true><<<nb, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
-        else k_fluid_pair<L, S, true><<<full, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
-    } else {
-        e = persistent_blocks(k_fluid_pair<L, S, false>, 0, ntiles, nb, kPThreads);
-        if (e != cudaSuccess) return e;
-        if (pd.n > 0) k_fluid_pair<L, S, false><<<nb, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
-        else k_fluid_pair<L, S, false><<<full, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
+    if (pd.n == 0) {
+        fkern<<<dim3(g.nt[0], g.nt[1], g.nt[2]), pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, 0, flags);
+        return cudaGetLastError();
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess || pd.n == 0) return e;
-    e = persistent_blocks(kern, smem, ntiles, nb, kPThreads);
-    if (e != cudaSuccess) return e;
-    kern<<<nb, dim3(32, kPWarps), smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
+    unsigned nb = 0;
+    bool side = false;
+    int nsm = 0;
+    if (!kSteal && ov && ov->aux) {
+        int dev = 0, rf_sm = 0, rp = 0, rf = 0, per = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&rf_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = block_registers(kern, kPThreads, rp);
+        if (e == cudaSuccess) e = block_registers(fkern, kPThreads, rf);
+        if (e == cudaSuccess) e = persistent_blocks(kern, smem, ntiles, nb, kPThreads, &per);
+        if (e != cudaSuccess) return e;
+        side = per >= kSideP && kSideP * rp + kSideF * rf <= rf_sm;
+    }
+    if (side) {
+        e = cudaEventRecord(ov->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->fork, 0);
+        if (e != cudaSuccess) return e;
+        kern<<<nsm * kSideP, pblock, smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+        fkern<<<nsm * kSideF, pblock, 0, ov->aux>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ov->join, ov->aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ov->join, 0);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (!kSteal) {
+            e = persistent_blocks(fkern, 0, ntiles, nb, kPThreads);
+            if (e != cudaSuccess) return e;
+            fkern<<<nb, pblock, 0, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        }
+        e = persistent_blocks(kern, smem, ntiles, nb, kPThreads);
+        if (e != cudaSuccess) return e;
+        kern<<<nb, pblock, smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     auto okern = k_collide_overflow<L, S, PSC>;
     if (osmem > 48 * 1024) {
         e = cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
@@ -896,13 +943,13 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
 template <typename S>
 cudaError_t launch_collide_stream_storage(int lattice, const void *fin, void *fout, const Geom &g,
                                           const Phys &ph, const Tiles &tl, const Parts &pd,
-                                          int *flags, cudaStream_t s) {
+                                          int *flags, cudaStream_t s, const Overlap *ov) {
     if (lattice == 9) {
-        return ph.psc == 0 ? launch_collide_stream_t<D2Q9, S, 0>(fin, fout, g, ph, tl, pd, flags, s)
-                           : launch_collide_stream_t<D2Q9, S, 1>(fin, fout, g, ph, tl, pd, flags, s);
+        return ph.psc == 0 ? launch_collide_stream_t<D2Q9, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov)
+                           : launch_collide_stream_t<D2Q9, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov);
     }
-    return ph.psc == 0 ? launch_collide_stream_t<D3Q19, S, 0>(fin, fout, g, ph, tl, pd, flags, s)
-                       : launch_collide_stream_t<D3Q19, S, 1>(fin, fout, g, ph, tl, pd, flags, s);
+    return ph.psc == 0 ? launch_collide_stream_t<D3Q19, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov)
+                       : launch_collide_stream_t<D3Q19, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov);
 }
 
 template <typename S>

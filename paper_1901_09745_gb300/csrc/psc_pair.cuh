@@ -436,12 +436,89 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     }
 }
 
+// One plain-fluid tile with two cells per thread (rows as in the particle-tile path): BGK +
+// Guo + pull on FP32 pairs. With F = 0 the Guo terms add exact zeros, so HASF = true gives
+// the same results as HASF = false.
+template <class L, typename S, bool HASF>
+__device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__restrict__ fout, const Geom &g,
+                                                const PhysT<typename Store<S>::T> &ph, const int x0, const int y0,
+                                                const int z0, int *flags) {
+    using T = typename Store<S>::T;
+    using P = Pr<T>;
+    using V = typename P::V;
+    constexpr int Q = L::Q;
+    const long long N = g.ncell;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    const PairCells<L> pc(lane, warp);
+    const int xA = x0 + pc.xA, xB = x0 + pc.xB;
+    const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
+    const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
+    const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
+    const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
+    const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
+    const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
+                          (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
+    constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
+    T da[Q], db[Q];
+    pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
+    V df[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
+    V drho = df[0], jx = P::sp((T)0), jy = P::sp((T)0), jz = P::sp((T)0);
+#pragma unroll
+    for (int i = 1; i < Q; ++i) drho = P::add(drho, df[i]);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (L::ex(i)) jx = L::ex(i) > 0 ? P::add(jx, df[i]) : P::sub(jx, df[i]);
+        if (L::ey(i)) jy = L::ey(i) > 0 ? P::add(jy, df[i]) : P::sub(jy, df[i]);
+        if (L::ez(i)) jz = L::ez(i) > 0 ? P::add(jz, df[i]) : P::sub(jz, df[i]);
+    }
+    const T ssc = SC ? (T)ph.sc.x : (T)1;
+    if (SC) {
+        const V is = P::sp((T)ph.sc.y);
+        drho = P::mul(drho, is); jx = P::mul(jx, is); jy = P::mul(jy, is); jz = P::mul(jz, is);
+    }
+    const V rho = P::add(P::sp((T)1), drho);
+    const V irho = P::mk((T)1 / rho.x, (T)1 / rho.y);
+    V ux, uy, uz;
+    if (HASF) {
+        ux = P::mul(P::add(jx, P::sp((T)0.5 * ph.F[0])), irho);
+        uy = P::mul(P::add(jy, P::sp((T)0.5 * ph.F[1])), irho);
+        uz = P::mul(P::add(jz, P::sp((T)0.5 * ph.F[2])), irho);
+    } else {
+        ux = P::mul(jx, irho); uy = P::mul(jy, irho); uz = P::mul(jz, irho);
+    }
+    if ((actA && !(rho.x > (T)0)) || (actB && !(rho.y > (T)0))) atomicOr(flags, 1);
+    const V uu = P::fma(ux, ux, P::fma(uy, uy, P::mul(uz, uz)));
+    const V base_eq = P::sub(drho, P::mul(P::sp((T)1.5), P::mul(rho, uu)));
+    const V om1 = P::sp((T)1 - ph.omega), om = P::sp(ph.omega);
+    V guo3uF = P::sp((T)0);
+    if (HASF) {
+        const V uF = P::fma(ux, P::sp(ph.F[0]), P::fma(uy, P::sp(ph.F[1]), P::mul(uz, P::sp(ph.F[2]))));
+        guo3uF = P::mul(P::sp((T)3 * ph.guo), uF);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T w = (T)weight<L>(i) * ssc;
+        const V eu = edot2<L, T>(i, ux, uy, uz);
+        // w (base_eq + rho eu (3 + 4.5 eu))
+        const V dfeq = P::mul(P::sp(w), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
+        V out = P::fma(om1, df[i], P::mul(om, dfeq));
+        if (HASF) {
+            const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
+            out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
+        }
+        store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
+    }
+}
+
 // The particle-tile kernel: a persistent grid takes tiles with candidates from the compact
-// list through a work counter (tiles differ in cost, so the counter balances the SMs); the
-// next tile's index is fetched while the current one runs; the last block to finish resets
-// the counters for the next launch. Tiles with more than kPairCap candidates are left to
-// k_collide_overflow.
-template <class L, typename S, int PSC>
+// list through a work counter (tiles differ in cost, so the counter balances the SMs; the
+// next tile's index is fetched while the current one runs). With STEAL it then takes the
+// tiles without candidates the same way, so one launch covers the lattice and its blocks
+// share out the end of the step. Tiles with more than kPairCap candidates are left to
+// k_collide_overflow, which also clears the counters for the next launch.
+template <class L, typename S, int PSC, bool STEAL>
 __global__ void __launch_bounds__(kPThreads, (sizeof(typename Store<S>::T) == 8) ? 2 : ((L::Q == 9) ? 7 : 4))
 k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
                  PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
@@ -465,7 +542,6 @@ k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
     for (;;) {
         const int it = s_next[buf];
         if (it >= npsc) break;
-        // the following tile's index, fetched now so its latency hides behind this tile
         if (tid == 0) s_next[buf ^ 1] = atomicAdd(&tl.stats[6], 1);
         const uint2 ent = tl.order[it];
         const int cnt = tl.count[ent.x];
@@ -486,101 +562,47 @@ k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
     }
     __syncthreads();
     pair_flush<L, T>(prev_cnt, prev_recs, sm + 2 * rsz + (buf ^ 1) * psz, s_mask[buf ^ 1], pd, tid);
-    if (tid == 0) {
-        __threadfence();
-        if (atomicAdd(&tl.stats[7], 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1) {
-            tl.stats[6] = 0;
-            tl.stats[7] = 0;
+    if (STEAL) {
+        const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
+        const int nfl = tl.stats[5];
+        const uint2 *const flist = tl.order + ntiles;
+        __syncthreads();
+        if (tid == 0) s_next[0] = atomicAdd(&tl.stats[3], 1);
+        __syncthreads();
+        buf = 0;
+        for (;;) {
+            const int it = s_next[buf];
+            if (it >= nfl) break;
+            if (tid == 0) s_next[buf ^ 1] = atomicAdd(&tl.stats[3], 1);
+            const uint2 ent = flist[it];
+            const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
+            fluid_tile_pair<L, S, true>(fin, fout, g, ph,
+                                        (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX,
+                                        (int)ty * L::TY, (int)tz * L::TZ, flags);
+            __syncthreads();     // the next index is visible, this one may be overwritten
+            buf ^= 1;
         }
     }
 }
-// Plain-fluid tiles with two cells per thread (rows as in the particle-tile kernel): BGK +
-// Guo + pull on FP32 pairs. With particles a persistent grid over the list of tiles without
-// candidates; without, one block per tile.
+
+// Plain-fluid tiles: without particles one block per tile; with particles a persistent
+// grid striding over the list of tiles without candidates (beside the particle-tile kernel).
 template <class L, typename S, bool HASF>
 __global__ void __launch_bounds__(kPThreads, (L::Q == 9) ? 8 : 5)
-k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph,
-             Tiles tl, int np, int *flags) {
-    using T = typename Store<S>::T;
-    using P = Pr<T>;
-    using V = typename P::V;
-    constexpr int Q = L::Q;
+k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph, Tiles tl,
+             int np, int *flags) {
+    if (np == 0) {
+        fluid_tile_pair<L, S, HASF>(fin, fout, g, ph, blockIdx.x * L::TX, blockIdx.y * L::TY, blockIdx.z * L::TZ,
+                                    flags);
+        return;
+    }
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    const int nf = (np > 0) ? tl.stats[5] : 1;
-    const uint2 *list = (np > 0) ? tl.order + ntiles : nullptr;
-    const long long N = g.ncell;
-    const int lane = threadIdx.x, warp = threadIdx.y;
-    const PairCells<L> pc(lane, warp);
-    for (int it = (np > 0) ? (int)blockIdx.x : 0; it < nf; it += gridDim.x) {
-        int x0, y0, z0;
-        if (list) {
-            const uint2 ent = list[it];
-            const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
-            x0 = (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
-            y0 = (int)ty * L::TY;
-            z0 = (int)tz * L::TZ;
-        } else {
-            x0 = blockIdx.x * L::TX; y0 = blockIdx.y * L::TY; z0 = blockIdx.z * L::TZ;
-        }
-        const int xA = x0 + pc.xA, xB = x0 + pc.xB;
-        const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
-        const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
-        const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
-        const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
-        const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
-        const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
-                              (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
-        constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
-        T da[Q], db[Q];
-        pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
-        V df[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
-        V drho = df[0], jx = P::sp((T)0), jy = P::sp((T)0), jz = P::sp((T)0);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) drho = P::add(drho, df[i]);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (L::ex(i)) jx = L::ex(i) > 0 ? P::add(jx, df[i]) : P::sub(jx, df[i]);
-            if (L::ey(i)) jy = L::ey(i) > 0 ? P::add(jy, df[i]) : P::sub(jy, df[i]);
-            if (L::ez(i)) jz = L::ez(i) > 0 ? P::add(jz, df[i]) : P::sub(jz, df[i]);
-        }
-        const T ssc = SC ? (T)ph.sc.x : (T)1;
-        if (SC) {
-            const V is = P::sp((T)ph.sc.y);
-            drho = P::mul(drho, is); jx = P::mul(jx, is); jy = P::mul(jy, is); jz = P::mul(jz, is);
-        }
-        const V rho = P::add(P::sp((T)1), drho);
-        const V irho = P::mk((T)1 / rho.x, (T)1 / rho.y);
-        V ux, uy, uz;
-        if (HASF) {
-            ux = P::mul(P::add(jx, P::sp((T)0.5 * ph.F[0])), irho);
-            uy = P::mul(P::add(jy, P::sp((T)0.5 * ph.F[1])), irho);
-            uz = P::mul(P::add(jz, P::sp((T)0.5 * ph.F[2])), irho);
-        } else {
-            ux = P::mul(jx, irho); uy = P::mul(jy, irho); uz = P::mul(jz, irho);
-        }
-        if ((actA && !(rho.x > (T)0)) || (actB && !(rho.y > (T)0))) atomicOr(flags, 1);
-        const V uu = P::fma(ux, ux, P::fma(uy, uy, P::mul(uz, uz)));
-        const V base_eq = P::sub(drho, P::mul(P::sp((T)1.5), P::mul(rho, uu)));
-        const V om1 = P::sp((T)1 - ph.omega), om = P::sp(ph.omega);
-        V guo3uF = P::sp((T)0);
-        if (HASF) {
-            const V uF = P::fma(ux, P::sp(ph.F[0]), P::fma(uy, P::sp(ph.F[1]), P::mul(uz, P::sp(ph.F[2]))));
-            guo3uF = P::mul(P::sp((T)3 * ph.guo), uF);
-        }
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const T w = (T)weight<L>(i) * ssc;
-            const V eu = edot2<L, T>(i, ux, uy, uz);
-            // w (base_eq + rho eu (3 + 4.5 eu))
-            const V dfeq = P::mul(P::sp(w), P::fma(P::mul(rho, eu), P::fma(P::sp((T)4.5), eu, P::sp((T)3)), base_eq));
-            V out = P::fma(om1, df[i], P::mul(om, dfeq));
-            if (HASF) {
-                const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
-                out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
-            }
-            store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
-        }
+    const int nfl = tl.stats[5];
+    const uint2 *const flist = tl.order + ntiles;
+    for (int it = blockIdx.x; it < nfl; it += gridDim.x) {
+        const uint2 ent = flist[it];
+        const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
+        fluid_tile_pair<L, S, HASF>(fin, fout, g, ph, (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX,
+                                    (int)ty * L::TY, (int)tz * L::TZ, flags);
     }
 }
