@@ -257,45 +257,27 @@ __device__ __forceinline__ float jkr_s(float t, int *fail) {
     return sc + e;
 }
 
-// One contact seen from particle i (neighbour j): force and torque on i in FP32. hist is
-// this view's copy of the pair history; returns 0 and clears it when not in contact.
-__device__ bool contact_on_i(const DemPhys &ph, int dim, const double *d64, double dist, double dn,
+// One contact seen from particle i (neighbour j): force and torque on i in FP32. The caller
+// has decided whether the pair is in contact (exactly, see k_dem_substep) and passes the
+// unit normal n (from i towards j) and the overlap delta_N in FP32. hist is this view's copy
+// of the pair history; returns 0 and clears it when not in contact.
+__device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, const float *n, const float dnf,
                              double ri, double rj, float imi, float imj, const double *Ui,
                              const double *Uj, const double *Omi, const double *Omj, float *h,
                              float *fo, float *to, int *fail) {
-    // the contact law runs in FP32; only the contact decisions below use FP64 (GB300 executes
-    // FP64, and FP64 division in particular, at a small fraction of the FP32 rate)
     const float rif = (float)ri, rjf = (float)rj;
     const float Rf = rif * rjf / (rif + rjf);
     const float Es = ph.Es;
     float FC = 0.0f, a0 = 0.0f;
-    const bool was = h[7] != 0.0f;
-    bool contact;
     if (ph.adhesive) {
         FC = (float)(3.0 * kPi) * ph.gamma * Rf;
         a0 = cbrtf((float)(9.0 * kPi) * ph.gamma * Rf * Rf / Es);
-        if (dn >= 0.0) {
-            contact = true;
-        } else if (was) {
-            // per-pair delta_C in FP64, so the persistence test matches a CPU reference
-            const double R64 = ri * rj / (ri + rj);
-            const double a064 = cbrt(9.0 * kPi * (double)ph.gamma * R64 * R64 / (double)Es);
-            const double dC = a064 * a064 * ph.dc_coef / R64;
-            contact = dn > -dC;
-        } else {
-            contact = false;
-        }
-    } else {
-        contact = dn > 0.0;
     }
     if (!contact) {
         for (int k = 0; k < kH; ++k) h[k] = 0.0f;
         for (int a = 0; a < 3; ++a) { fo[a] = 0.0f; to[a] = 0.0f; }
         return false;
     }
-    const float inv = 1.0f / (float)dist;
-    const float n[3] = {(float)d64[0] * inv, (float)d64[1] * inv, (float)d64[2] * inv};
-    const float dnf = (float)dn;
     float ac, Fne, kr = 0.0f;
     if (ph.adhesive) {
         const float s = jkr_s(dnf * Rf / (a0 * a0), fail);
@@ -398,6 +380,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
     const int dim = g.dim;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0}, ri = 1.0;
+    double fi[3] = {0, 0, 0}, ti[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, im = 0.0, iI = 0.0;
     int fail = 0;
     if (valid) {
 #pragma unroll
@@ -406,6 +389,13 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         const float4 pif = b.Xf[i];
         const float imi = (float)b.minv[2 * i];
         const int nn = b.nbr_n[i];
+        if (sub == 0) {
+            // the integration's inputs, loaded before the contact loop's stores
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { fi[a] = b.Ff[3 * i + a]; ti[a] = b.Tf[3 * i + a]; xr[a] = b.Xref[3 * i + a]; }
+            im = b.minv[2 * i];
+            iI = b.minv[2 * i + 1];
+        }
         for (int s = sub; s < nn; s += kLPP) {
             const int j = b.nbr[i * kNB + s];
             float *hp = b.hist + ((size_t)i * kNB + s) * kH;
@@ -422,8 +412,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                 }
             }
             const bool was = hp[7] != 0.0f;
-            const float dnf = (pif.w + pj.w) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
-            if (dnf < -b.reject) {
+            const float dpre = (pif.w + pj.w) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
+            if (dpre < -b.reject) {
                 // provably out of contact (the margin dwarfs the FP32 error)
                 if (was) for (int k = 0; k < kH; ++k) hp[k] = 0.0f;
                 continue;
@@ -442,17 +432,58 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                 }
             }
             const double rj = b.R[j];
-            // exact overlap in FP64 with IEEE-rounded operations (bit-identical at both ends)
+            // d^2 in FP64 with IEEE-rounded operations (bit-identical at both ends and in a
+            // CPU reference), S = r_i + r_j. delta_N = S - |d| is formed, as the reference
+            // forms it, only for pairs within a few ulps of touching: elsewhere the sign of
+            // d^2 - S^2 (one rounding, so its sign is exact) decides delta_N >= 0 and > 0,
+            // and delta_N itself enters the FP32 contact law as (S^2 - d^2) / (S + |d|).
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
-            const double dist = __dsqrt_rn(d2);
-            const double dn = __dsub_rn(__dadd_rn(ri, rj), dist);
+            const double S = __dadd_rn(ri, rj);
+            const double u = __fma_rn(-S, S, d2);
+            const float d2f = (float)d2, inv = rsqrtf(d2f);
+            bool ge0 = u < 0.0, gt0 = ge0;
+            float dnf = (float)(-u) / ((float)S + d2f * inv);
+            double dn = 0.0;
+            bool exact = false;
+            if (fabs(u) <= S * S * 0x1p-48) {
+                dn = __dsub_rn(S, __dsqrt_rn(d2));
+                exact = true;
+                ge0 = dn >= 0.0;
+                gt0 = dn > 0.0;
+                dnf = (float)dn;
+            }
+            bool contact;
+            if (!ph.adhesive) {
+                contact = gt0;
+            } else if (ge0) {
+                contact = true;
+            } else if (!was) {
+                contact = false;
+            } else {
+                // a stretched neck persists while delta_N > -delta_C: decided in FP32 unless
+                // the two agree to 1e-5, then with delta_N and delta_C in FP64
+                const float rif = (float)ri, rjf = (float)rj;
+                const float Rf = rif * rjf / (rif + rjf);
+                const float a0f = cbrtf((float)(9.0 * kPi) * ph.gamma * Rf * Rf / ph.Es);
+                const float dCf = a0f * a0f * (float)ph.dc_coef / Rf;
+                const float gap = dnf + dCf;
+                if (fabsf(gap) > 1e-5f * dCf) {
+                    contact = gap > 0.0f;
+                } else {
+                    if (!exact) dn = __dsub_rn(S, __dsqrt_rn(d2));
+                    const double R64 = ri * rj / (ri + rj);
+                    const double a064 = cbrt(9.0 * kPi * (double)ph.gamma * R64 * R64 / (double)ph.Es);
+                    contact = dn > -(a064 * a064 * ph.dc_coef / R64);
+                }
+            }
+            const float nv[3] = {(float)d[0] * inv, (float)d[1] * inv, (float)d[2] * inv};
             const float imj = (float)b.minv[2 * j];
             float hl[kH];
             for (int k = 0; k < kH; ++k) hl[k] = hp[k];
             float fo[3], to[3];
             const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
             const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
-            if (contact_on_i(ph, dim, d, dist, dn, ri, rj, imi, imj, ui, uj, oi, oj, hl, fo, to, &fail)) {
+            if (contact_on_i(ph, dim, contact, nv, dnf, ri, rj, imi, imj, ui, uj, oi, oj, hl, fo, to, &fail)) {
                 for (int a = 0; a < 3; ++a) { acc[a] += (double)fo[a]; acc[3 + a] += (double)to[a]; }
             }
             if (was || hl[7] != 0.0f) for (int k = 0; k < kH; ++k) hp[k] = hl[k];
@@ -466,12 +497,11 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
     if (fail) atomicAdd(&b.flags[1], 1);
     if (!valid || sub != 0) return;
     // Eq. 21, semi-implicit Euler, hydrodynamic force/torque frozen over the sub-steps
-    const double im = b.minv[2 * i], iI = b.minv[2 * i + 1];
     double un[3], xn[3], on[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a < dim) {
-            un[a] = ui[a] + ph.dt * ((b.Ff[3 * i + a] + acc[a]) * im + ph.g[a]);
+            un[a] = ui[a] + ph.dt * ((fi[a] + acc[a]) * im + ph.g[a]);
             xn[a] = xi[a] + ph.dt * un[a];
             if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] * g.inv_n[a]);
         } else {
@@ -479,13 +509,13 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             xn[a] = xi[a];
         }
         const bool spin = (dim == 3) || (a == 2);
-        on[a] = spin ? oi[a] + ph.dt * (b.Tf[3 * i + a] + acc[3 + a]) * iI : oi[a];
+        on[a] = spin ? oi[a] + ph.dt * (ti[a] + acc[3 + a]) * iI : oi[a];
     }
     float disp2 = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= dim) break;
-        float dd = (float)(xn[a] - b.Xref[3 * i + a]);
+        float dd = (float)(xn[a] - xr[a]);
         if (g.periodic[a]) {
             const float half = 0.5f * (float)g.n[a];
             if (dd > half) dd -= (float)g.n[a];
