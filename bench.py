@@ -241,7 +241,7 @@ def run_ours(args, rank, local_rank, world):
         sampler.start()
     # the collide-stream kernels' own duration, from CUDA events around every TIMING_EVERY-th
     # step of the timed run (the other steps replay the step's CUDA graph)
-    P.lbm_kernel_timing(ctx, TIMING_EVERY)
+    P.lbm_kernel_timing(ctx, max(1, min(TIMING_EVERY, args.steps // 4)))
     barrier(world, dev)
     torch.cuda.synchronize(dev)
     t0 = torch.cuda.Event(enable_timing=True)

@@ -236,11 +236,13 @@ __device__ __forceinline__ void rotate_into_plane(float *xi, const float *n) {
 // pull-off point where the original form loses all digits to cancellation. The left side
 // is increasing and convex for e >= 0, and both starting guesses below lie to the right of
 // the root, so Newton decreases monotonically onto it.
-__device__ __forceinline__ float jkr_s(float t, int *fail) {
+__device__ __forceinline__ float jkr_s(float t, int *fail, float s_prev) {
     const float sc = 0.55032120814910446f;            // 6^(-1/3)
     const float tau = fmaxf(t + 0.5f * sc, 0.0f);      // t - t_c
     const float c2 = 6.0f * sc * sc, c1 = 4.0f * sc;
-    float e = fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
+    // the previous sub-step's root when there is one (Newton from the left of the root
+    // overshoots once to the right, then decreases monotonically as below)
+    float e = (tau > 0.0f && s_prev > sc) ? s_prev - sc : fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
     if (tau > 0.0f) {
         int it = 0;
         for (; it < 40; ++it) {
@@ -262,10 +264,9 @@ __device__ __forceinline__ float jkr_s(float t, int *fail) {
 // unit normal n (from i towards j) and the overlap delta_N in FP32. hist is this view's copy
 // of the pair history; returns 0 and clears it when not in contact.
 __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, const float *n, const float dnf,
-                             double ri, double rj, float imi, float imj, const double *Ui,
-                             const double *Uj, const double *Omi, const double *Omj, float *h,
+                             const float rif, const float rjf, float imi, float imj, const float *Ui,
+                             const float *Uj, const float *omi, const float *omj, float *h,
                              float *fo, float *to, int *fail) {
-    const float rif = (float)ri, rjf = (float)rj;
     const float Rf = rif * rjf / (rif + rjf);
     const float Es = ph.Es;
     float FC = 0.0f, a0 = 0.0f;
@@ -278,9 +279,10 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, con
         for (int a = 0; a < 3; ++a) { fo[a] = 0.0f; to[a] = 0.0f; }
         return false;
     }
-    float ac, Fne, kr = 0.0f;
+    float ac, Fne, kr = 0.0f, s_store = 1.0f;
     if (ph.adhesive) {
-        const float s = jkr_s(dnf * Rf / (a0 * a0), fail);
+        const float s = jkr_s(dnf * Rf / (a0 * a0), fail, h[7]);
+        s_store = s;
         const float s3 = s * s * s;
         ac = s * s * a0;
         Fne = 4.0f * FC * (s3 * s3 - s3);          // Eq. 26 with (a/a0)^3 = s^6, (a/a0)^1.5 = s^3
@@ -300,12 +302,10 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, con
     // relative velocity of the contact points
     const float arm_i[3] = {rif * n[0], rif * n[1], rif * n[2]};
     const float arm_j[3] = {-rjf * n[0], -rjf * n[1], -rjf * n[2]};
-    const float omi[3] = {(float)Omi[0], (float)Omi[1], (float)Omi[2]};
-    const float omj[3] = {(float)Omj[0], (float)Omj[1], (float)Omj[2]};
     float w1[3], w2[3], vij[3], vt[3];
     cross3f(omi, arm_i, w1);
     cross3f(omj, arm_j, w2);
-    for (int a = 0; a < 3; ++a) vij[a] = ((float)Ui[a] + w1[a]) - ((float)Uj[a] + w2[a]);
+    for (int a = 0; a < 3; ++a) vij[a] = (Ui[a] + w1[a]) - (Uj[a] + w2[a]);
     const float vn = dot3f(vij, n);
     for (int a = 0; a < 3; ++a) vt[a] = vij[a] - vn * n[a];
 
@@ -352,7 +352,7 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, con
             for (int a = 0; a < 3; ++a) { Mr[a] *= sc; xr[a] *= sc; }
         }
     }
-    h[7] = 1.0f;
+    h[7] = s_store;     // contact flag; JKR: the contact-radius root s (> 0)
 
     float tq[3];
     cross3f(arm_i, Ft, tq);
@@ -373,11 +373,14 @@ constexpr int kLPP = 4;   // lanes per particle in the sub-step kernel
 
 // One DEM sub-step. kLPP lanes share a particle and split its neighbour slots; their FP64
 // sums are combined with shuffles in a fixed order, then the first lane integrates.
+template <int DIM>
 __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kLPP, sub = t % kLPP;
     const bool valid = i < b.n;
-    const int dim = g.dim;
+    constexpr int dim = DIM;
+    // force and torque components a 2D disc has: F_x, F_y and T_z
+    auto used = [](int q) { return DIM == 3 || q == 0 || q == 1 || q == 5; };
     double acc[6] = {0, 0, 0, 0, 0, 0};
     double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0}, ri = 1.0;
     double fi[3] = {0, 0, 0}, ti[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, im = 0.0, iI = 0.0;
@@ -388,6 +391,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         ri = b.R[i];
         const float4 pif = b.Xf[i];
         const float imi = (float)b.minv[2 * i];
+        const float uif[3] = {(float)ui[0], (float)ui[1], (float)ui[2]};
+        const float oif[3] = {(float)oi[0], (float)oi[1], (float)oi[2]};
         const int nn = b.nbr_n[i];
         if (sub == 0) {
             // the integration's inputs, loaded before the contact loop's stores
@@ -440,12 +445,12 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
             const double S = __dadd_rn(ri, rj);
             const double u = __fma_rn(-S, S, d2);
-            const float d2f = (float)d2, inv = rsqrtf(d2f);
-            bool ge0 = u < 0.0, gt0 = ge0;
-            float dnf = (float)(-u) / ((float)S + d2f * inv);
+            const float d2f = (float)d2, inv = rsqrtf(d2f), uf = (float)u, Sf = (float)S;
+            bool ge0 = uf < 0.0f, gt0 = ge0;
+            float dnf = -uf / (Sf + d2f * inv);
             double dn = 0.0;
             bool exact = false;
-            if (fabs(u) <= S * S * 0x1p-48) {
+            if (fabsf(uf) <= Sf * Sf * 0x1p-47f) {     // |d^2 - S^2| <= ~2^-48 S^2
                 dn = __dsub_rn(S, __dsqrt_rn(d2));
                 exact = true;
                 ge0 = dn >= 0.0;
@@ -462,8 +467,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             } else {
                 // a stretched neck persists while delta_N > -delta_C: decided in FP32 unless
                 // the two agree to 1e-5, then with delta_N and delta_C in FP64
-                const float rif = (float)ri, rjf = (float)rj;
-                const float Rf = rif * rjf / (rif + rjf);
+                const float Rf = pif.w * pj.w / (pif.w + pj.w);
                 const float a0f = cbrtf((float)(9.0 * kPi) * ph.gamma * Rf * Rf / ph.Es);
                 const float dCf = a0f * a0f * (float)ph.dc_coef / Rf;
                 const float gap = dnf + dCf;
@@ -481,10 +485,14 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             float hl[kH];
             for (int k = 0; k < kH; ++k) hl[k] = hp[k];
             float fo[3], to[3];
-            const double uj[3] = {b.U[3 * j], b.U[3 * j + 1], b.U[3 * j + 2]};
-            const double oj[3] = {b.Om[3 * j], b.Om[3 * j + 1], b.Om[3 * j + 2]};
-            if (contact_on_i(ph, dim, contact, nv, dnf, ri, rj, imi, imj, ui, uj, oi, oj, hl, fo, to, &fail)) {
-                for (int a = 0; a < 3; ++a) { acc[a] += (double)fo[a]; acc[3 + a] += (double)to[a]; }
+            const float ujf[3] = {(float)b.U[3 * j], (float)b.U[3 * j + 1], (float)b.U[3 * j + 2]};
+            const float ojf[3] = {(float)b.Om[3 * j], (float)b.Om[3 * j + 1], (float)b.Om[3 * j + 2]};
+            if (contact_on_i(ph, dim, contact, nv, dnf, pif.w, pj.w, imi, imj, uif, ujf, oif, ojf, hl, fo, to, &fail)) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (used(a)) acc[a] += (double)fo[a];
+                    if (used(3 + a)) acc[3 + a] += (double)to[a];
+                }
             }
             if (was || hl[7] != 0.0f) for (int k = 0; k < kH; ++k) hp[k] = hl[k];
         }
@@ -493,7 +501,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
 #pragma unroll
     for (int off = 1; off < kLPP; off <<= 1)
 #pragma unroll
-        for (int q = 0; q < 6; ++q) acc[q] += __shfl_xor_sync(kFullMask, acc[q], off);
+        for (int q = 0; q < 6; ++q)
+            if (used(q)) acc[q] += __shfl_xor_sync(kFullMask, acc[q], off);
     if (fail) atomicAdd(&b.flags[1], 1);
     if (!valid || sub != 0) return;
     // Eq. 21, semi-implicit Euler, hydrodynamic force/torque frozen over the sub-steps
@@ -711,7 +720,8 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps, int cur) {
         const int src = k & 1, dst = src ^ 1;
         b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src];
         b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst];
-        k_dem_substep<<<blocks, threads, 0, s>>>(d->g, d->ph, b);
+        if (d->g.dim == 2) k_dem_substep<2><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
+        else k_dem_substep<3><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
     }
     return cudaGetLastError();
 }
