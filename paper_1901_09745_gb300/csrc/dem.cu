@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kNB = 32;        // neighbour slots per particle (one warp lane each)
 constexpr int kH = 8;          // history floats per slot: xi_s[3], xi_t, xi_r[3], contact flag
+static_assert(kH == 8, "history slots are copied as two float4");
 constexpr unsigned kFullMask = 0xffffffffu;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -40,6 +41,7 @@ struct DemGeom {
     double skin;
     float margin;       // slack for FP32 position copies (>> their rounding error)
     double inv_n[3];    // 1 / n per axis (no FP64 division on the device)
+    double bscale[3];   // nb / n per axis: bin of x = floor(x * bscale)
 };
 
 struct DemPhys {
@@ -67,8 +69,8 @@ struct DemBufs {
     float reject;                   // pairs with an FP32 overlap below -reject cannot touch
 };
 
-__device__ __forceinline__ int bin_of(double x, int n, int nb, int periodic) {
-    int b = (int)floor(x * nb / n);
+__device__ __forceinline__ int bin_of(double x, double bscale, int nb, int periodic) {
+    int b = (int)floor(x * bscale);
     if (periodic) { b %= nb; if (b < 0) b += nb; }
     else { b = b < 0 ? 0 : (b >= nb ? nb - 1 : b); }
     return b;
@@ -82,7 +84,7 @@ __global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, fl
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-        if (a < g.dim) b[a] = bin_of(X[3 * i + a], g.n[a], g.nb[a], g.periodic[a]);
+        if (a < g.dim) b[a] = bin_of(X[3 * i + a], g.bscale[a], g.nb[a], g.periodic[a]);
     const int bin = b[0] + g.nb[0] * (b[1] + g.nb[1] * b[2]);
     const int slot = atomicAdd(&count[bin], 1);
     if (slot < g.bin_cap) list[bin * g.bin_cap + slot] = i;
@@ -116,10 +118,20 @@ __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, co
     const double xi[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
     const double ri = R[i];
     const float4 pi = Xf[i];
+    // the previous list of i, one slot per lane (for the history carry-over below)
+    const int on = old_n[i];
+    const int oldj = (lane < on) ? old_nbr[i * kNB + lane] : -1;
+    double mi = 0.0, ii = 0.0;
+    if (lane == 0) {
+        double m, I;
+        mass_inertia(g.dim, density, ri, &m, &I);
+        mi = 1.0 / m;
+        ii = 1.0 / I;
+    }
     int bx[3], by[3], bz[3], nbx, nby, nbz = 1;
-    nbx = axis_bins(bin_of(xi[0], g.n[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], bx);
-    nby = axis_bins(bin_of(xi[1], g.n[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], by);
-    if (g.dim == 3) nbz = axis_bins(bin_of(xi[2], g.n[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], bz);
+    nbx = axis_bins(bin_of(xi[0], g.bscale[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], bx);
+    nby = axis_bins(bin_of(xi[1], g.bscale[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], by);
+    if (g.dim == 3) nbz = axis_bins(bin_of(xi[2], g.bscale[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], bz);
     else bz[0] = 0;
     // the (up to 27) neighbouring bins: lane b holds bin b and its slot count, then a warp
     // prefix sum lets the lanes walk all slots of all bins 32 at a time
@@ -189,28 +201,31 @@ __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, co
     __syncwarp();
     if (lane < cnt) s_buf[warp][rank] = j;
     __syncwarp();
+    j = (lane < cnt) ? s_buf[warp][lane] : -2;
+    // carry each pair's history over from the previous list of i: the slot whose neighbour
+    // is j (lists hold each neighbour once)
+    int found = -1;
+    for (int q = 0; q < on; ++q) {
+        const int v = __shfl_sync(kFullMask, oldj, q);
+        if (v == j) found = q;
+    }
     if (lane < cnt) {
-        j = s_buf[warp][lane];
-        // carry the pair's history from the previous (sorted) list of i
-        const int on = old_n[i];
-        int lo = 0, hi = on - 1, found = -1;
-        while (lo <= hi) {
-            const int mid = (lo + hi) >> 1;
-            const int v = old_nbr[i * kNB + mid];
-            if (v == j) { found = mid; break; }
-            if (v < j) lo = mid + 1; else hi = mid - 1;
-        }
         new_nbr[i * kNB + lane] = j;
-        for (int h = 0; h < kH; ++h)
-            new_hist[((size_t)i * kNB + lane) * kH + h] = (found >= 0) ? old_hist[((size_t)i * kNB + found) * kH + h] : 0.0f;
+        float4 *dst = reinterpret_cast<float4 *>(new_hist + ((size_t)i * kNB + lane) * kH);
+        if (found >= 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(old_hist + ((size_t)i * kNB + found) * kH);
+            dst[0] = src[0];
+            dst[1] = src[1];
+        } else {
+            dst[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            dst[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
     }
     if (lane == 0) {
         new_n[i] = cnt;
         for (int a = 0; a < 3; ++a) Xref[3 * i + a] = xi[a];
-        double m, I;
-        mass_inertia(g.dim, density, ri, &m, &I);
-        minv[2 * i] = 1.0 / m;
-        minv[2 * i + 1] = 1.0 / I;
+        minv[2 * i] = mi;
+        minv[2 * i + 1] = ii;
     }
 }
 
@@ -621,6 +636,7 @@ static lbm_status dem_setup_bins(dem_ctx *d) {
     for (int a = 0; a < 3; ++a) {
         d->g.nb[a] = (a < d->g.dim) ? (int)(fl->g.n[a] / side) : 1;
         if (d->g.nb[a] < 1) d->g.nb[a] = 1;
+        d->g.bscale[a] = (double)d->g.nb[a] / fl->g.n[a];
         nb *= d->g.nb[a];
     }
     // bin capacity from the densest possible packing of the smallest admissible particles
