@@ -13,22 +13,30 @@ namespace psc {
 // Tile ranges along one axis covered by the cell interval [lo, hi] (cell centres within
 // r + h of the particle centre). Periodic axes wrap (at most two pieces, merged when they
 // meet); wall axes clip to the lattice. Returns the number of ranges (0..2).
-__device__ __forceinline__ int axis_tile_ranges(long long lo, long long hi, int n, int t, int nt,
-                                                int periodic, int *a, int *b) {
+__device__ __forceinline__ int axis_tile_ranges(int lo, int hi, int n, int t, int nt, int periodic, int *a,
+                                                int *b) {
     if (periodic) {
         if (hi - lo + 1 >= n) { a[0] = 0; b[0] = nt - 1; return 1; }
-        const long long A = ((lo % n) + n) % n, B = ((hi % n) + n) % n;
-        if (A <= B) { a[0] = (int)(A / t); b[0] = (int)(B / t); return 1; }
-        const int thi = (int)(A / t), tlo = (int)(B / t);
+        const int A = ((lo % n) + n) % n, B = ((hi % n) + n) % n;
+        if (A <= B) { a[0] = A / t; b[0] = B / t; return 1; }
+        const int thi = A / t, tlo = B / t;
         if (tlo >= thi) { a[0] = 0; b[0] = nt - 1; return 1; }
         a[0] = 0; b[0] = tlo; a[1] = thi; b[1] = nt - 1;
         return 2;
     }
-    const long long A = lo < 0 ? 0 : lo, B = hi > n - 1 ? n - 1 : hi;
+    const int A = lo < 0 ? 0 : lo, B = hi > n - 1 ? n - 1 : hi;
     if (A > B) return 0;
-    a[0] = (int)(A / t); b[0] = (int)(B / t);
+    a[0] = A / t; b[0] = B / t;
     return 1;
 }
+
+// The k-th tile (0 <= k < length of all ranges) of one axis.
+__device__ __forceinline__ int axis_tile(int k, int nr, const int *a, const int *b) {
+    const int l0 = b[0] - a[0] + 1;
+    return (nr < 2 || k < l0) ? a[0] + k : a[1] + (k - l0);
+}
+
+constexpr int kBinBatch = 8;   // tiles whose slot atomics one thread has in flight at once
 
 __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,25 +48,42 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
             pd.Pf[2 * p + 1] = make_float4((float)pd.U[3 * p + 2], (float)pd.Om[3 * p], (float)pd.Om[3 * p + 1],
                                            (float)pd.Om[3 * p + 2]);
         }
-        int ra[3][2], rb[3][2], nr[3];
+        int ra[3][2], rb[3][2], nr[3], len[3];
         const double r = pd.R[p];
         for (int ax = 0; ax < 3; ++ax) {
-            if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; continue; }
+            if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; len[ax] = 1; continue; }
             const double X = pd.X[3 * p + ax];
-            const long long lo = (long long)ceil(X - r - h), hi = (long long)floor(X + r + h);
+            const int lo = (int)ceil(X - r - h), hi = (int)floor(X + r + h);
             nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
+            len[ax] = 0;
+            for (int k = 0; k < nr[ax]; ++k) len[ax] += rb[ax][k] - ra[ax][k] + 1;
         }
-        for (int iz = 0; iz < nr[2]; ++iz)
-        for (int tz = ra[2][iz]; tz <= rb[2][iz]; ++tz)
-        for (int iy = 0; iy < nr[1]; ++iy)
-        for (int ty = ra[1][iy]; ty <= rb[1][iy]; ++ty)
-        for (int ix = 0; ix < nr[0]; ++ix)
-        for (int tx = ra[0][ix]; tx <= rb[0][ix]; ++tx) {
-            const long long tile = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
-            const int slot = atomicAdd(&tl.count[tile], 1);
-            if (slot < tl.cap) tl.list[tile * tl.cap + slot] = p;
-            else if (slot == tl.cap) atomicAdd(&tl.stats[0], 1);
-            mx = max(mx, slot + 1);
+        // every tile of the box, kBinBatch at a time: the slot atomics of a batch are
+        // independent, so their round trips overlap
+        const int total = len[0] * len[1] * len[2];
+        for (int k0 = 0; k0 < total; k0 += kBinBatch) {
+            long long tile[kBinBatch];
+            int slot[kBinBatch];
+#pragma unroll
+            for (int q = 0; q < kBinBatch; ++q) {
+                const int k = k0 + q;
+                if (k < total) {
+                    const int kx = k % len[0], kyz = k / len[0];
+                    const int tx = axis_tile(kx, nr[0], ra[0], rb[0]);
+                    const int ty = axis_tile(kyz % len[1], nr[1], ra[1], rb[1]);
+                    const int tz = axis_tile(kyz / len[1], nr[2], ra[2], rb[2]);
+                    tile[q] = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+                    slot[q] = atomicAdd(&tl.count[tile[q]], 1);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kBinBatch; ++q) {
+                if (k0 + q < total) {
+                    if (slot[q] < tl.cap) tl.list[tile[q] * tl.cap + slot[q]] = p;
+                    else if (slot[q] == tl.cap) atomicAdd(&tl.stats[0], 1);
+                    mx = max(mx, slot[q] + 1);
+                }
+            }
         }
     }
     // the largest count: one atomic per warp, not per (particle, tile)

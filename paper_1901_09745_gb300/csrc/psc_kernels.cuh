@@ -259,15 +259,16 @@ __device__ __forceinline__ void write_record(T *rec, const Geom &g, const Parts 
     for (int a = 0; a < 3; ++a) {
         T rel = (T)0;
         if (a < L::D) {
-            double d = pd.X[3 * id + a] - (double)org[a];
+            const double x = pd.X[3 * id + a];
+            int shift = org[a];
             if (g.periodic[a]) {
-                // minimum image with respect to the tile centre
-                const double cen = 0.5 * (ext[a] - 1);
-                double e = d - cen;
-                e -= (double)g.n[a] * rint(e * g.inv_n[a]);
-                d = e + cen;
+                // minimum image with respect to the tile centre; the image is decided in
+                // FP32 (candidates lie far from the half-box distance where it could
+                // differ), and X - (origin + image shift) is one exact FP64 subtraction
+                const float e = (float)x - ((float)org[a] + 0.5f * (float)(ext[a] - 1));
+                shift += g.n[a] * (int)rintf(e * (float)g.inv_n[a]);
             }
-            rel = (T)d;
+            rel = (T)(x - (double)shift);
         }
         rec[R_PX + a] = rel;
     }
