@@ -59,6 +59,8 @@ struct DemBufs {
     const double *X, *U, *Om, *R;   // state at the start of the sub-step
     const float4 *Xf;               // FP32 copy (x, y, z, r) of the same positions
     float4 *Xfo;                    // FP32 copy of the new positions
+    const float4 *Vf;               // FP32 copy of U, Omega: [n][2] {Ux, Uy, Uz, Ox}, {Oy, Oz, 0, 0}
+    float4 *Vfo;                    // the same of the new velocities
     double *Xo, *Uo, *Omo;          // state at its end
     const double *Ff, *Tf;          // hydrodynamic force / torque (frozen)
     const double *Xref;             // positions when the neighbour list was built
@@ -76,11 +78,13 @@ __device__ __forceinline__ int bin_of(double x, double bscale, int nb, int perio
     return b;
 }
 
-__global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, float4 *Xf, int *count,
-                          int *list, int *flags) {
+__global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, const double *U,
+                          const double *Om, float4 *Xf, float4 *Vf, int *count, int *list, int *flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     Xf[i] = make_float4((float)X[3 * i], (float)X[3 * i + 1], (float)X[3 * i + 2], (float)R[i]);
+    Vf[2 * i] = make_float4((float)U[3 * i], (float)U[3 * i + 1], (float)U[3 * i + 2], (float)Om[3 * i]);
+    Vf[2 * i + 1] = make_float4((float)Om[3 * i + 1], (float)Om[3 * i + 2], 0.0f, 0.0f);
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -406,8 +410,9 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         ri = b.R[i];
         const float4 pif = b.Xf[i];
         const float imi = (float)b.minv[2 * i];
-        const float uif[3] = {(float)ui[0], (float)ui[1], (float)ui[2]};
-        const float oif[3] = {(float)oi[0], (float)oi[1], (float)oi[2]};
+        const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
+        const float uif[3] = {vi0.x, vi0.y, vi0.z};
+        const float oif[3] = {vi0.w, vi1.x, vi1.y};
         const int nn = b.nbr_n[i];
         if (sub == 0) {
             // the integration's inputs, loaded before the contact loop's stores
@@ -500,8 +505,9 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             float hl[kH];
             for (int k = 0; k < kH; ++k) hl[k] = hp[k];
             float fo[3], to[3];
-            const float ujf[3] = {(float)b.U[3 * j], (float)b.U[3 * j + 1], (float)b.U[3 * j + 2]};
-            const float ojf[3] = {(float)b.Om[3 * j], (float)b.Om[3 * j + 1], (float)b.Om[3 * j + 2]};
+            const float4 vj0 = b.Vf[2 * j], vj1 = b.Vf[2 * j + 1];
+            const float ujf[3] = {vj0.x, vj0.y, vj0.z};
+            const float ojf[3] = {vj0.w, vj1.x, vj1.y};
             if (contact_on_i(ph, dim, contact, nv, dnf, pif.w, pj.w, imi, imj, uif, ujf, oif, ojf, hl, fo, to, &fail)) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
@@ -551,6 +557,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) { b.Xo[3 * i + a] = xn[a]; b.Uo[3 * i + a] = un[a]; b.Omo[3 * i + a] = on[a]; }
     b.Xfo[i] = make_float4((float)xn[0], (float)xn[1], (float)xn[2], (float)ri);
+    b.Vfo[2 * i] = make_float4((float)un[0], (float)un[1], (float)un[2], (float)on[0]);
+    b.Vfo[2 * i + 1] = make_float4((float)on[1], (float)on[2], 0.0f, 0.0f);
 }
 
 }  // namespace
@@ -564,10 +572,11 @@ struct dem_ctx {
     DemPhys ph;
     double *X2, *U2, *Om2, *Xref, *minv;
     float4 *Xf[2];           // FP32 copies of the positions (current, next)
+    float4 *Vf[2];           // FP32 copies of the velocities and spins (current, next)
     float reject;
     // CUDA graph of one dem_step call (even sub-step counts), one per neighbour-list parity
     cudaGraphExec_t gexec[2];
-    const void *gkey[2][16];
+    const void *gkey[2][17];
     int gsub[2];
     int *bin_count, *bin_list;
     long long nbins;
@@ -585,6 +594,7 @@ void dem_release(dem_ctx *d) {
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
     dfree((void **)&d->minv);
     dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
+    dfree((void **)&d->Vf[0]); dfree((void **)&d->Vf[1]);
     for (int k = 0; k < 2; ++k) if (d->gexec[k]) cudaGraphExecDestroy(d->gexec[k]);
     dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
@@ -608,10 +618,13 @@ static lbm_status dem_reserve(dem_ctx *d) {
     dfree((void **)&d->X2); dfree((void **)&d->U2); dfree((void **)&d->Om2); dfree((void **)&d->Xref);
     dfree((void **)&d->minv);
     dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
+    dfree((void **)&d->Vf[0]); dfree((void **)&d->Vf[1]);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     const size_t v = (size_t)cap * 3 * sizeof(double);
     DCK(cudaMalloc(&d->Xf[0], (size_t)cap * sizeof(float4)), "cudaMalloc(DEM FP32 positions)");
     DCK(cudaMalloc(&d->Xf[1], (size_t)cap * sizeof(float4)), "cudaMalloc(DEM FP32 positions)");
+    DCK(cudaMalloc(&d->Vf[0], (size_t)cap * 2 * sizeof(float4)), "cudaMalloc(DEM FP32 velocities)");
+    DCK(cudaMalloc(&d->Vf[1], (size_t)cap * 2 * sizeof(float4)), "cudaMalloc(DEM FP32 velocities)");
     DCK(cudaMalloc(&d->minv, (size_t)cap * 2 * sizeof(double)), "cudaMalloc(DEM inverse mass)");
     DCK(cudaMalloc(&d->X2, v), "cudaMalloc(DEM X)");
     DCK(cudaMalloc(&d->U2, v), "cudaMalloc(DEM U)");
@@ -712,7 +725,8 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps, int cur) {
     const int nx = cur ^ 1;
     cudaError_t e = cudaMemsetAsync(d->bin_count, 0, (size_t)d->nbins * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_dem_bin<<<(n + 127) / 128, 128, 0, s>>>(d->g, n, fl->dX, fl->dR, d->Xf[0], d->bin_count, d->bin_list,
+    k_dem_bin<<<(n + 127) / 128, 128, 0, s>>>(d->g, n, fl->dX, fl->dR, fl->dU, fl->dOm, d->Xf[0], d->Vf[0],
+                                               d->bin_count, d->bin_list,
                                                fl->flags);
     k_dem_nbr<<<(n + 7) / 8, 256, 0, s>>>(d->g, n, fl->dX, fl->dR, d->Xf[0], d->bin_count, d->bin_list,
                                            d->nbr_n[cur], d->nbr[cur], d->hist[cur], d->nbr_n[nx], d->nbr[nx],
@@ -734,8 +748,8 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps, int cur) {
     double *X[2] = {fl->dX, d->X2}, *U[2] = {fl->dU, d->U2}, *Om[2] = {fl->dOm, d->Om2};
     for (int k = 0; k < substeps; ++k) {
         const int src = k & 1, dst = src ^ 1;
-        b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src];
-        b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst];
+        b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src]; b.Vf = d->Vf[src];
+        b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst]; b.Vfo = d->Vf[dst];
         if (d->g.dim == 2) k_dem_substep<2><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
         else k_dem_substep<3><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
     }
@@ -773,14 +787,14 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     DCK(cudaStreamIsCapturing(fl->stream, &cs), "cudaStreamIsCapturing");
     unsigned rbits;
     memcpy(&rbits, &d->reject, sizeof(rbits));
-    const void *key[16] = {fl->dX, fl->dU, fl->dOm, fl->dR, fl->dF, fl->dT, d->X2, d->U2, d->Om2, d->Xf[0],
+    const void *key[17] = {d->Vf[0], fl->dX, fl->dU, fl->dOm, fl->dR, fl->dF, fl->dT, d->X2, d->U2, d->Om2, d->Xf[0],
                            d->minv, d->bin_count, (const void *)(size_t)d->n, (const void *)(size_t)rbits,
                            (const void *)(size_t)(d->g.nb[0] + 4096LL * (d->g.nb[1] + 4096LL * d->g.nb[2])),
                            (const void *)(size_t)d->g.bin_cap};
     bool replayed = false;
     if (substeps % 2 == 0 && cs == cudaStreamCaptureStatusNone) {
         bool same = d->gexec[cur] && d->gsub[cur] == substeps;
-        for (int k = 0; same && k < 16; ++k) same = (d->gkey[cur][k] == key[k]);
+        for (int k = 0; same && k < 17; ++k) same = (d->gkey[cur][k] == key[k]);
         if (!same) {
             if (d->gexec[cur]) { cudaGraphExecDestroy(d->gexec[cur]); d->gexec[cur] = NULL; }
             cudaGraph_t graph = NULL;
@@ -793,7 +807,7 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
             cudaGraphDestroy(graph);
             DCK(ei, "cudaGraphInstantiate");
             d->gsub[cur] = substeps;
-            for (int k = 0; k < 16; ++k) d->gkey[cur][k] = key[k];
+            for (int k = 0; k < 17; ++k) d->gkey[cur][k] = key[k];
         }
         DCK(cudaGraphLaunch(d->gexec[cur], fl->stream), "cudaGraphLaunch");
         replayed = true;
