@@ -38,6 +38,17 @@ __device__ __forceinline__ int axis_tile(int k, int nr, const int *a, const int 
 
 constexpr int kBinBatch = 8;   // tiles whose slot atomics one thread has in flight at once
 
+// Distance along one axis from x to the cell centres a..b of a tile (minimum image on a
+// periodic axis of length n).
+__device__ __forceinline__ float axis_gap(float x, float a, float b, float n, int periodic) {
+    float d = fmaxf(fmaxf(a - x, x - b), 0.0f);
+    if (periodic) {
+        d = fminf(d, fmaxf(fmaxf(a - (x + n), (x + n) - b), 0.0f));
+        d = fminf(d, fmaxf(fmaxf(a - (x - n), (x - n) - b), 0.0f));
+    }
+    return d;
+}
+
 __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int mx = 0;   // largest slot taken by this thread
@@ -50,6 +61,11 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
         }
         int ra[3][2], rb[3][2], nr[3], len[3];
         const double r = pd.R[p];
+        // a tile is a candidate only if some cell centre of it can lie within r + h (the
+        // distance from the particle to the tile's box of cell centres; a margin far above
+        // the FP32 rounding of these distances keeps the test conservative)
+        const float reach = (float)(r + h) + 0.01f;
+        const float xp[3] = {(float)pd.X[3 * p], (float)pd.X[3 * p + 1], dim == 3 ? (float)pd.X[3 * p + 2] : 0.0f};
         for (int ax = 0; ax < 3; ++ax) {
             if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; len[ax] = 1; continue; }
             const double X = pd.X[3 * p + ax];
@@ -72,13 +88,25 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
                     const int tx = axis_tile(kx, nr[0], ra[0], rb[0]);
                     const int ty = axis_tile(kyz % len[1], nr[1], ra[1], rb[1]);
                     const int tz = axis_tile(kyz / len[1], nr[2], ra[2], rb[2]);
-                    tile[q] = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
-                    slot[q] = atomicAdd(&tl.count[tile[q]], 1);
+                    tile[q] = -1;
+                    const int org[3] = {tx * g.t[0], ty * g.t[1], tz * g.t[2]};
+                    float d2 = 0.0f;
+#pragma unroll
+                    for (int ax = 0; ax < 3; ++ax) {
+                        if (ax >= dim) break;
+                        const float gap = axis_gap(xp[ax], (float)org[ax], (float)min(org[ax] + g.t[ax], g.n[ax]) - 1.0f,
+                                                   (float)g.n[ax], g.periodic[ax]);
+                        d2 += gap * gap;
+                    }
+                    if (d2 <= reach * reach) {
+                        tile[q] = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+                        slot[q] = atomicAdd(&tl.count[tile[q]], 1);
+                    }
                 }
             }
 #pragma unroll
             for (int q = 0; q < kBinBatch; ++q) {
-                if (k0 + q < total) {
+                if (k0 + q < total && tile[q] >= 0) {
                     if (slot[q] < tl.cap) tl.list[tile[q] * tl.cap + slot[q]] = p;
                     else if (slot[q] == tl.cap) atomicAdd(&tl.stats[0], 1);
                     mx = max(mx, slot[q] + 1);
