@@ -152,7 +152,7 @@ __device__ __forceinline__ void store_pair(S *__restrict__ fout, const long long
     if (actB) Store<S>::str(fout, iB, b);
 }
 
-template <class L> constexpr int pair_nslot() { return (L::D == 2) ? 4 : 2; }
+template <class L> constexpr int pair_nslot() { return 4; }
 
 template <class L, typename T> __host__ __device__ constexpr size_t pair_smem_bytes() {
     // records [2][kPairCap][RW] | partials [2][kPWarps][kPairCap][NC] | brackets
