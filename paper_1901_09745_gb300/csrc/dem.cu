@@ -424,8 +424,17 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         for (int s = sub; s < nn; s += kLPP) {
             const int j = b.nbr[i * kNB + s];
             float *hp = b.hist + ((size_t)i * kNB + s) * kH;
-            // FP32 pre-filter on the position copies: pairs clearly apart skip the FP64 work
+            // everything the pair may need, loaded at once (one round trip after j)
             const float4 pj = b.Xf[j];
+            double xj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) if (a < dim) xj[a] = b.X[3 * j + a];
+            const double rj = b.R[j];
+            const float4 vj0 = b.Vf[2 * j], vj1 = b.Vf[2 * j + 1];
+            const float imj = (float)b.minv[2 * j];
+            float4 *hp4 = reinterpret_cast<float4 *>(hp);
+            const float4 h0 = hp4[0], h1 = hp4[1];
+            // FP32 pre-filter on the position copies: pairs clearly apart skip the FP64 work
             float df[3] = {pj.x - pif.x, pj.y - pif.y, pj.z - pif.z};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -436,11 +445,11 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                     else if (df[a] < -half) df[a] += (float)g.n[a];
                 }
             }
-            const bool was = hp[7] != 0.0f;
+            const bool was = h1.w != 0.0f;
             const float dpre = (pif.w + pj.w) - sqrtf(df[0] * df[0] + df[1] * df[1] + df[2] * df[2]);
             if (dpre < -b.reject) {
                 // provably out of contact (the margin dwarfs the FP32 error)
-                if (was) for (int k = 0; k < kH; ++k) hp[k] = 0.0f;
+                if (was) { hp4[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); hp4[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
                 continue;
             }
             // separation X_j - X_i in FP64 (exact subtraction), minimum image; the periodic
@@ -449,14 +458,13 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 if (a >= dim) break;
-                d[a] = __dsub_rn(b.X[3 * j + a], xi[a]);
+                d[a] = __dsub_rn(xj[a], xi[a]);
                 if (g.periodic[a]) {
                     const float half = 0.5f * (float)g.n[a], v = (float)d[a];
                     if (v > half) d[a] = __dsub_rn(d[a], (double)g.n[a]);
                     else if (v < -half) d[a] = __dadd_rn(d[a], (double)g.n[a]);
                 }
             }
-            const double rj = b.R[j];
             // d^2 in FP64 with IEEE-rounded operations (bit-identical at both ends and in a
             // CPU reference), S = r_i + r_j. delta_N = S - |d| is formed, as the reference
             // forms it, only for pairs within a few ulps of touching: elsewhere the sign of
@@ -501,11 +509,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                 }
             }
             const float nv[3] = {(float)d[0] * inv, (float)d[1] * inv, (float)d[2] * inv};
-            const float imj = (float)b.minv[2 * j];
-            float hl[kH];
-            for (int k = 0; k < kH; ++k) hl[k] = hp[k];
+            float hl[kH] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
             float fo[3], to[3];
-            const float4 vj0 = b.Vf[2 * j], vj1 = b.Vf[2 * j + 1];
             const float ujf[3] = {vj0.x, vj0.y, vj0.z};
             const float ojf[3] = {vj0.w, vj1.x, vj1.y};
             if (contact_on_i(ph, dim, contact, nv, dnf, pif.w, pj.w, imi, imj, uif, ujf, oif, ojf, hl, fo, to, &fail)) {
@@ -515,7 +520,10 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                     if (used(3 + a)) acc[3 + a] += (double)to[a];
                 }
             }
-            if (was || hl[7] != 0.0f) for (int k = 0; k < kH; ++k) hp[k] = hl[k];
+            if (was || hl[7] != 0.0f) {
+                hp4[0] = make_float4(hl[0], hl[1], hl[2], hl[3]);
+                hp4[1] = make_float4(hl[4], hl[5], hl[6], hl[7]);
+            }
         }
     }
     // combine the kLPP partial sums (fixed butterfly order)
