@@ -326,11 +326,15 @@ def run_ours(args, rank, local_rank, world):
                    "l2": "inputs larger than L2: %.0f MB of populations read+written per step"
                          % (bytes_per_launch / 1e6),
                    "parallelism": "replicas (one independent domain per GPU)"},
-        "roofline": {"bound": "hbm", "kernel": "k_collide_stream", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": "k_collide_stream with k_fluid_pair and k_collide_overflow "
+                                               "(one collide-stream step)", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
-                     "avg_launch_us": round(k_avg_s * 1e6, 2), "launches_timed": k_n},
+                     "avg_launch_us": round(k_avg_s * 1e6, 2), "launches_timed": k_n,
+                     # the measured DRAM bytes of a step (ncu) over the same duration
+                     "dram_achieved": round(traffic / k_avg_s / 1e9, 1) if traffic else None,
+                     "dram_frac": round(traffic / k_avg_s / 1e9 / peak, 4) if traffic else None},
         "e2e": {"value": round(ncell * e2e_steps * world / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(n * 10 * 8), "d2h_bytes_per_step": int(n * 6 * 8),
                 "steps": e2e_steps},
