@@ -877,7 +877,8 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     using T = typename Store<S>::T;
     constexpr int NC = (L::D == 2) ? 3 : 6;
     constexpr bool kSteal = (L::D == 3) || sizeof(T) == 8;
-    constexpr int kSideP = 4, kSideF = 3;     // blocks per SM side by side (2D)
+    // blocks per SM side by side (2D): 4 x 128 threads x 80 registers + 3 x 128 x 64 = 64 K
+    constexpr int kSideP = 4, kSideF = 3;
     const size_t smem = pair_smem_bytes<L, T>();
     const size_t osmem = cs_smem_bytes<T>(tl.cap, NC);
     auto kern = k_collide_stream<L, S, PSC, kSteal>;

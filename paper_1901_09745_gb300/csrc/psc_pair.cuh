@@ -519,7 +519,7 @@ __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__
 // share out the end of the step. Tiles with more than kPairCap candidates are left to
 // k_collide_overflow, which also clears the counters for the next launch.
 template <class L, typename S, int PSC, bool STEAL>
-__global__ void __launch_bounds__(kPThreads, (sizeof(typename Store<S>::T) == 8) ? 2 : ((L::Q == 9) ? 7 : 4))
+__global__ void __launch_bounds__(kPThreads, (sizeof(typename Store<S>::T) == 8) ? 2 : ((L::Q == 9) ? 6 : 4))
 k_collide_stream(const S *__restrict__ fin, S *__restrict__ fout, Geom g,
                  PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
     using T = typename Store<S>::T;
