@@ -95,18 +95,14 @@ __global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, co
     else atomicAdd(&flags[2], 1);
 }
 
-// Distinct bin indices along one axis around b (wrapping, clipping, no duplicates).
-__device__ __forceinline__ int axis_bins(int b, int nb, int periodic, int *out) {
-    int k = 0;
-    for (int o = -1; o <= 1; ++o) {
-        int c = b + o;
-        if (periodic) { c %= nb; if (c < 0) c += nb; }
-        else if (c < 0 || c >= nb) continue;
-        bool dup = false;
-        for (int q = 0; q < k; ++q) dup |= (out[q] == c);
-        if (!dup) out[k++] = c;
-    }
-    return k;
+// The distinct bins along one axis around bin b: n of them, the k-th at axis_at(k, ...)
+// (periodic: b - 1, b, b + 1 wrapped, fewer when nb < 3; walls: clipped to the lattice).
+__device__ __forceinline__ void axis_span(int b, int nb, int periodic, int &start, int &n) {
+    if (periodic) { start = b - 1 + nb; n = nb < 3 ? nb : 3; }
+    else { start = b > 0 ? b - 1 : 0; n = (b + 1 < nb ? b + 1 : nb - 1) - start + 1; }
+}
+__device__ __forceinline__ int axis_at(int k, int start, int nb, int periodic) {
+    return periodic ? (start + k) % nb : start + k;
 }
 
 __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I);
@@ -132,18 +128,18 @@ __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, co
         mi = 1.0 / m;
         ii = 1.0 / I;
     }
-    int bx[3], by[3], bz[3], nbx, nby, nbz = 1;
-    nbx = axis_bins(bin_of(xi[0], g.bscale[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], bx);
-    nby = axis_bins(bin_of(xi[1], g.bscale[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], by);
-    if (g.dim == 3) nbz = axis_bins(bin_of(xi[2], g.bscale[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], bz);
-    else bz[0] = 0;
+    int sx, sy, sz = 0, nbx, nby, nbz = 1;
+    axis_span(bin_of(xi[0], g.bscale[0], g.nb[0], g.periodic[0]), g.nb[0], g.periodic[0], sx, nbx);
+    axis_span(bin_of(xi[1], g.bscale[1], g.nb[1], g.periodic[1]), g.nb[1], g.periodic[1], sy, nby);
+    if (g.dim == 3) axis_span(bin_of(xi[2], g.bscale[2], g.nb[2], g.periodic[2]), g.nb[2], g.periodic[2], sz, nbz);
     // the (up to 27) neighbouring bins: lane b holds bin b and its slot count, then a warp
     // prefix sum lets the lanes walk all slots of all bins 32 at a time
     const int nbins = nbx * nby * nbz;
     int mybin = 0, mycnt = 0;
     if (lane < nbins) {
         const int c = lane % nbx, bb = (lane / nbx) % nby, aa = lane / (nbx * nby);
-        mybin = bx[c] + g.nb[0] * (by[bb] + g.nb[1] * bz[aa]);
+        const int cz = (g.dim == 3) ? axis_at(aa, sz, g.nb[2], g.periodic[2]) : 0;
+        mybin = axis_at(c, sx, g.nb[0], g.periodic[0]) + g.nb[0] * (axis_at(bb, sy, g.nb[1], g.periodic[1]) + g.nb[1] * cz);
         mycnt = min(count[mybin], g.bin_cap);
     }
     int incl = mycnt;
