@@ -66,3 +66,28 @@ def test_clock_summary_flags_throttle_reasons():
     s = cs.summary()
     assert s["sm_mhz"] == 2010 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
     assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+
+
+def test_recorded_traffic_only_for_the_sources_it_was_measured_on(tmp_path, monkeypatch):
+    """The roofline's `traffic` comes from the committed ncu summary only while the kernel
+    sources hash to the value recorded with it; otherwise it is reported as null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(
+        {"c2/f32": {"bytes_per_launch": 304.7e6, "source_hash": "abc"},
+         "c3/f32": {"bytes_per_launch": 2797e6, "source_hash": "old"}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    assert bench.recorded_traffic("c2", "f32") == pytest.approx(304.7e6)
+    assert bench.recorded_traffic("c3", "f32") is None        # measured on other sources
+    assert bench.recorded_traffic("c2", "f16") is None        # never measured
+
+
+def test_committed_traffic_entries_are_well_formed():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        d = json.load(fh)
+    for key in ("c2/f32", "c3/f32"):
+        e = d[key]
+        assert e["bytes_per_launch"] > 0 and len(e["source_hash"]) == 16
+        assert sum(e["kernels"].values()) == pytest.approx(e["bytes_per_launch"], rel=1e-3)
