@@ -47,7 +47,7 @@ typedef enum {
     LBM_ERR_ARG = 1,            /* invalid argument (message in lbm_last_error) */
     LBM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     LBM_ERR_OOM = 3,            /* device allocation failed */
-    LBM_ERR_UNSUPPORTED = 4,    /* valid request this build does not provide */
+    LBM_ERR_UNSUPPORTED = 4,    /* valid request the library does not provide */
     LBM_ERR_UNSTABLE = 5,       /* a cell reached a non-positive or NaN density */
     LBM_ERR_OVERFLOW = 6,       /* a fixed-capacity list overflowed */
     LBM_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
