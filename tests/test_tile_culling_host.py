@@ -1,0 +1,62 @@
+"""The binning kernel makes a particle a tile's candidate only if the distance from its
+centre to the tile's box of cell centres (minimum image on periodic axes) is at most
+r + h + 0.01 (k_bin, in FP32). This checks on the host, by brute force over the cells,
+that the test never drops a tile holding a cell centre within r + h of the particle
+(where Table 1 can give a non-zero solid fraction), in 2D and 3D, across periodic faces
+and at walls."""
+import numpy as np
+
+
+def _axis_gap(x, a, b, n, periodic):
+    f = np.float32
+    x, a, b, n = f(x), f(a), f(b), f(n)
+    d = max(max(a - x, x - b), f(0))
+    if periodic:
+        d = min(d, max(max(a - (x + n), (x + n) - b), f(0)))
+        d = min(d, max(max(a - (x - n), (x - n) - b), f(0)))
+    return d
+
+
+def _kept(X, reach, org, tshape, n, periodic, dim):
+    d2 = np.float32(0)
+    for ax in range(dim):
+        g = _axis_gap(X[ax], org[ax], min(org[ax] + tshape[ax], n[ax]) - 1, n[ax], periodic[ax])
+        d2 += g * g
+    return d2 <= np.float32(reach) * np.float32(reach)
+
+
+def _needed(X, r, h, org, tshape, n, periodic, dim):
+    axes = []
+    for ax in range(dim):
+        c = np.arange(org[ax], min(org[ax] + tshape[ax], n[ax]), dtype=float)
+        dc = c - X[ax]
+        if periodic[ax]:
+            dc -= n[ax] * np.rint(dc / n[ax])
+        axes.append(dc)
+    grids = np.meshgrid(*axes, indexing="ij")
+    d2 = sum(g * g for g in grids)
+    return bool(np.any(d2 < (r + h) ** 2))
+
+
+def test_tile_culling_keeps_every_tile_a_shell_reaches():
+    rng = np.random.default_rng(77)
+    h = 1.0
+    checked = 0
+    for dim, tshape in ((2, (32, 8, 1)), (3, (32, 4, 2))):
+        for _ in range(60):
+            n = [int(v) for v in rng.integers(40, 90, 3)]
+            if dim == 2:
+                n[2] = 1
+            periodic = [int(v) for v in rng.integers(0, 2, 3)]
+            r = rng.uniform(3.0, 9.0)
+            X = rng.uniform(0, 1, 3) * np.array(n, dtype=float)
+            reach = np.float32(r + h) + np.float32(0.01)
+            nt = [(n[a] + tshape[a] - 1) // tshape[a] for a in range(3)]
+            for tz in range(nt[2] if dim == 3 else 1):
+                for ty in range(nt[1]):
+                    for tx in range(nt[0]):
+                        org = (tx * tshape[0], ty * tshape[1], tz * tshape[2])
+                        if _needed(X, r, h, org, tshape, n, periodic, dim):
+                            assert _kept(X, reach, org, tshape, n, periodic, dim), (dim, n, periodic, r, X, org)
+                            checked += 1
+    assert checked > 500
