@@ -255,9 +255,11 @@ __device__ __forceinline__ float jkr_s(float t, int *fail, float s_prev) {
     const float sc = 0.55032120814910446f;            // 6^(-1/3)
     const float tau = fmaxf(t + 0.5f * sc, 0.0f);      // t - t_c
     const float c2 = 6.0f * sc * sc, c1 = 4.0f * sc;
-    // the previous sub-step's root when there is one (Newton from the left of the root
-    // overshoots once to the right, then decreases monotonically as below)
-    float e = (tau > 0.0f && s_prev > sc) ? s_prev - sc : fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
+    // the previous sub-step's root when there is one, kept within [e0 / 4, e0] of the cold
+    // guess e0 (which lies right of the root): Newton from the left of the root overshoots
+    // once to the right (by at most about root^2 / start), then decreases monotonically
+    const float e0 = fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
+    float e = (tau > 0.0f && s_prev > sc) ? fminf(fmaxf(s_prev - sc, 0.25f * e0), e0) : e0;
     if (tau > 0.0f) {
         int it = 0;
         for (; it < 40; ++it) {
