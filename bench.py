@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dem", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-d3", action="store_true", help="skip the D3Q19 workloads (c3, c3dense, c5, c5dense)")
+    ap.add_argument("--d3", default="c3,c3dense,c5,c5dense", help="D3Q19 workloads to time")
     return ap.parse_args(argv)
 
 
@@ -184,17 +186,23 @@ WORKLOAD_TEXT = {
           "solid fraction 0.40, velocities N(0,1e-3), JKR DEM 10 sub-steps per LBM step",
     "c3": "D3Q19 256^3 periodic, tau 0.6, 2000 static spheres r=6, body force 1e-6",
     "c3dense": "D3Q19 256^3 periodic, tau 0.6, 5563 static spheres r=6 (solid fraction 0.3)",
-    "c5": "D3Q19 512^3 channel (walls z), tau 0.55, 50000 spheres r~U(3,8)",
+    "c5": "D3Q19 512^3 channel (walls z), tau 0.55, 50000 spheres r~U(3,8) (random sequential addition, "
+          "solid fraction 0.31)",
+    "c5dense": "D3Q19 512^3 channel (walls z), tau 0.55, 71830 spheres r~U(3,8) at solid fraction 0.45 "
+               "(growth and relaxation, many near-contacts), JKR DEM 10 sub-steps per LBM step",
     "c4": "D3Q19 128^3 periodic, tau 0.7, 200 static spheres r=5, body force 1e-6, 500 steps, "
           "checkpoint every 50",
 }
-DEFAULT_STORAGE = {"c2": "f32", "c3": "f32", "c3dense": "f32", "c5": "f16", "c4": "f32", "c1": "f64"}
+DEFAULT_STORAGE = {"c2": "f32", "c3": "f32", "c3dense": "f32", "c5": "f16", "c5dense": "f16", "c4": "f32",
+                   "c1": "f64"}
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 TIMING_EVERY = 8
 
 
 def dem_defaults(w):
-    """Contact-model parameters of the coupled workloads, in lattice units (see DESIGN)."""
+    """Contact-model parameters of the coupled workloads, in lattice units: E = 2, Poisson
+    ratio 0.3, surface energy 2e-4, particle/fluid density ratio 3, friction 0.3, critical
+    rolling angle 0.01, normal damping 0.3."""
     return dict(E=2.0, poisson=0.3, gamma=2e-4, density=3.0, mu_f=0.3, theta_crit=0.01,
                 alpha_n=0.3, k_t_scale=1.0, eta_t_scale=1.0, dt_dem=1.0 / w["dem"]["substeps"],
                 gravity=(0.0, 0.0, 0.0), adhesive=1)
@@ -297,6 +305,9 @@ def run_ours(args, rank, local_rank, world):
                                "GBs": round(byt / (us * 1e-6) / 1e9, 1)}
 
     adjoint = adjoint_timing(P, torch, stream) if (rank == 0 and not args.no_adjoint) else None
+    peak0, _ = load_peaks()
+    d3 = (d3_workloads(P, torch, stream, [v for v in args.d3.split(",") if v], peak0)
+          if (rank == 0 and not args.no_d3) else None)
 
     if rank != 0:
         return None
@@ -346,7 +357,106 @@ def run_ours(args, rank, local_rank, world):
     }
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if d3:
+        line["workloads"] = d3
     return line
+
+
+def collide_stream_us(P, w, storage, stream, steps):
+    """Mean duration (us) of one collide-stream step (its kernels, CUDA events on the
+    launching stream) on workload w with static particles, after 3 warm-up steps."""
+    nx, ny, nz = w["n"]
+    ctx = P.lbm_create(w["lattice"], nx, ny, nz, bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                       storage=storage, stream=stream.cuda_stream)
+    P.lbm_set_particles(ctx, w["X"], w["U"], w["Om"], w["r"])
+    P.lbm_step(ctx, 3)
+    P.lbm_kernel_timing(ctx, 1)
+    P.lbm_step(ctx, steps)
+    kms, kn = P.lbm_kernel_timing(ctx, 0)
+    info = P.lbm_get_info(ctx)
+    P.lbm_destroy(ctx)
+    return kms / max(kn, 1) * 1e3, kn, info
+
+
+def d3_workloads(P, torch, stream, names, peak):
+    """The D3Q19 workloads the metric's FP16-against-FP32 comparison is defined on: per
+    workload and storage the collide-stream step's duration, MLUPS and fraction of the
+    measured copy bandwidth (algorithmic bytes 2 Q s per cell); for the dense channel also
+    the coupled step (collide-stream + 10 DEM sub-steps)."""
+    import synth
+    out = {}
+    for name in names:
+        w = synth.workload(name)
+        nx, ny, nz = w["n"]
+        ncell = nx * ny * nz
+        big = ncell > 5e7
+        rec = {"workload": "%s: %s" % (name, WORKLOAD_TEXT.get(name, "")), "cells": ncell,
+               "particles": int(len(w["r"])), "solid_fraction": round(w["solid_fraction"], 4),
+               "default_storage": DEFAULT_STORAGE[name], "storage": {}}
+        for st in ("f32", "f16", "bf16"):
+            us, kn, info = collide_stream_us(P, w, st, stream, 20 if big else 50)
+            byt = 2.0 * w["lattice"] * BYTES[st] * ncell
+            gbs = byt / (us * 1e-6) / 1e9
+            rec["storage"][st] = {"kernel_us": round(us, 2), "launches_timed": kn,
+                                  "kernel_mlups": round(ncell / us, 1), "bytes_per_cell": 2 * w["lattice"] * BYTES[st],
+                                  "GBs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                                  "overflow_tiles": int(info["overflow_tiles"]),
+                                  "max_tile_candidates": int(info["max_tile_candidates"])}
+        s32, s16 = rec["storage"]["f32"]["kernel_us"], rec["storage"]["f16"]["kernel_us"]
+        rec["f16_over_f32_time"] = round(s16 / s32, 3)
+        d = rec["storage"][DEFAULT_STORAGE[name]]
+        rec["roofline"] = {"bound": "hbm", "storage": DEFAULT_STORAGE[name], "achieved": d["GBs"], "peak": peak,
+                           "unit": "GB/s", "frac": d["frac"], "traffic": None,
+                           "algorithmic_bytes_per_launch": 2.0 * w["lattice"] * BYTES[DEFAULT_STORAGE[name]] * ncell,
+                           "avg_launch_us": d["kernel_us"]}
+        if w.get("dem") is not None:
+            rec["coupled"] = coupled_timing(P, torch, stream, w, DEFAULT_STORAGE[name], steps=10)
+        out[name] = rec
+        del w
+    return out
+
+
+def coupled_timing(P, torch, stream, w, storage, steps):
+    """Coupled step (collide-stream + DEM sub-steps) on a D3Q19 workload: time per step with
+    CUDA events on the context's stream, the DEM's share, its counters, and the adhesion
+    scale against the drag (pull-off force F_C = 3 pi gamma R of the smallest pair against
+    the mean hydrodynamic force)."""
+    nx, ny, nz = w["n"]
+    sub = w["dem"]["substeps"]
+    ctx = P.lbm_create(w["lattice"], nx, ny, nz, bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                       storage=storage, stream=stream.cuda_stream)
+    P.lbm_set_particles(ctx, w["X"], w["U"], w["Om"], w["r"])
+    prm = dem_defaults(w)
+    dem = P.dem_create(ctx, **prm)
+    for _ in range(3):
+        P.lbm_step(ctx, 1)
+        P.dem_step(dem, sub)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(steps):
+        P.lbm_step(ctx, 1)
+        P.dem_step(dem, sub)
+    ev[1].record(stream)
+    for _ in range(steps):
+        P.dem_step(dem, sub)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    F, T = P.lbm_get_forces(ctx)
+    info = P.dem_get_info(dem)
+    pairs, _ = P.dem_get_contacts(dem)
+    P.dem_destroy(dem)
+    P.lbm_destroy(ctx)
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    dem_ms = ev[1].elapsed_time(ev[2]) / steps
+    ncell = nx * ny * nz
+    rmin = float(np.min(w["r"]))
+    FC = 3.0 * np.pi * prm["gamma"] * (rmin / 2.0)
+    return {"storage": storage, "ms_per_step": round(ms, 4), "mlups": round(ncell / (ms * 1e3), 1),
+            "dem_ms_per_call": round(dem_ms, 4), "dem_substeps": sub, "contacts": int(len(pairs)),
+            "dem_overflows": int(info["overflows"]), "dem_solve_failures": int(info["solve_failures"]),
+            "skin_violations": int(info["skin_violations"]),
+            "pull_off_force_min": FC, "mean_abs_drag": float(np.mean(np.linalg.norm(F, axis=1)))}
 
 
 def adjoint_timing(P, torch, stream):
@@ -388,54 +498,89 @@ def adjoint_timing(P, torch, stream):
 
 
 # ------------------------------------------------------------------------ CPU oracle
-def oracle_sample(workload, box):
-    """A bounded sub-box of the workload (same solid fraction and radius distribution)."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_sample(workload, box, seed_offset=0):
+    """A bounded sub-box of the workload (same solid fraction and radius distribution);
+    seed_offset draws a different packing (the disjoint samples of the all-core runs)."""
     import synth
     w = synth.workload(workload)
     scale = box / float(w["n"][0])
-    return synth.workload(workload, scale=scale)
+    return synth.workload(workload, scale=scale, seed_offset=seed_offset)
 
 
-def run_oracle_steps(ws, steps):
+def _oracle_worker(task):
+    """One host process: build its own seeded sub-box, run `steps` oracle steps (or as many
+    as fit in `budget_s`), return (lattice updates, seconds)."""
+    workload, box, seed_offset, steps, budget_s = task
     import oracle as O
+    ws = oracle_sample(workload, box, seed_offset)
     p = O.make_params(ws["lattice"], *ws["n"], bc=ws["bc"], tau=ws["tau"], body_force=ws["body_force"])
     f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    ncell = int(np.prod(ws["n"]))
+    O.run(p, f, 1, ws["X"], ws["U"], ws["Om"], ws["r"])          # warm
+    if steps is None:
+        t = time.perf_counter()
+        O.run(p, f, 2, ws["X"], ws["U"], ws["Om"], ws["r"])
+        t1 = (time.perf_counter() - t) / 2.0
+        steps = int(max(2, min(5000, budget_s / max(t1, 1e-6))))
     t = time.perf_counter()
     O.run(p, f, steps, ws["X"], ws["U"], ws["Om"], ws["r"])
-    return time.perf_counter() - t
+    return ncell * steps, time.perf_counter() - t, "x".join(map(str, ws["n"])), steps
 
 
-def cpu_baseline(workload, budget_s=12.0):
-    ws = oracle_sample(workload, 256 if workload in ("c2",) else 48)
-    ncell = int(np.prod(ws["n"]))
-    t1 = run_oracle_steps(ws, 2) / 2.0
-    steps = int(max(2, min(2000, budget_s / max(t1, 1e-6))))
-    t = run_oracle_steps(ws, steps)
-    return {"value": round(ncell * steps / t / 1e6, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%s sub-box %s (same solid fraction and radii), %d LBM steps, static particles, "
-                      "no DEM, FP64, single thread" % (workload, "x".join(map(str, ws["n"])), steps)}
+def _oracle_pool(tasks):
+    """Run the tasks in `len(tasks)` processes started with spawn (a process forked after
+    the GPU was used would inherit its state)."""
+    import multiprocessing as mp
+    import oracle as O
+    O.lib()                       # build the oracle once, before the workers load it
+    with mp.get_context("spawn").Pool(len(tasks)) as pool:
+        return pool.map(_oracle_worker, tasks)
+
+
+def cpu_baseline(workload, budget_s=8.0):
+    """The FP64 oracle as it stands on the host cores: one process on one sub-box, then one
+    process per core, each on its own seeded sub-box of the same solid fraction and radii
+    (the oracle itself is single-threaded and is not changed for this)."""
+    box = 256 if workload in ("c2",) else 48
+    cores = host_cores()
+    one = _oracle_pool([(workload, box, 0, None, budget_s)])[0]
+    allc = _oracle_pool([(workload, box, k, None, budget_s) for k in range(cores)])
+    mlups_1 = one[0] / one[1] / 1e6
+    mlups_all = sum(r[0] for r in allc) / max(r[1] for r in allc) / 1e6
+    return {"value": round(mlups_all, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "value_1core": round(mlups_1, 3),
+            "sample": "%s sub-boxes %s (same solid fraction and radii; a different seeded packing per "
+                      "process), static particles, no DEM, FP64; %d processes x ~%d steps, value = all "
+                      "lattice updates / slowest process time; value_1core = one process alone"
+                      % (workload, one[2], cores, int(np.mean([r[3] for r in allc])))}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step one LBM step of a 512^2 (2D) or 64^3 (3D)
+    sub-box of the workload in every host process (one per core, disjoint seeded
+    sub-boxes); the time of a step is the slowest process's."""
     if rank != 0:
         return None
-    ws = oracle_sample(args.workload, 512 if args.workload == "c2" else 64)
-    ncell = int(np.prod(ws["n"]))
-    for _ in range(min(args.warmup, 1)):
-        run_oracle_steps(ws, 1)
-    total, steps_run = 0.0, 0
-    for _ in range(args.steps):
-        total += run_oracle_steps(ws, 1)
-        steps_run += 1
-        if total > 150.0:   # keep the reference arm within a few minutes
-            break
-    mlups = ncell * steps_run / total / 1e6
-    cb = {"value": round(mlups, 3), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-          "sample": "one LBM step of a %s sub-box of %s per step (static particles, FP64, 1 thread)"
-                    % ("x".join(map(str, ws["n"])), args.workload)}
+    box = 512 if args.workload == "c2" else 64
+    cores = host_cores()
+    steps = max(1, args.steps)
+    res = _oracle_pool([(args.workload, box, k, steps, None) for k in range(cores)])
+    total_lu = sum(r[0] for r in res)
+    t = max(r[1] for r in res)
+    mlups = total_lu / t / 1e6
+    cb = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+          "sample": "%d processes, each %d LBM steps of its own %s sub-box of %s (static particles, FP64)"
+                    % (cores, steps, res[0][2], args.workload)}
     return {"metric": "PSC collide-stream + DEM step throughput (MLUPS)", "value": round(mlups, 3),
-            "unit": "MLUPS", "impl": "reference", "n_gpus": world, "steps": steps_run,
-            "warmup": args.warmup, "ms_per_step": total / steps_run * 1e3, "higher_is_better": True,
+            "unit": "MLUPS", "impl": "reference", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": t / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "%s: %s" % (args.workload, WORKLOAD_TEXT.get(args.workload, ""))},
             "cpu_baseline": cb,

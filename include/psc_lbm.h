@@ -115,8 +115,12 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 
 /* Checkpoint: raw copy of the populations, particles and step counter into a caller
- * buffer (host). With buf = NULL, *used receives the size needed. lbm_load_state
- * restores a buffer written by lbm_save_state of a context with identical parameters. */
+ * buffer (host); when a DEM context is attached (dem_create) and has stepped, also its
+ * neighbour lists and per-contact spring history. With buf = NULL, *used receives the size
+ * needed. lbm_load_state restores a buffer written by lbm_save_state of a context with
+ * identical parameters (and the DEM section into the attached DEM context; without one the
+ * DEM starts again without contact history), so that the run continues exactly as the
+ * saved one did. */
 lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t *used);
 lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size);
 
@@ -222,12 +226,14 @@ lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
  *           contexts: post-collision deviations f_i - w_i, [Q][nz][ny][nx], element type
  *           double / float / half / bfloat16 (FP16 scaled by dev_scale, default 4096), the
  *           bytes lbm_save_state writes after its 64-byte header.
- *   f_out   device buffer of the same size receiving the state after the step (must not
- *           alias f_in). Each buffer must be aligned to its element size.
+ *   f_out   device buffer of the same size receiving the state after the step. f_out ==
+ *           f_in and buffers not aligned to their element size are rejected with
+ *           LBM_ERR_ARG (partly overlapping buffers are not detected: do not pass them).
  *   n, X, U, Omega, radius   particles as for lbm_set_particles, but device pointers; the
  *           caller guarantees the radius and box-size conditions stated there (the device
  *           data is not inspected on the host).
- *   F, T    device buffers (n x 3) receiving the force and torque of this step.
+ *   F, T    device buffers (n x 3) receiving the force and torque of this step. Every
+ *           particle array must be 8-byte aligned (LBM_ERR_ARG otherwise).
  *
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * and creates a second stream and two events there (a D2Q9 step runs two kernels side by

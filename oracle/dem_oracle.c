@@ -8,7 +8,7 @@
  * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU-baseline leg of
  * the benchmark may load this file; it shares nothing with the CUDA library.
  *
- * Readings of what the paper leaves open (also listed in the design notes):
+ * Readings of what the paper leaves open (the CUDA library takes the same readings):
  *  J1 JKR with work of adhesion 2 gamma, consistent with F_C = 3 pi gamma R and Eq. 27:
  *     delta_N = (a0^2/R) [ (a/a0)^2 - (2/3) (a/a0)^(1/2) ]; the contact radius a is taken on
  *     the stable branch a/a0 >= 6^(-2/3), found here by bisection; delta_C = a0^2/(2 6^(1/3) R).

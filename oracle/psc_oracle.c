@@ -20,8 +20,8 @@
  *       streaming, Eq. 1, with periodic wrap and halfway bounce-back walls, Eq. 6
  *   O6  hydrodynamic force and torque per particle, Eq. 14 (or Eq. 11)
  *
- * Readings where the paper is silent, garbled or ambiguous (each is also listed with
- * its justification in the design notes):
+ * Readings where the paper is silent, garbled or ambiguous (the same readings are taken,
+ * in independent code, by the CUDA library):
  *   R1  Eq. 17/19 integrand is sqrt(r^2-x^2-y^2) (sqrt(r^2-x^2) in 2D); the printed
  *       closed forms then hold with principal-value arctangents.
  *   R2  Table 1 Step 3 as printed swaps the two branches; Sec. 2.4 states cells inside

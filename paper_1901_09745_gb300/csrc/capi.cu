@@ -568,7 +568,8 @@ extern "C" lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_
 }
 
 // Checkpoint layout: header (8 x int64), then the raw current population buffer, then
-// X, U, Omega (n x 3 doubles each) and the radii.
+// X, U, Omega (n x 3 doubles each) and the radii, then, when a DEM context is attached and
+// has built its neighbour lists, the DEM section (lists and contact history, dem.cu).
 struct StateHeader {
     long long magic, q, nx, ny, nz, storage, np, steps;
 };
@@ -578,7 +579,8 @@ extern "C" lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t
     if (!ctx || !used) return LBM_ERR_ARG;
     size_t pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
     size_t part = (size_t)ctx->np * 10 * sizeof(double);
-    size_t need = sizeof(StateHeader) + pop + part;
+    size_t dem = ctx->dem ? dem_state_bytes(ctx->dem) : 0;
+    size_t need = sizeof(StateHeader) + pop + part + dem;
     *used = need;
     if (!buf) return LBM_OK;
     if (cap < need) { ctx_error(ctx, "state buffer too small: need %zu bytes, have %zu", need, cap); return LBM_ERR_ARG; }
@@ -593,6 +595,11 @@ extern "C" lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t
         CK(cudaMemcpyAsync(p, ctx->dU, v, cudaMemcpyDeviceToHost, ctx->stream), "save U"); p += v;
         CK(cudaMemcpyAsync(p, ctx->dOm, v, cudaMemcpyDeviceToHost, ctx->stream), "save Omega"); p += v;
         CK(cudaMemcpyAsync(p, ctx->dR, (size_t)ctx->np * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "save radius");
+        p += (size_t)ctx->np * sizeof(double);
+    }
+    if (dem) {
+        lbm_status st = dem_state_save(ctx->dem, p);
+        if (st != LBM_OK) return st;
     }
     CK(cudaStreamSynchronize(ctx->stream), "sync");
     return LBM_OK;
@@ -618,6 +625,13 @@ extern "C" lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size)
     lbm_status st = lbm_set_particles(ctx, (int)h.np, (const double *)p, (const double *)(p + v),
                                       (const double *)(p + 2 * v), (const double *)(p + 3 * v), 0);
     if (st != LBM_OK) return st;
+    const size_t used = sizeof(h) + pop + (size_t)h.np * 10 * sizeof(double);
+    if (ctx->dem) {
+        // the DEM section when the checkpoint has one; else the DEM starts without history
+        if (size > used) st = dem_state_load(ctx->dem, (const char *)buf + used, size - used);
+        else dem_state_clear(ctx->dem);
+        if (st != LBM_OK) return st;
+    }
     ctx->steps = h.steps;
     return LBM_OK;
 }

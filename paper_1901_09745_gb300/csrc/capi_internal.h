@@ -70,3 +70,9 @@ void ctx_update_wrap(lbm_ctx *ctx);
 lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n);
 lbm_status ctx_reserve_particles(lbm_ctx *ctx, int n);
 void dem_release(dem_ctx *dem);
+// Checkpoint section of an attached DEM context (its neighbour lists and per-contact
+// history): bytes needed (0 when it holds no lists), write into host memory, restore.
+size_t dem_state_bytes(const dem_ctx *dem);
+lbm_status dem_state_save(dem_ctx *dem, char *dst);
+lbm_status dem_state_load(dem_ctx *dem, const char *src, size_t size);
+void dem_state_clear(dem_ctx *dem);

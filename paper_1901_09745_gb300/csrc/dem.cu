@@ -770,6 +770,9 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     if (fl->np != d->n) d->lists_valid = 0;
     lbm_status st = dem_reserve(d);
     if (st != LBM_OK) return st;
+    // no list to carry contact history over from (first call, a new particle count, or a
+    // checkpoint without a DEM section): every pair starts without history
+    if (!d->lists_valid) DCK(cudaMemsetAsync(d->nbr_n[d->cur], 0, (size_t)d->n * sizeof(int), fl->stream), "memset");
     st = dem_setup_bins(d);
     if (st != LBM_OK) return st;
     // largest delta_C of any pair (R <= r_max / 2) plus a margin far above the FP32 error of
@@ -832,6 +835,68 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     d->launches += kernels;
     fl->launches += kernels;
     fl->bins_valid = 0;   // particles moved: the fluid re-bins before its next step
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint section
+// Layout: {magic, n, kNB, kH} as int64, then the current list: counts (n int32), slots
+// (n x kNB int32), history (n x kNB x kH float). The next dem_step rebuilds the list from
+// the positions and carries the history over from this one, so a run resumed from it
+// continues exactly as the saved run did.
+static const long long kDemMagic = 0x50534344454d3031LL;   // "PSCDEM01"
+
+size_t dem_state_bytes(const dem_ctx *d) {
+    if (!d || !d->lists_valid || d->n <= 0) return 0;
+    const size_t n = (size_t)d->n;
+    return 4 * sizeof(long long) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float);
+}
+
+lbm_status dem_state_save(dem_ctx *d, char *dst) {
+    if (dem_state_bytes(d) == 0) return LBM_OK;
+    const size_t n = (size_t)d->n;
+    const long long h[4] = {kDemMagic, d->n, kNB, kH};
+    memcpy(dst, h, sizeof(h));
+    dst += sizeof(h);
+    cudaStream_t s = d->fl->stream;
+    DCK(cudaMemcpyAsync(dst, d->nbr_n[d->cur], n * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM counts");
+    dst += n * sizeof(int);
+    DCK(cudaMemcpyAsync(dst, d->nbr[d->cur], n * kNB * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM lists");
+    dst += n * kNB * sizeof(int);
+    DCK(cudaMemcpyAsync(dst, d->hist[d->cur], n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, s),
+        "save DEM history");
+    return LBM_OK;
+}
+
+void dem_state_clear(dem_ctx *d) {
+    if (d) d->lists_valid = 0;
+}
+
+lbm_status dem_state_load(dem_ctx *d, const char *src, size_t size) {
+    long long h[4];
+    if (size < sizeof(h)) { ctx_error(d->fl, "DEM checkpoint section truncated"); return LBM_ERR_ARG; }
+    memcpy(h, src, sizeof(h));
+    if (h[0] != kDemMagic || h[1] != d->fl->np || h[2] != kNB || h[3] != kH) {
+        ctx_error(d->fl, "DEM checkpoint section does not match this context");
+        return LBM_ERR_ARG;
+    }
+    const size_t n = (size_t)h[1];
+    if (size < sizeof(h) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float)) {
+        ctx_error(d->fl, "DEM checkpoint section truncated");
+        return LBM_ERR_ARG;
+    }
+    lbm_status st = dem_reserve(d);
+    if (st != LBM_OK) return st;
+    src += sizeof(h);
+    cudaStream_t s = d->fl->stream;
+    DCK(cudaMemcpyAsync(d->nbr_n[d->cur], src, n * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM counts");
+    src += n * sizeof(int);
+    DCK(cudaMemcpyAsync(d->nbr[d->cur], src, n * kNB * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM lists");
+    src += n * kNB * sizeof(int);
+    DCK(cudaMemcpyAsync(d->hist[d->cur], src, n * kNB * kH * sizeof(float), cudaMemcpyHostToDevice, s),
+        "load DEM history");
+    DCK(cudaStreamSynchronize(s), "sync");
+    d->n = (int)n;
+    d->lists_valid = 1;
     return LBM_OK;
 }
 

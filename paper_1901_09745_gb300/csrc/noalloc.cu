@@ -13,6 +13,7 @@
 // each call clears the parts that must start at zero. Calls that overlap on the GPU (two
 // streams, or two host threads) race on it and give wrong results: serialise them.
 #include <math.h>
+#include <stdint.h>
 #include <mutex>
 #include <stdio.h>
 #include <string.h>
@@ -64,6 +65,14 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     if (n < 0 || n > (1 << 24)) return fail(LBM_ERR_ARG, "particle count must be in [0, 2^24]");
     if (n > 0 && (!X || !U || !Omega || !radius || !F || !T))
         return fail(LBM_ERR_ARG, "particle arrays and F, T must not be NULL when n > 0");
+    // the pull reads neighbours' values that an in-place step would already have overwritten
+    if (f_in == f_out) return fail(LBM_ERR_ARG, "f_out must not alias f_in (the step reads f_in while writing f_out)");
+    const size_t elem = (p->storage == LBM_F64) ? 8 : (p->storage == LBM_F32) ? 4 : 2;
+    if ((uintptr_t)f_in % elem || (uintptr_t)f_out % elem)
+        return fail(LBM_ERR_ARG, "f_in and f_out must be aligned to the element size of the storage");
+    if (n > 0 && ((uintptr_t)X % 8 || (uintptr_t)U % 8 || (uintptr_t)Omega % 8 || (uintptr_t)radius % 8 ||
+                  (uintptr_t)F % 8 || (uintptr_t)T % 8))
+        return fail(LBM_ERR_ARG, "particle arrays and F, T must be 8-byte aligned");
 
     const bool is2d = (p->lattice == LBM_D2Q9);
     Geom g;

@@ -65,10 +65,15 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
         // distance from the particle to the tile's box of cell centres; a margin far above
         // the FP32 rounding of these distances keeps the test conservative)
         const float reach = (float)(r + h) + 0.01f;
-        const float xp[3] = {(float)pd.X[3 * p], (float)pd.X[3 * p + 1], dim == 3 ? (float)pd.X[3 * p + 2] : 0.0f};
+        // the centre wrapped into [0, n] on periodic axes: the culling below compares it with
+        // its images at +-n only, and callers may pass positions any number of periods out
+        double xw[3] = {pd.X[3 * p], pd.X[3 * p + 1], dim == 3 ? pd.X[3 * p + 2] : 0.0};
+        for (int ax = 0; ax < dim; ++ax)
+            if (g.periodic[ax]) xw[ax] -= (double)g.n[ax] * floor(xw[ax] * g.inv_n[ax]);
+        const float xp[3] = {(float)xw[0], (float)xw[1], (float)xw[2]};
         for (int ax = 0; ax < 3; ++ax) {
             if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; len[ax] = 1; continue; }
-            const double X = pd.X[3 * p + ax];
+            const double X = xw[ax];
             const int lo = (int)ceil(X - r - h), hi = (int)floor(X + r + h);
             nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
             len[ax] = 0;

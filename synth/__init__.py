@@ -18,7 +18,9 @@ centres at integer coordinates):
   c3  D3Q19 256^3 periodic, tau 0.6, body force (1e-6, 0, 0), static spheres r = 6
       (2000 as stated, or 5563 for solid fraction 0.3).
   c4  D3Q19 128^3 periodic, tau 0.7, 200 static spheres r = 5, 500 steps.
-  c5  D3Q19 512^3 channel (walls in z), tau 0.55, spheres r ~ U(3, 8).
+  c5  D3Q19 512^3 channel (walls in z), tau 0.55, 50000 spheres r ~ U(3, 8) by random
+      sequential addition (solid fraction 0.31); c5dense the same channel at solid
+      fraction 0.45 (71,830 spheres) by growth and relaxation, with many near-contacts.
 
 ``scale`` shrinks a workload's box (same solid fraction and radius distribution) for
 sub-box parity runs.
@@ -124,6 +126,95 @@ def rsa_pack(rng, box, radii, periodic, lo=None, hi=None, gap=0.0, wall_gap=0.5,
     return X
 
 
+def _pairs_within(X, box, periodic, cut):
+    """All pairs (i < j) closer than ``cut`` (minimum image on periodic axes), by a k-d tree."""
+    from scipy.spatial import cKDTree
+    box = np.asarray(box, dtype=np.float64)
+    dim = X.shape[1]
+    # the tree wraps every axis it is given a box size for; wall axes get a span far larger
+    # than the domain, so nothing wraps there
+    span = np.where(np.asarray(periodic[:dim], dtype=bool), box[:dim], 1e9)
+    Y = X.copy()
+    for a in range(dim):
+        if periodic[a]:
+            Y[:, a] %= box[a]
+        else:
+            Y[:, a] += 1e8
+    return cKDTree(Y, boxsize=span).query_pairs(cut, output_type="ndarray")
+
+
+def grow_relax_pack(rng, box, radii, periodic, wall_gap=0.5, s0=0.75, stages=12, sweeps=25, gap=0.0):
+    """Dense packing by growth and relaxation: centres start uniform at random; the radii
+    grow from s0 to their full size in ``stages`` steps, and after each growth overlapping
+    pairs are pushed apart along their line of centres (each by half the overlap, repeated
+    up to ``sweeps`` times; at full size until none is left) and wall axes are clamped.
+    Reaches solid fractions random sequential addition cannot, with many near-contacts.
+    Pairs come from a list of those within r_i + r_j + 2, rebuilt when a particle has moved
+    one unit."""
+    dim = len(box)
+    radii = np.asarray(radii, dtype=np.float64)
+    n = radii.size
+    box = np.asarray(box, dtype=np.float64)
+    per = np.asarray(periodic[:dim], dtype=bool)
+    lo = np.where(per, 0.0, -0.5 + wall_gap + radii[:, None])
+    hi = np.where(per, box, box - 0.5 - wall_gap - radii[:, None])
+    X = lo + rng.random((n, dim)) * (hi - lo)
+    rmax = float(radii.max())
+    margin = 2.0
+    pairs, Xref, rsum = None, None, None
+
+    def sep(i, j):
+        d = X[j] - X[i]
+        for a in range(dim):
+            if per[a]:
+                d[:, a] -= box[a] * np.rint(d[:, a] / box[a])
+        return d
+
+    near, age = None, 0
+    for s in np.linspace(s0, 1.0, stages):
+        limit = sweeps if s < 1.0 else 400 * sweeps
+        for _ in range(limit):
+            if pairs is None or np.max(np.abs(_min_image(X - Xref, box, periodic))) > 0.5 * margin:
+                pairs = _pairs_within(X, box, periodic, 2 * rmax + margin)
+                d = sep(pairs[:, 0], pairs[:, 1])
+                keep = (d * d).sum(axis=1) < (radii[pairs[:, 0]] + radii[pairs[:, 1]] + margin) ** 2
+                pairs = pairs[keep]
+                rsum = radii[pairs[:, 0]] + radii[pairs[:, 1]]
+                Xref = X.copy()
+                near = None
+            if near is None or age >= 8:
+                # the pairs within half a unit of touching (no particle moves that far in 8
+                # sweeps of this relaxation but the ones pushed apart)
+                d = sep(pairs[:, 0], pairs[:, 1])
+                near = np.nonzero((d * d).sum(axis=1) < (s * rsum + gap + 0.5) ** 2)[0]
+                age = 0
+            age += 1
+            i, j = pairs[near, 0], pairs[near, 1]
+            d = sep(i, j)
+            dist = np.sqrt((d * d).sum(axis=1))
+            ov = s * rsum[near] + gap - dist
+            m = ov > 1e-9 * rsum[near]
+            if not np.any(m):
+                if age == 1:
+                    break
+                age = 8       # confirm on a fresh near list before leaving the stage
+                continue
+            im, jm = i[m], j[m]
+            push = (0.5 * (ov[m] + 1e-6) / np.maximum(dist[m], 1e-12))[:, None] * d[m]
+            for a in range(dim):
+                X[:, a] += np.bincount(jm, weights=push[:, a], minlength=n) - np.bincount(im, weights=push[:, a], minlength=n)
+                if per[a]:
+                    X[:, a] %= box[a]
+                else:
+                    np.clip(X[:, a], lo[:, a], hi[:, a], out=X[:, a])
+    pairs = _pairs_within(X, box, periodic, 2 * rmax)
+    d = sep(pairs[:, 0], pairs[:, 1])
+    ov = radii[pairs[:, 0]] + radii[pairs[:, 1]] + gap - np.sqrt((d * d).sum(axis=1))
+    if ov.size and np.max(ov) > 1e-6:
+        raise RuntimeError("packing failed: overlaps remain (max %.3g)" % ov.max())
+    return X
+
+
 def _pad3(a):
     a = np.asarray(a, dtype=np.float64)
     if a.shape[-1] == 3:
@@ -200,6 +291,19 @@ def workload(name, scale=1.0, n_particles=None, seed_offset=0):
         return dict(name=name, lattice=19, n=(L, L, L), bc=(0, 0, 0), tau=0.7,
                     body_force=(1e-6, 0.0, 0.0), X=X, U=np.zeros_like(X), Om=np.zeros_like(X),
                     r=r, steps=500, dem=None, checkpoint=50,
+                    solid_fraction=float(4.0 / 3.0 * np.pi * (r ** 3).sum() / L ** 3))
+    if name == "c5dense":
+        # the 512^3 channel at solid fraction 0.45: 71,830 spheres r ~ U(3, 8) (mean volume
+        # 4/3 pi E[r^3] = 840.9) by growth and relaxation, which leaves many near-contacts
+        rng = rng_for(5 + seed_offset)
+        L = max(16, int(round(512 * scale)))
+        N = n_particles if n_particles is not None else int(round(71830 * (L / 512.0) ** 3))
+        r = rng.uniform(3.0, 8.0, size=N)
+        X = grow_relax_pack(rng, (L, L, L), r, (True, True, False))
+        U = rng.normal(0.0, 1e-3, size=(N, 3))
+        return dict(name=name, lattice=19, n=(L, L, L), bc=(0, 0, 1), tau=0.55,
+                    body_force=(1e-6, 0.0, 0.0), X=X, U=U, Om=np.zeros_like(X), r=r,
+                    steps=2000, dem=dict(substeps=10),
                     solid_fraction=float(4.0 / 3.0 * np.pi * (r ** 3).sum() / L ** 3))
     if name == "c5":
         rng = rng_for(4 + seed_offset)

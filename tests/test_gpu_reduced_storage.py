@@ -1,7 +1,8 @@
 """FP16 / BF16 deviation storage (FP32 compute) against the FP64 oracle.
 
 The paper has no reduced-precision result to pin these to; the error against the FP64
-oracle is measured and reported here (and in the design notes), with loose bounds that a
+oracle is measured and reported here (written to the file named by PSC_ERROR_REPORT when
+set), with loose bounds that a
 broken storage path (wrong scale, wrong rounding, lost increments) would exceed by orders
 of magnitude. Each test prints its errors next to the FP32 errors of the same run.
 """

@@ -117,6 +117,47 @@ def test_hertz_collision_without_damping_is_elastic(dim):
     assert _kinetic(p2, st2) < 0.95 * k0
 
 
+@pytest.mark.parametrize("v", [1e-2, 3e-2])
+def test_hertz_normal_damping_energy_loss_small_alpha(v):
+    """Normal damping (reading of the constants the paper takes from the literature):
+    eta_N = alpha_n sqrt(m* k_N) with k_N = 2 E* a the Hertz contact stiffness dF/ddelta.
+    To first order in alpha_n a head-on Hertz collision loses the work of the damping force
+    along the undamped trajectory,
+
+      W = 2 int_0^dmax eta_N(d) w(d) dd,  (1/2) m* w^2 + (8/15) E* sqrt(R) d^(5/2) = (1/2) m* w0^2,
+
+    a quadrature independent of the oracle's integrator (to second order the loss is
+    W (1 - W / 2E0)); a wrong factor in k_N or m* (m instead of m*, E* a instead of
+    2 E* a) changes W by sqrt(2). With this form of eta_N the loss is the same fraction of
+    the impact energy at every impact speed."""
+    E, nu, r, alpha = 2.0, 0.3, 3.0, 0.01
+    p = O.make_dem_params(E=E, poisson=nu, adhesive=0, alpha_n=alpha, dt=2e-3, dim=3, n=(64, 64, 64))
+    X, U, Om, rad = _two_spheres(v=v, r=r, gap=0.0)
+    st = O.DemState(X, U, Om, rad)
+    k0 = _kinetic(p, st)
+    touched = False
+    for _ in range(1000):
+        O.dem_step(p, st, substeps=100)
+        touched |= st.ncontact > 0
+        if touched and st.ncontact == 0:
+            break
+    assert touched and st.ncontact == 0
+    lost = k0 - _kinetic(p, st)
+    Es = E / (2 * (1 - nu * nu))
+    R = r / 2
+    m = p.density * 4 / 3 * math.pi * r ** 3
+    ms = m / 2
+    dmax = (15 * ms * v * v / (16 * Es * math.sqrt(R))) ** 0.4
+    w = lambda d: math.sqrt(max(v * v - 16 / 15 * Es * math.sqrt(R) * d ** 2.5 / ms, 0.0))
+    eta = lambda d: alpha * math.sqrt(ms * 2 * Es * math.sqrt(R * d))
+    W = 2 * integrate.quad(lambda d: eta(d) * w(d), 0.0, dmax, epsabs=0, epsrel=1e-10, limit=200)[0]
+    # the second-order term: the damped trajectory is slower by about half the lost
+    # fraction on average, so the damping does about that much less work
+    E0 = 0.5 * ms * v * v
+    assert k0 == pytest.approx(E0, rel=1e-12)
+    assert lost == pytest.approx(W * (1 - W / (2 * E0)), rel=3e-3)
+
+
 def test_hertz_force_closed_form():
     E, nu = 2.0, 0.3
     p = O.make_dem_params(E=E, poisson=nu, adhesive=0, alpha_n=0.0, dim=3)

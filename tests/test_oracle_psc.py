@@ -293,6 +293,75 @@ def test_momentum_budget_exact(lattice, psc):
         assert not np.allclose(M1 - M0, budget, rtol=1e-6, atol=1e-12)
 
 
+def _static_shared_setup(lattice, psc, seed=17):
+    """Static particles (u_s = 0) of which two overlap, so that cells hold two particles,
+    on a random pre-collision state with a body force."""
+    p, f, X, U, Om, r = _moving_setup(lattice, psc, seed)
+    return p, f, X, np.zeros_like(U), np.zeros_like(Om), r
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+@pytest.mark.parametrize("psc", [0, 1])
+def test_per_particle_force_from_the_momentum_exchange_identity(lattice, psc):
+    """Eq. 11 (original) and Eq. 14 (modified) particle by particle. For a static particle
+    the per-cell momentum exchange sum_i Omega^s_i e_i of Eq. 10 equals F - rho u (rho u the
+    force-shifted momentum of Eq. 5 before the step), the same for every particle in the
+    cell, so
+
+      original: F_s = -sum_{n touched by s} B_n (F - rho u),  B_n = sum_s B(eps_{n,s}) (Eq. 8)
+      modified: F_s = -sum_{n touched by s} B_{n,s} (F - rho u)  (Eq. 13, reading R6),
+
+    and the fluid gains F sum_n (1 - B_n) + sum_n B_n (F - rho u) in both schemes. The
+    weights come from the separately pinned solid fractions (Table 1) and B (Eq. 9, 13);
+    the step computes the exchange as an explicit sum over the velocities. Where particles
+    share cells the two schemes' weights differ, so weighting a particle's force by its own
+    B(eps_s) instead of the cell's B_n (or the reverse) fails here."""
+    p, f, X, U, Om, r = _static_shared_setup(lattice, psc)
+    tau = p.tau
+    Fb = np.array([p.body_force[0], p.body_force[1], p.body_force[2]])
+    e = O.lattice_tables(lattice)[0].astype(np.float64)
+    rho, u = O.macro(p, f)
+    m = Fb - rho[..., None] * u                         # per-cell exchange, (nz, ny, nx, 3)
+    m = m.reshape(-1, 3)
+    eps_sum, nrec, pid, eps = O.solid_fraction(p, X, r)
+    ncell = eps_sum.size
+    Bn = np.zeros(ncell)
+    Bs = np.zeros_like(eps)                              # per (cell, record) weight
+    shared = 0
+    for c in np.nonzero(nrec)[0]:
+        k = nrec[c]
+        Bn_c, Bs_c = O.cell_weights(eps[c, :k], tau, mode=psc)
+        Bn[c] = Bn_c
+        Bs[c, :k] = Bs_c if psc == 0 else Bn_c           # Eq. 11 weights every particle by B_n
+        shared += (np.count_nonzero(eps[c, :k] > 0) > 1)
+    assert shared > 0
+    expect = np.zeros((len(r), 3))
+    for c in np.nonzero(nrec)[0]:
+        for k in range(nrec[c]):
+            if eps[c, k] > 0:
+                expect[pid[c, k]] -= Bs[c, k] * m[c]
+    M0 = np.einsum("izyx,ia->a", f, e)
+    Fp, Tp, Bn_step = O.step(p, f, X, U, Om, r, want_Bn=True)
+    M1 = np.einsum("izyx,ia->a", f, e)
+    assert np.allclose(Bn_step.reshape(-1), Bn, rtol=0, atol=1e-15)
+    scale = np.abs(expect).max()
+    assert np.max(np.abs(Fp - expect)) <= 1e-11 * scale
+    fluid = Fb * (1.0 - Bn).sum() + (Bn[:, None] * m).sum(0)
+    assert np.allclose(M1 - M0, fluid, rtol=1e-10, atol=1e-15)
+    # the other scheme's weighting is far off in the shared cells: the test can tell them apart
+    alt = np.zeros_like(expect)
+    for c in np.nonzero(nrec)[0]:
+        k = nrec[c]
+        if psc == 1:
+            w_alt = np.array([O.B(v, tau) for v in eps[c, :k]])
+        else:
+            w_alt = np.full(k, O.cell_weights(eps[c, :k], tau, mode=1)[0])
+        for q in range(k):
+            if eps[c, q] > 0:
+                alt[pid[c, q]] -= w_alt[q] * m[c]
+    assert np.max(np.abs(alt - expect)) > 1e-6 * scale
+
+
 @pytest.mark.parametrize("lattice", [9, 19])
 def test_comoving_particle_feels_no_force(lattice):
     """A particle translating with a uniform equilibrium flow (no body force) leaves the

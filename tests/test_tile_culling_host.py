@@ -2,8 +2,8 @@
 centre to the tile's box of cell centres (minimum image on periodic axes) is at most
 r + h + 0.01 (k_bin, in FP32). This checks on the host, by brute force over the cells,
 that the test never drops a tile holding a cell centre within r + h of the particle
-(where Table 1 can give a non-zero solid fraction), in 2D and 3D, across periodic faces
-and at walls."""
+(where Table 1 can give a non-zero solid fraction), in 2D and 3D, across periodic faces,
+for centres several periods outside the box, and at walls."""
 import numpy as np
 
 
@@ -17,10 +17,16 @@ def _axis_gap(x, a, b, n, periodic):
     return d
 
 
+def _wrapped(x, n, periodic):
+    # k_bin wraps the centre into [0, n] on periodic axes (FP64) before the FP32 culling
+    return x - n * np.floor(x * (1.0 / n)) if periodic else x
+
+
 def _kept(X, reach, org, tshape, n, periodic, dim):
     d2 = np.float32(0)
     for ax in range(dim):
-        g = _axis_gap(X[ax], org[ax], min(org[ax] + tshape[ax], n[ax]) - 1, n[ax], periodic[ax])
+        x = _wrapped(X[ax], n[ax], periodic[ax])
+        g = _axis_gap(x, org[ax], min(org[ax] + tshape[ax], n[ax]) - 1, n[ax], periodic[ax])
         d2 += g * g
     return d2 <= np.float32(reach) * np.float32(reach)
 
@@ -49,7 +55,12 @@ def test_tile_culling_keeps_every_tile_a_shell_reaches():
                 n[2] = 1
             periodic = [int(v) for v in rng.integers(0, 2, 3)]
             r = rng.uniform(3.0, 9.0)
+            # centres up to three periods out on periodic axes (the C ABI accepts any
+            # position there), inside the box on wall axes
             X = rng.uniform(0, 1, 3) * np.array(n, dtype=float)
+            for a in range(3):
+                if periodic[a]:
+                    X[a] += n[a] * int(rng.integers(-3, 3))
             reach = np.float32(r + h) + np.float32(0.01)
             nt = [(n[a] + tshape[a] - 1) // tshape[a] for a in range(3)]
             for tz in range(nt[2] if dim == 3 else 1):
