@@ -201,9 +201,10 @@ TIMING_EVERY = 8
 
 def dem_defaults(w):
     """Contact-model parameters of the coupled workloads, in lattice units: E = 2, Poisson
-    ratio 0.3, surface energy 2e-4, particle/fluid density ratio 3, friction 0.3, critical
-    rolling angle 0.01, normal damping 0.3."""
-    return dict(E=2.0, poisson=0.3, gamma=2e-4, density=3.0, mu_f=0.3, theta_crit=0.01,
+    ratio 0.3, the workload's surface energy (2e-4 for the 2D channel, 2e-2 for the 512^3
+    channels), particle/fluid density ratio 3, friction 0.3, critical rolling angle 0.01,
+    normal damping 0.3."""
+    return dict(E=2.0, poisson=0.3, gamma=w["dem"].get("gamma", 2e-4), density=3.0, mu_f=0.3, theta_crit=0.01,
                 alpha_n=0.3, k_t_scale=1.0, eta_t_scale=1.0, dt_dem=1.0 / w["dem"]["substeps"],
                 gravity=(0.0, 0.0, 0.0), adhesive=1)
 

@@ -30,6 +30,12 @@ import math
 import numpy as np
 
 
+# surface energy of the 512^3 channel workloads: the pull-off force 3 pi gamma R of the
+# smallest pair (r = 3, R = 1.5) is 0.28, several times the largest mean hydrodynamic force
+# the spheres see in the first steps (about 0.06, from their random initial velocities)
+C5_GAMMA = 2e-2
+
+
 def rng_for(k):
     return np.random.default_rng(1000 * k + 1)
 
@@ -268,7 +274,7 @@ def workload(name, scale=1.0, n_particles=None, seed_offset=0):
         Om[:, 2] = rng.normal(0.0, 1e-3, size=N) / r
         return dict(name=name, lattice=9, n=(L, L, 1), bc=(0, 1, 0), tau=0.7,
                     body_force=(0.0, 0.0, 0.0), X=X, U=U, Om=Om, r=r, steps=None,
-                    dem=dict(substeps=10), band=(y0, y0 + band_h),
+                    dem=dict(substeps=10, gamma=2e-4), band=(y0, y0 + band_h),
                     solid_fraction=float(np.pi * (r ** 2).sum() / (L * L)),
                     band_solid_fraction=float(np.pi * (r ** 2).sum() / (L * band_h)))
     if name in ("c3", "c3dense"):
@@ -303,7 +309,7 @@ def workload(name, scale=1.0, n_particles=None, seed_offset=0):
         U = rng.normal(0.0, 1e-3, size=(N, 3))
         return dict(name=name, lattice=19, n=(L, L, L), bc=(0, 0, 1), tau=0.55,
                     body_force=(1e-6, 0.0, 0.0), X=X, U=U, Om=np.zeros_like(X), r=r,
-                    steps=2000, dem=dict(substeps=10),
+                    steps=2000, dem=dict(substeps=10, gamma=C5_GAMMA),
                     solid_fraction=float(4.0 / 3.0 * np.pi * (r ** 3).sum() / L ** 3))
     if name == "c5":
         rng = rng_for(4 + seed_offset)
@@ -314,7 +320,7 @@ def workload(name, scale=1.0, n_particles=None, seed_offset=0):
         U = rng.normal(0.0, 1e-3, size=(N, 3))
         return dict(name=name, lattice=19, n=(L, L, L), bc=(0, 0, 1), tau=0.55,
                     body_force=(1e-6, 0.0, 0.0), X=X, U=U, Om=np.zeros_like(X), r=r,
-                    steps=2000, dem=dict(substeps=10),
+                    steps=2000, dem=dict(substeps=10, gamma=C5_GAMMA),
                     solid_fraction=float(4.0 / 3.0 * np.pi * (r ** 3).sum() / L ** 3))
     raise KeyError(name)
 

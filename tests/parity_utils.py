@@ -35,10 +35,10 @@ def run_oracle(case, f0, steps):
     return dict(f=f, F=F, T=T, rho=rho, u=u)
 
 
-def run_gpu(P, case, f0, steps, storage="f32", tile_cap=0):
+def run_gpu(P, case, f0, steps, storage="f32", tile_cap=0, no_tma=False):
     ctx = P.lbm_create(case["lattice"], *case["n"], bc=case["bc"], tau=case["tau"],
                        body_force=case["body_force"], storage=storage, psc=case.get("psc", 0),
-                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap)
+                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap, no_tma=no_tma)
     if f0 is not None:
         P.lbm_set_populations(ctx, f0)
     if len(case["r"]):
@@ -78,6 +78,7 @@ def ragged_case2d(psc=0, bc=(0, 1, 0), n=(77, 45, 1)):
     # exceeds one), so its cases move particle 1 to a 0.6 lu gap.
     if psc == 1:
         X[1, 0] = 70.0
+    X[X[:, 0] > 69.0, 0] += n[0] - 77      # keep the particles at the high-x face with the box
     U = np.zeros((7, 3)); U[:, :2] = rng.normal(0, 2e-3, (7, 2))
     Om = np.zeros((7, 3)); Om[:, 2] = rng.normal(0, 5e-4, 7)
     return dict(lattice=9, n=n, bc=bc, tau=0.7, body_force=(2e-5, -5e-6, 0.0), X=X, U=U, Om=Om,
@@ -93,6 +94,7 @@ def ragged_case3d(psc=0, bc=(0, 0, 1), n=(45, 29, 23)):
     r = np.array([4.5, 3.8, 4.0, 3.9, 5.0, 4.2])   # 2-3 overlap; 0, 1, 4, 5 cross faces
     if psc == 1:
         X[3, 0] = 27.9    # 2-3 at a 0.1 lu gap for the original scheme
+    X[X[:, 0] > 40.0, 0] += n[0] - 45      # keep the particles at the high-x face with the box
     U = rng.normal(0, 2e-3, (6, 3))
     Om = rng.normal(0, 5e-4, (6, 3))
     return dict(lattice=19, n=n, bc=bc, tau=0.62, body_force=(1e-5, 2e-6, -3e-6), X=X, U=U, Om=Om,
