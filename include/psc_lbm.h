@@ -75,9 +75,6 @@ typedef struct {
                                <= 0 selects 4096 for FP16 and 1 for BF16 */
     int tile_cap;           /* candidate particles kept per lattice tile (<= 0: 64) */
     void *stream;           /* cudaStream_t to queue work on; NULL: the library makes one */
-    int no_tma;             /* 0: FP32 / 16-bit storage with nx x element size a multiple of 16
-                               stage each tile's populations in shared memory by TMA copies;
-                               1: load them directly (the same step, slower; for comparisons) */
 } lbm_params;
 
 /* Create a fluid at rest, f_i = f_i^eq(rho = 1, u = 0) = w_i (Eq. 3), with no particles.

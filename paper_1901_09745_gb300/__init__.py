@@ -54,7 +54,6 @@ class LbmParams(C.Structure):
         ("dev_scale", C.c_double),
         ("tile_cap", C.c_int),
         ("stream", C.c_void_p),
-        ("no_tma", C.c_int),
     ]
 
 
@@ -184,7 +183,7 @@ class Lbm:
 # ------------------------------------------------------------------------ the C calls
 def lbm_create(lattice, nx, ny, nz=1, bc=(0, 0, 0), tau=0.8, body_force=(0.0, 0.0, 0.0),
                storage="f32", psc=LBM_PSC_MODIFIED, shell_h=1.0, dev_scale=0.0, tile_cap=0,
-               stream=None, no_tma=False):
+               stream=None):
     p = LbmParams()
     p.lattice = int(lattice)
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
@@ -197,7 +196,6 @@ def lbm_create(lattice, nx, ny, nz=1, bc=(0, 0, 0), tau=0.8, body_force=(0.0, 0.
     p.shell_h = float(shell_h)
     p.dev_scale = float(dev_scale)
     p.tile_cap = int(tile_cap)
-    p.no_tma = int(bool(no_tma))
     if stream is None:
         try:
             import torch

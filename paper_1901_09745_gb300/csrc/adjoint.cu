@@ -397,7 +397,7 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
             for (int t = t0 + 1; t < t1; ++t) {
                 ACK(launch_collide_stream(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - 1 - t0),
                                           seg + popa * (size_t)(t - t0), ctx->g, ctx->ph, tl, scratch_parts,
-                                          ctx->flags, ctx->stream, &ctx->ov, nullptr),
+                                          ctx->flags, ctx->stream, &ctx->ov),
                     "segment recompute");
             }
             for (int t = t1 - 1; t >= t0; --t) {

@@ -16,13 +16,13 @@
 
 namespace psc {
 cudaError_t launch_collide_stream_f64(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *, const CUtensorMap *);
+                                     const Overlap *);
 cudaError_t launch_collide_stream_f32(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *, const CUtensorMap *);
+                                     const Overlap *);
 cudaError_t launch_collide_stream_f16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *, const CUtensorMap *);
+                                     const Overlap *);
 cudaError_t launch_collide_stream_bf16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *, const CUtensorMap *);
+                                     const Overlap *);
 cudaError_t launch_gather_f64(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f32(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f16(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
@@ -34,12 +34,12 @@ cudaError_t launch_set_bf16(int, const double *, void *, const Geom &, const Phy
 
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout, const Geom &g,
                                   const Phys &ph, const Tiles &tl, const Parts &pd, int *flags,
-                                  cudaStream_t s, const Overlap *ov, const CUtensorMap *tm) {
+                                  cudaStream_t s, const Overlap *ov) {
     switch (storage) {
-    case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s, ov, nullptr);
-    case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s, ov, tm);
-    case ST_F16: return launch_collide_stream_f16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov, tm);
-    default: return launch_collide_stream_bf16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov, tm);
+    case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    case ST_F16: return launch_collide_stream_f16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
+    default: return launch_collide_stream_bf16(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
     }
 }
 cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out, double *rho, double *u,
@@ -215,10 +215,6 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f[1], 0, bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flags, 0, 4 * sizeof(int), ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    // tensor maps of both population buffers for the TMA staging of the pull (none when the
-    // geometry or storage does not allow it: the kernels then load without TMA)
-    for (int b = 0; e == cudaSuccess && b < 2; ++b)
-        ctx->tmap_ok[b] = encode_pop_tmap(&ctx->tmap[b], p->storage, p->lattice, ctx->f[b], g) == cudaSuccess;
     if (e != cudaSuccess) {
         ctx_error(NULL, "lbm_create: %s", cudaGetErrorString(e));
         lbm_status s2 = (e == cudaErrorMemoryAllocation) ? LBM_ERR_OOM : LBM_ERR_CUDA;
@@ -407,8 +403,7 @@ static lbm_status ctx_enqueue_step(lbm_ctx *ctx, bool bin, cudaEvent_t *ev) {
     }
     if (ev) CK(cudaEventRecord(ev[0], ctx->stream), "cudaEventRecord");
     CK(launch_collide_stream(ctx->p.storage, ctx->q, ctx->f[ctx->cur], ctx->f[ctx->cur ^ 1], ctx->g, ctx->ph,
-                             ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream, &ctx->ov,
-                             (ctx->tmap_ok[ctx->cur] && !ctx->p.no_tma) ? &ctx->tmap[ctx->cur] : nullptr),
+                             ctx_tiles(ctx), ctx_parts(ctx), ctx->flags, ctx->stream, &ctx->ov),
        "collide-stream kernel");
     if (ev) CK(cudaEventRecord(ev[1], ctx->stream), "cudaEventRecord");
     return LBM_OK;
@@ -499,7 +494,6 @@ lbm_status ctx_check_flags(lbm_ctx *ctx) {
     CK(cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "read flags");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
     if (h[0] & 1) { ctx_error(ctx, "a cell reached a non-positive or NaN density (unstable run)"); return LBM_ERR_UNSTABLE; }
-    if (h[0] & 4) { ctx_error(ctx, "a TMA copy of the populations did not complete within its wait limit"); return LBM_ERR_TIMEOUT; }
     if (h[1]) { ctx_error(ctx, "JKR contact-radius solve did not converge for %d contacts", h[1]); return DEM_ERR_NO_CONVERGENCE; }
     if (h[2]) { ctx_error(ctx, "%d DEM bin or neighbour-list overflows (more neighbours than slots)", h[2]); return LBM_ERR_OVERFLOW; }
     if (h[3]) { ctx_error(ctx, "%d particle moves exceeded half the DEM neighbour-list skin in one call; raise dem_params.skin", h[3]); return LBM_ERR_OVERFLOW; }

@@ -17,8 +17,6 @@ struct lbm_ctx {
     int cur;
     cudaStream_t stream;
     psc::Overlap ov;           // second stream + fork/join events of the 2D step
-    CUtensorMap tmap[2];       // tensor maps of f[0], f[1] for the TMA staging of the pull
-    int tmap_ok[2];            // 1 when the map could be encoded (FP32/16-bit, aligned rows)
     int own_stream;
     int device;
     int *flags;                // device flag word: [0] bit 0 unstable density, [1] DEM failures

@@ -160,13 +160,9 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     if (e == cudaSuccess && n > 0) e = launch_f_of_r(is2d ? 2 : 3, radius, (double *)(base + o_fr), n, s);
     if (e == cudaSuccess && n > 0) e = launch_bin(is2d ? 2 : 3, g, ph, tl, pd, s);
     if (e == cudaSuccess && n > 0) e = launch_pack(p->lattice, rec_double, g, tl, pd, ntiles, s);
-    // the tensor map of f_in for the TMA staging of the pull (host-side encoding, nothing
-    // allocated); without one the kernels load directly
-    CUtensorMap tm;
-    const bool use_tma = !p->no_tma && encode_pop_tmap(&tm, p->storage, p->lattice, f_in, g) == cudaSuccess;
     if (e == cudaSuccess)
         e = launch_collide_stream(p->storage, p->lattice, f_in, f_out, g, ph, tl, pd, flags, s,
-                                  g_overlap[dev].join ? &g_overlap[dev] : nullptr, use_tma ? &tm : nullptr);
+                                  g_overlap[dev].join ? &g_overlap[dev] : nullptr);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
     return LBM_OK;
 }

@@ -2,7 +2,6 @@
 // launchers of the PSC lattice-Boltzmann library. Host-visible; no CUDA device code here.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -63,18 +62,10 @@ struct Overlap {
     cudaEvent_t fork, join;
 };
 
-// Fused solid-fraction + PSC collision + pull streaming + force reduction (one step). `tm`,
-// when not null, is the tensor map of fin (encode_pop_tmap): the kernels then stage each
-// tile's populations in shared memory by TMA (FP32 and 16-bit storage).
+// Fused solid-fraction + PSC collision + pull streaming + force reduction (one step).
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout,
                                   const Geom &g, const Phys &ph, const Tiles &tl,
-                                  const Parts &pd, int *flags, cudaStream_t s, const Overlap *ov,
-                                  const CUtensorMap *tm);
-// Tensor map of a population buffer for the TMA staging of the pull: dims (nx, ny, [nz,] Q),
-// boxes of one tile's rows per direction. cudaErrorNotSupported when the storage is FP64 or
-// the rows do not start on 16-byte boundaries (nx times the element size not a multiple of
-// 16, or a misaligned base); the caller then runs the kernels without TMA.
-cudaError_t encode_pop_tmap(CUtensorMap *map, int storage, int lattice, const void *base, const Geom &g);
+                                  const Parts &pd, int *flags, cudaStream_t s, const Overlap *ov);
 // Pre-collision populations (full f, FP64) and/or Eq. 5 moments of the current state.
 cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out,
                           double *rho, double *u, const Geom &g, const Phys &ph,

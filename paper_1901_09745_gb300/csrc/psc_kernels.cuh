@@ -32,7 +32,6 @@
 
 #include "lattice.cuh"
 #include "psc_internal.h"
-#include "tma.cuh"
 
 namespace psc {
 
@@ -871,78 +870,11 @@ inline cudaError_t block_registers(K kern, int threads, int &regs) {
 // share every SM for the whole step; without a second stream, one after the other. In 3D
 // (and FP64) the particle-tile kernel holds all the registers an SM has, and takes the
 // fluid tiles itself once its own are done. Then the overflow kernel.
-// The same step with each tile's populations staged in shared memory by TMA (tma.cuh):
-// the fluid-tile kernel over all tiles (no particles); in 2D the particle-tile kernel and
-// the fluid-tile kernel side by side on two streams when there is a second stream; in 3D
-// (or on one stream) the particle-tile kernel over both lists. Then the overflow kernel.
-template <class L, typename S, int PSC>
-cudaError_t launch_collide_stream_tma(const CUtensorMap &tm, const void *fin, void *fout, const Geom &g, const Phys &ph,
-                                      const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s,
-                                      const Overlap *ov) {
-    using T = typename Store<S>::T;
-    using B = TmaBox<L, S>;
-    constexpr int NC = (L::D == 2) ? 3 : 6;
-    constexpr int NSF = 2;                        // stages of the fluid-tile kernel
-    const PhysT<T> pt = make_phys<T>(ph);
-    const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
-    auto fkern = hasF ? k_fluid_tma<L, S, true, NSF> : k_fluid_tma<L, S, false, NSF>;
-    const size_t fsmem = (size_t)NSF * B::STAGE_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(fkern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
-    if (e != cudaSuccess) return e;
-    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    const dim3 pblock(32, kPWarps);
-    unsigned nb = 0;
-    if (pd.n == 0) {
-        e = persistent_blocks(fkern, fsmem, ntiles, nb, kPThreads);
-        if (e != cudaSuccess) return e;
-        fkern<<<nb, pblock, fsmem, s>>>(tm, (const S *)fin, (S *)fout, g, pt, tl, 0, flags);
-        return cudaGetLastError();
-    }
-    const bool side = (L::D == 2) && ov && ov->aux;
-    const size_t psmem = tma_pair_smem_bytes<L, S>();
-    if (side) {
-        // 2D: 4 particle-tile blocks (80 registers) and 3 fluid-tile blocks (64) per SM
-        auto kern = k_collide_stream_tma<L, S, PSC, false>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-        int dev = 0, nsm = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaEventRecord(ov->fork, s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->fork, 0);
-        if (e != cudaSuccess) return e;
-        kern<<<nsm * 4, pblock, psmem, s>>>(tm, (const S *)fin, (S *)fout, g, pt, tl, pd, flags);
-        fkern<<<nsm * 3, pblock, fsmem, ov->aux>>>(tm, (const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
-        e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaEventRecord(ov->join, ov->aux);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ov->join, 0);
-        if (e != cudaSuccess) return e;
-    } else {
-        auto kern = k_collide_stream_tma<L, S, PSC, true>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-        if (e == cudaSuccess) e = persistent_blocks(kern, psmem, ntiles, nb, kPThreads);
-        if (e != cudaSuccess) return e;
-        kern<<<nb, pblock, psmem, s>>>(tm, (const S *)fin, (S *)fout, g, pt, tl, pd, flags);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    auto okern = k_collide_overflow<L, S, PSC>;
-    const size_t osmem = cs_smem_bytes<T>(tl.cap, NC);
-    if (osmem > 48 * 1024) {
-        e = cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
-        if (e != cudaSuccess) return e;
-    }
-    okern<<<32, dim3(L::TX, L::TY, L::TZ), osmem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
-    return cudaGetLastError();
-}
-
 template <class L, typename S, int PSC>
 cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, const Phys &ph,
                                     const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s,
-                                    const Overlap *ov, const CUtensorMap *tm) {
+                                    const Overlap *ov) {
     using T = typename Store<S>::T;
-    if constexpr (sizeof(T) == 4) {
-        if (tm) return launch_collide_stream_tma<L, S, PSC>(*tm, fin, fout, g, ph, tl, pd, flags, s, ov);
-    }
     constexpr int NC = (L::D == 2) ? 3 : 6;
     constexpr bool kSteal = (L::D == 3) || sizeof(T) == 8;
     // blocks per SM side by side (2D): 4 x 128 threads x 80 registers + 3 x 128 x 64 = 64 K
@@ -1013,13 +945,13 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
 template <typename S>
 cudaError_t launch_collide_stream_storage(int lattice, const void *fin, void *fout, const Geom &g,
                                           const Phys &ph, const Tiles &tl, const Parts &pd,
-                                          int *flags, cudaStream_t s, const Overlap *ov, const CUtensorMap *tm) {
+                                          int *flags, cudaStream_t s, const Overlap *ov) {
     if (lattice == 9) {
-        return ph.psc == 0 ? launch_collide_stream_t<D2Q9, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov, tm)
-                           : launch_collide_stream_t<D2Q9, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov, tm);
+        return ph.psc == 0 ? launch_collide_stream_t<D2Q9, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov)
+                           : launch_collide_stream_t<D2Q9, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov);
     }
-    return ph.psc == 0 ? launch_collide_stream_t<D3Q19, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov, tm)
-                       : launch_collide_stream_t<D3Q19, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov, tm);
+    return ph.psc == 0 ? launch_collide_stream_t<D3Q19, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov)
+                       : launch_collide_stream_t<D3Q19, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov);
 }
 
 template <typename S>

@@ -152,55 +152,16 @@ __device__ __forceinline__ void store_pair(S *__restrict__ fout, const long long
     if (actB) Store<S>::str(fout, iB, b);
 }
 
-// Is the cell on a face of the lattice (its pull may wrap or bounce back)?
-template <class L>
-__device__ __forceinline__ bool on_face(const Geom &g, const int x, const int y, const int z) {
-    return x == 0 || x == g.n[0] - 1 || y == 0 || y == g.n[1] - 1 ||
-           (L::D == 3 && (z == 0 || z == g.n[2] - 1));
-}
+template <class L> constexpr int pair_nslot() { return 4; }
 
-// Pull of the lane's two cells from a TMA stage (psc_tma.cuh): tile column `lane`, tile rows
-// rA and rB (row index z * TY + y within the tile). Cells on a face of the lattice, and
-// cells beyond it in a ragged tile, take the global-memory pull (wrap, bounce-back).
-template <class L, typename S>
-__device__ __forceinline__ void pull_pair_stage(const S *__restrict__ stage, const S *__restrict__ fin, const Geom &g,
-                                                const PhysT<typename Store<S>::T> &ph, const int lane, const int rA,
-                                                const int rB, const int xA, const int xB, const int yA, const int yB,
-                                                const int zA, const int zB, const long long cellA,
-                                                const long long cellB, const bool actA, const bool actB,
-                                                typename Store<S>::T *da, typename Store<S>::T *db) {
-    using B = TmaBox<L, S>;
-    constexpr bool SC = Store<S>::kScaled;
-#pragma unroll
-    for (int i = 0; i < L::Q; ++i) {
-        const S *pl = stage + i * B::ELEMS + B::col(L::ex(i), lane);
-        da[i] = SC ? Store<S>::ldr(pl, rA * B::BX) : Store<S>::ld(pl, rA * B::BX, ph.sc);
-        db[i] = SC ? Store<S>::ldr(pl, rB * B::BX) : Store<S>::ld(pl, rB * B::BX, ph.sc);
-    }
-    if (!actA || on_face<L>(g, xA, yA, zA)) pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da);
-    if (!actB || on_face<L>(g, xB, yB, zB)) pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db);
-}
-
-// Candidate brackets kept per warp row (further candidates are evaluated again). With a
-// TMA stage beside them, the 3D kernel keeps three so that four blocks still fit an SM.
-template <class L, bool TMA = false> constexpr int pair_nslot() { return (TMA && L::D == 3) ? 3 : 4; }
-
-template <class L, typename T, bool TMA = false> __host__ __device__ constexpr size_t pair_smem_bytes() {
+template <class L, typename T> __host__ __device__ constexpr size_t pair_smem_bytes() {
     // records [2][kPairCap][RW] | partials [2][kPWarps][kPairCap][NC] | brackets
     // [kPWarps][NSLOT + 1][NC][32] pairs (the last slot is scratch for further candidates)
     return (size_t)2 * kPairCap * RW * sizeof(T) + (size_t)2 * kPWarps * kPairCap * ((L::D == 2) ? 3 : 6) * sizeof(T) +
-           (size_t)kPWarps * (pair_nslot<L, TMA>() + 1) * ((L::D == 2) ? 3 : 6) * 32 * 2 * sizeof(T);
+           (size_t)kPWarps * (pair_nslot<L>() + 1) * ((L::D == 2) ? 3 : 6) * 32 * 2 * sizeof(T);
 }
 
-// No work after the tile's barrier (the kernels without a TMA stage).
-struct NoHook {
-    __device__ __forceinline__ void operator()() const {}
-};
-
-// TMA = true: the populations come from the tile's TMA stage `stage` (psc_tma.cuh) and
-// `hook` runs right after the tile's barrier, when every warp has read the stage (it issues
-// the next tile's copies into it).
-template <class L, typename S, int PSC, bool TMA = false, class Hook = NoHook>
+template <class L, typename S, int PSC>
 __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, const S *__restrict__ fin,
                                               S *__restrict__ fout, const Geom &g,
                                               const PhysT<typename Store<S>::T> &ph, const Tiles &tl,
@@ -208,14 +169,13 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
                                               typename Store<S>::T *part, unsigned *s_mask, const int prev_cnt,
                                               const typename Store<S>::T *prev_recs,
                                               const typename Store<S>::T *prev_part, const unsigned *prev_mask,
-                                              typename Pr<typename Store<S>::T>::V *sbr,
-                                              const S *__restrict__ stage = nullptr, Hook hook = Hook()) {
+                                              typename Pr<typename Store<S>::T>::V *sbr) {
     using T = typename Store<S>::T;
     using P = Pr<T>;
     using V = typename P::V;
     constexpr int Q = L::Q;
     constexpr int NC = (L::D == 2) ? 3 : 6;
-    constexpr int NSLOT = pair_nslot<L, TMA>();
+    constexpr int NSLOT = pair_nslot<L>();
     const int cap = tl.cap;
 
     const unsigned tile = ent.x, ty = ent.y & 0xffffu, tz = ent.y >> 16;
@@ -254,9 +214,7 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     // sums unscaled once, and the outputs are formed scaled (s folded into the weights)
     constexpr bool SC = Store<S>::kScaled;
     T da[Q], db[Q];
-    if (TMA) pull_pair_stage<L, S>(stage, fin, g, ph, lane, pc.zA * L::TY + pc.yA, pc.zB * L::TY + pc.yB, xA, xB, yA,
-                                   yB, zA, zB, cellA, cellB, actA, actB, da, db);
-    else pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
+    pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
     V df[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -290,9 +248,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
         if (w < nwords) srec[w] = rw[j];
     }
     // the block's one barrier per tile: records staged, and every warp is done with the
-    // previous tile, whose partial forces are added up now (and, with TMA, with the stage)
+    // previous tile, whose partial forces are added up now
     __syncthreads();
-    hook();
     pair_flush<L, T>(prev_cnt, prev_recs, prev_part, prev_mask, pd, tid);
 
     // ---- candidates that can reach either row (one lane per candidate, ballot)
@@ -482,13 +439,10 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
 // One plain-fluid tile with two cells per thread (rows as in the particle-tile path): BGK +
 // Guo + pull on FP32 pairs. With F = 0 the Guo terms add exact zeros, so HASF = true gives
 // the same results as HASF = false.
-// TMA = true: the populations come from the tile's stage, and `hook` runs once the lane's
-// values are in registers (it holds the barrier after which the stage may be refilled).
-template <class L, typename S, bool HASF, bool TMA = false, class Hook = NoHook>
+template <class L, typename S, bool HASF>
 __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__restrict__ fout, const Geom &g,
                                                 const PhysT<typename Store<S>::T> &ph, const int x0, const int y0,
-                                                const int z0, int *flags, const S *__restrict__ stage = nullptr,
-                                                Hook hook = Hook()) {
+                                                const int z0, int *flags) {
     using T = typename Store<S>::T;
     using P = Pr<T>;
     using V = typename P::V;
@@ -506,13 +460,7 @@ __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
     constexpr bool SC = Store<S>::kScaled;   // as in psc_tile_pair: scale folded in
     T da[Q], db[Q];
-    if (TMA) {
-        pull_pair_stage<L, S>(stage, fin, g, ph, lane, pc.zA * L::TY + pc.yA, pc.zB * L::TY + pc.yB, xA, xB, yA, yB,
-                              zA, zB, cellA, cellB, actA, actB, da, db);
-        hook();
-    } else {
-        pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
-    }
+    pull_pair<L, S>(fin, g, ph, interior, xA, xB, yA, yB, zA, zB, cellA, cellB, actA, actB, da, db);
     V df[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) df[i] = P::mk(da[i], db[i]);
@@ -657,181 +605,4 @@ k_fluid_pair(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<type
         fluid_tile_pair<L, S, HASF>(fin, fout, g, ph, (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX,
                                     (int)ty * L::TY, (int)tz * L::TZ, flags);
     }
-}
-
-// ------------------------------------------------------------ kernels with a TMA stage
-// The same tile bodies, with each tile's populations brought into shared memory by TMA
-// (tma.cuh) one tile ahead: while a block computes tile k, the copies of its next tile are
-// in flight. Used for FP32 and 16-bit storage when every row of the lattice starts on a
-// 16-byte boundary (nx times the element size a multiple of 16).
-
-// Origin of list entry `ent` ({tile id, ty | tz << 16}).
-template <class L>
-__device__ __forceinline__ void tile_origin(const Geom &g, const uint2 ent, int &x0, int &y0, int &z0) {
-    const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
-    x0 = (int)(ent.x - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
-    y0 = (int)ty * L::TY;
-    z0 = (int)tz * L::TZ;
-}
-
-template <class L, typename S> __host__ __device__ constexpr size_t tma_pair_smem_bytes() {
-    return (size_t)TmaBox<L, S>::STAGE_BYTES + pair_smem_bytes<L, typename Store<S>::T, true>();
-}
-
-// Particle tiles (and, with STEAL, then the tiles without candidates) from one work counter
-// over the two lists, one tile of TMA prefetch: the next tile's index is claimed a tile
-// ahead, and its copies are issued right after the current tile's barrier.
-template <class L, typename S, int PSC, bool STEAL>
-__global__ void __launch_bounds__(kPThreads, (L::Q == 9) ? 6 : 4)
-k_collide_stream_tma(const __grid_constant__ CUtensorMap tmap, const S *__restrict__ fin, S *__restrict__ fout, Geom g,
-                     PhysT<typename Store<S>::T> ph, Tiles tl, Parts pd, int *flags) {
-    using T = typename Store<S>::T;
-    using V = typename Pr<T>::V;
-    constexpr int NC = (L::D == 2) ? 3 : 6;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
-    __shared__ unsigned s_mask[2][kPWarps];
-    __shared__ int s_it[2];
-    S *const stage = reinterpret_cast<S *>(smem);
-    T *const sm = reinterpret_cast<T *>(smem + TmaBox<L, S>::STAGE_BYTES);
-    constexpr int rsz = kPairCap * RW, psz = kPWarps * kPairCap * NC;
-    V *const sbr = reinterpret_cast<V *>(sm + 2 * (rsz + psz));
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    const int npsc = tl.stats[4];
-    const int ntot = STEAL ? npsc + tl.stats[5] : npsc;
-    const uint2 *const flist = tl.order + ntiles;
-    const int limit = min(tl.cap, kPairCap);
-    auto entry = [&](const int it) { return it < npsc ? tl.order[it] : flist[it - npsc]; };
-    auto issue = [&](const int it) {
-        int x0, y0, z0;
-        tile_origin<L>(g, entry(it), x0, y0, z0);
-        tma_issue_tile<L, S>(&tmap, reinterpret_cast<unsigned char *>(stage), &bar, x0, y0, z0);
-    };
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        mbar_fence_init();
-        const int it0 = atomicAdd(&tl.stats[6], 1);
-        s_it[0] = it0;
-        if (it0 < ntot) issue(it0);
-        s_it[1] = atomicAdd(&tl.stats[6], 1);
-    }
-    __syncthreads();
-    const T *blocks = reinterpret_cast<const T *>(tl.blocks);
-    int buf = 0, prev_cnt = 0;
-    const T *prev_recs = blocks;
-    unsigned parity = 0;
-    bool timed_out = false;
-    for (int k = 0;; ++k) {
-        const int it = s_it[k & 1];
-        if (it >= ntot) break;
-        // after the tile's barrier: the stage is free; the one thread that claims tiles
-        // issues the next tile's copies (its index it claimed itself a tile ago) and claims
-        // the tile after it (every thread has read s_it[k & 1] before the barrier)
-        auto hook = [&]() {
-            if (tid == 0) {
-                const int itn = s_it[(k + 1) & 1];
-                if (itn < ntot) issue(itn);
-                s_it[k & 1] = atomicAdd(&tl.stats[6], 1);
-            }
-        };
-        if (!mbar_wait_bounded(&bar, parity)) timed_out = true;
-        parity ^= 1u;
-        const uint2 ent = entry(it);
-        if (it < npsc) {
-            const int cnt = tl.count[ent.x];
-            const T *recs = blocks + (size_t)ent.x * block_elems<T>(tl.cap) + head_elems<T>();
-            T *const cur_part = sm + 2 * rsz + buf * psz;
-            T *const prv_part = sm + 2 * rsz + (buf ^ 1) * psz;
-            if (cnt <= limit) {
-                psc_tile_pair<L, S, PSC, true>(ent, cnt, fin, fout, g, ph, tl, pd, flags, sm + buf * rsz, cur_part,
-                                               s_mask[buf], prev_cnt, prev_recs, prv_part, s_mask[buf ^ 1], sbr, stage,
-                                               hook);
-                prev_cnt = cnt;
-            } else {       // more candidates than the pair path holds: k_collide_overflow's
-                __syncthreads();
-                hook();
-                pair_flush<L, T>(prev_cnt, prev_recs, prv_part, s_mask[buf ^ 1], pd, tid);
-                prev_cnt = 0;
-            }
-            prev_recs = recs;
-            buf ^= 1;
-        } else {
-            int x0, y0, z0;
-            tile_origin<L>(g, ent, x0, y0, z0);
-            const T *pr = prev_recs;
-            const T *pp = sm + 2 * rsz + (buf ^ 1) * psz;
-            const unsigned *pm = s_mask[buf ^ 1];
-            const int pc = prev_cnt;
-            fluid_tile_pair<L, S, true, true>(fin, fout, g, ph, x0, y0, z0, flags, stage, [&]() {
-                __syncthreads();
-                hook();
-                pair_flush<L, T>(pc, pr, pp, pm, pd, tid);    // the last particle tile's partials
-            });
-            prev_cnt = 0;
-        }
-    }
-    __syncthreads();
-    pair_flush<L, T>(prev_cnt, prev_recs, sm + 2 * rsz + (buf ^ 1) * psz, s_mask[buf ^ 1], pd, tid);
-    if (timed_out) {
-        atomicOr(flags, 4);
-        mbar_wait_bounded(&bar, parity ^ 1u);     // copies of a stuck phase, once more
-    }
-}
-
-// Tiles without candidates (all tiles when there are no particles), a fixed share per block
-// of a persistent grid, NS stages of TMA prefetch.
-template <class L, typename S, bool HASF, int NS>
-__global__ void __launch_bounds__(kPThreads, (L::Q == 9) ? 8 : 5)
-k_fluid_tma(const __grid_constant__ CUtensorMap tmap, const S *__restrict__ fin, S *__restrict__ fout, Geom g,
-            PhysT<typename Store<S>::T> ph, Tiles tl, int np, int *flags) {
-    using B = TmaBox<L, S>;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar[NS];
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
-    const int nlist = np == 0 ? (int)ntiles : tl.stats[5];
-    const uint2 *const flist = tl.order + ntiles;
-    auto origin = [&](const int it, int &x0, int &y0, int &z0) {
-        if (np == 0) {
-            const unsigned t = (unsigned)it, txy = t / (unsigned)g.nt[0];
-            x0 = (int)(t - txy * (unsigned)g.nt[0]) * L::TX;
-            y0 = (int)(txy % (unsigned)g.nt[1]) * L::TY;
-            z0 = (int)(txy / (unsigned)g.nt[1]) * L::TZ;
-        } else {
-            tile_origin<L>(g, flist[it], x0, y0, z0);
-        }
-    };
-    auto issue = [&](const int s, const int it) {
-        int x0, y0, z0;
-        origin(it, x0, y0, z0);
-        tma_issue_tile<L, S>(&tmap, smem + (size_t)s * B::STAGE_BYTES, &bar[s], x0, y0, z0);
-    };
-    if (tid == 0) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
-        mbar_fence_init();
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const int it = blockIdx.x + s * gridDim.x;
-            if (it < nlist) issue(s, it);
-        }
-    }
-    __syncthreads();
-    bool timed_out = false;
-    for (int k = 0;; ++k) {
-        const int it = blockIdx.x + k * gridDim.x;
-        if (it >= nlist) break;
-        const int s = k % NS;
-        if (!mbar_wait_bounded(&bar[s], (unsigned)(k / NS) & 1u)) timed_out = true;
-        int x0, y0, z0;
-        origin(it, x0, y0, z0);
-        fluid_tile_pair<L, S, HASF, true>(fin, fout, g, ph, x0, y0, z0, flags,
-                                          reinterpret_cast<const S *>(smem + (size_t)s * B::STAGE_BYTES), [&]() {
-                                              __syncthreads();
-                                              const int nit = it + NS * gridDim.x;
-                                              if (tid == 0 && nit < nlist) issue(s, nit);
-                                          });
-    }
-    if (timed_out) atomicOr(flags, 4);
 }

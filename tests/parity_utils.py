@@ -35,10 +35,10 @@ def run_oracle(case, f0, steps):
     return dict(f=f, F=F, T=T, rho=rho, u=u)
 
 
-def run_gpu(P, case, f0, steps, storage="f32", tile_cap=0, no_tma=False):
+def run_gpu(P, case, f0, steps, storage="f32", tile_cap=0):
     ctx = P.lbm_create(case["lattice"], *case["n"], bc=case["bc"], tau=case["tau"],
                        body_force=case["body_force"], storage=storage, psc=case.get("psc", 0),
-                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap, no_tma=no_tma)
+                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap)
     if f0 is not None:
         P.lbm_set_populations(ctx, f0)
     if len(case["r"]):
