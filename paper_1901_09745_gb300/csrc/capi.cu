@@ -374,6 +374,7 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
     }
     ctx->np = n;
     ctx->bins_valid = 0;
+    if (ctx->dem) dem_particles_changed(ctx->dem);
     ctx_update_wrap(ctx);
     return LBM_OK;
 }

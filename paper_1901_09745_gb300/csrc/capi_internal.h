@@ -76,3 +76,6 @@ size_t dem_state_bytes(const dem_ctx *dem);
 lbm_status dem_state_save(dem_ctx *dem, char *dst);
 lbm_status dem_state_load(dem_ctx *dem, const char *src, size_t size);
 void dem_state_clear(dem_ctx *dem);
+// The fluid context's particles were replaced by the host: the DEM rebuilds its neighbour
+// list at its next call.
+void dem_particles_changed(dem_ctx *dem);

@@ -1,10 +1,18 @@
 // dem.cu -- adhesive DEM contact update on the GPU (Liu & Wu, arXiv 1901.09745, Sec. 2.5).
 //
 // Per dem_step call (one LBM step):
-//   1. k_dem_bin:  particles into a uniform bin grid (bin side >= 2 r_max + skin).
-//   2. k_dem_nbr:  one warp per particle builds its neighbour list (every j with
-//                  |X_j - X_i| < r_i + r_j + skin), sorted by j, and carries each pair's
-//                  contact history over from the previous list.
+//   0. k_dem_decide: whether the neighbour list is rebuilt in this call: when a sub-step
+//                  of the previous call saw a particle a quarter of the skin away from
+//                  where it was at the last build, or the host changed the particles.
+//   1. k_dem_bin:  FP32 copies of the positions and velocities; on a rebuild, particles
+//                  into a uniform bin grid (bin side >= 2 r_max + skin).
+//   2. k_dem_nbr:  on a rebuild, one warp per particle builds its neighbour list (every j
+//                  with |X_j - X_i| < r_i + r_j + skin), sorted by j, into the other of the
+//                  two list buffers, carrying each pair's contact history over from the
+//                  current one. Between rebuilds the sub-steps keep the current list: a
+//                  pair not on it was farther apart than r_i + r_j + skin at the build, and
+//                  neither particle has moved skin/2 since (a sub-step that sees one move
+//                  that far reports it), so it cannot touch.
 //   3. k_dem_substep (x substeps): one warp per particle, one lane per neighbour:
 //        contact detection in FP64 with IEEE-rounded operations only (no FMA), so both
 //        ends of a pair and a CPU reference agree bit for bit on delta_N;
@@ -64,12 +72,40 @@ struct DemBufs {
     double *Xo, *Uo, *Omo;          // state at its end
     const double *Ff, *Tf;          // hydrodynamic force / torque (frozen)
     const double *Xref;             // positions when the neighbour list was built
-    const int *nbr_n, *nbr;         // neighbour count and slots [n][kNB]
-    float *hist;                    // [n][kNB][kH]
+    const int *nbr_n[2], *nbr[2];   // neighbour counts and slots [n][kNB] of both lists
+    float *hist[2];                 // [n][kNB][kH] of both lists
+    int *state;                     // DemState words (the current list is state[kListIdx])
     const double *minv;             // [n][2]: 1/m, 1/I
     int *flags;                     // [1] solve failures, [2] list overflow, [3] skin exceeded
     float reject;                   // pairs with an FP32 overlap below -reject cannot touch
 };
+
+// Device words of a DEM context: a rebuild request (nonzero: rebuild the neighbour list at
+// the next call; set by a sub-step or by the host), the index (0/1) of the current list
+// buffer, and this call's decision.
+enum { kRebuildReq = 0, kListIdx = 1, kRebuildNow = 2, kStateWords = 4 };
+
+// Programmatic dependent launch: a kernel launched with that attribute may start while the
+// kernel before it in the stream runs; it waits here until that kernel has finished and its
+// writes are visible, before touching anything the predecessor produced. A kernel lets its
+// successor start early with dep_launch().
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// The call's decision (thread 0), and the bin counts cleared for the binning (all threads;
+// unused when the list is kept).
+__global__ void k_dem_decide(int *state, int *count, long long nbins) {
+    dep_wait();
+    dep_launch();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long k = t; k < nbins; k += (long long)gridDim.x * blockDim.x) count[k] = 0;
+    if (t == 0) {
+        const int rb = state[kRebuildReq] != 0;
+        state[kRebuildNow] = rb;
+        if (rb) state[kListIdx] ^= 1;
+        state[kRebuildReq] = 0;
+    }
+}
 
 __device__ __forceinline__ int bin_of(double x, double bscale, int nb, int periodic) {
     int b = (int)floor(x * bscale);
@@ -79,12 +115,16 @@ __device__ __forceinline__ int bin_of(double x, double bscale, int nb, int perio
 }
 
 __global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, const double *U,
-                          const double *Om, float4 *Xf, float4 *Vf, int *count, int *list, int *flags) {
+                          const double *Om, float4 *Xf, float4 *Vf, int *count, int *list, int *flags,
+                          const int *state) {
+    dep_wait();
+    dep_launch();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     Xf[i] = make_float4((float)X[3 * i], (float)X[3 * i + 1], (float)X[3 * i + 2], (float)R[i]);
     Vf[2 * i] = make_float4((float)U[3 * i], (float)U[3 * i + 1], (float)U[3 * i + 2], (float)Om[3 * i]);
     Vf[2 * i + 1] = make_float4((float)Om[3 * i + 1], (float)Om[3 * i + 2], 0.0f, 0.0f);
+    if (!state[kRebuildNow]) return;
     int b[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -108,13 +148,21 @@ __device__ __forceinline__ int axis_at(int k, int start, int nb, int periodic) {
 __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I);
 
 __global__ void k_dem_nbr(DemGeom g, int n, const double *X, const double *R, const float4 *Xf,
-                          const int *count, const int *list, const int *old_n, const int *old_nbr,
-                          const float *old_hist, int *new_n, int *new_nbr, float *new_hist, double *Xref,
-                          double *minv, double density, int *flags) {
+                          const int *count, const int *list, int *const *lists_n, int *const *lists,
+                          float *const *hists, double *Xref, double *minv, double density, int *flags,
+                          const int *state) {
     __shared__ int s_buf[8][kNB];
+    dep_wait();
+    dep_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (i >= n) return;   // whole warp leaves together
+    if (i >= n || !state[kRebuildNow]) return;   // whole warp leaves together
+    // the new list goes to the buffer the decision selected; the previous one is the other
+    const int nw = state[kListIdx], od = nw ^ 1;
+    const int *old_n = lists_n[od], *old_nbr = lists[od];
+    const float *old_hist = hists[od];
+    int *new_n = lists_n[nw], *new_nbr = lists[nw];
+    float *new_hist = hists[nw];
     const double xi[3] = {X[3 * i], X[3 * i + 1], X[3 * i + 2]};
     const double ri = R[i];
     const float4 pi = Xf[i];
@@ -392,9 +440,14 @@ constexpr int kLPP = 4;   // lanes per particle in the sub-step kernel
 // sums are combined with shuffles in a fixed order, then the first lane integrates.
 template <int DIM>
 __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
+    dep_wait();
+    dep_launch();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kLPP, sub = t % kLPP;
     const bool valid = i < b.n;
+    const int li = b.state[kListIdx];
+    const int *const nbr_n = b.nbr_n[li], *const nbr = b.nbr[li];
+    float *const hist = b.hist[li];
     constexpr int dim = DIM;
     // force and torque components a 2D disc has: F_x, F_y and T_z
     auto used = [](int q) { return DIM == 3 || q == 0 || q == 1 || q == 5; };
@@ -411,7 +464,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
         const float uif[3] = {vi0.x, vi0.y, vi0.z};
         const float oif[3] = {vi0.w, vi1.x, vi1.y};
-        const int nn = b.nbr_n[i];
+        const int nn = nbr_n[i];
         if (sub == 0) {
             // the integration's inputs, loaded before the contact loop's stores
 #pragma unroll
@@ -420,8 +473,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             iI = b.minv[2 * i + 1];
         }
         for (int s = sub; s < nn; s += kLPP) {
-            const int j = b.nbr[i * kNB + s];
-            float *hp = b.hist + ((size_t)i * kNB + s) * kH;
+            const int j = nbr[i * kNB + s];
+            float *hp = hist + ((size_t)i * kNB + s) * kH;
             // everything the pair may need, loaded at once (one round trip after j)
             const float4 pj = b.Xf[j];
             double xj[3] = {0.0, 0.0, 0.0};
@@ -560,6 +613,8 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         disp2 += dd * dd;
     }
     if (disp2 > 0.25f * (float)(g.skin * g.skin)) atomicAdd(&b.flags[3], 1);
+    // a quarter of the skin used: the next call rebuilds the list
+    if (disp2 > 0.0625f * (float)(g.skin * g.skin)) b.state[kRebuildReq] = 1;
 #pragma unroll
     for (int a = 0; a < 3; ++a) { b.Xo[3 * i + a] = xn[a]; b.Uo[3 * i + a] = un[a]; b.Omo[3 * i + a] = on[a]; }
     b.Xfo[i] = make_float4((float)xn[0], (float)xn[1], (float)xn[2], (float)ri);
@@ -580,18 +635,33 @@ struct dem_ctx {
     float4 *Xf[2];           // FP32 copies of the positions (current, next)
     float4 *Vf[2];           // FP32 copies of the velocities and spins (current, next)
     float reject;
-    // CUDA graph of one dem_step call (even sub-step counts), one per neighbour-list parity
-    cudaGraphExec_t gexec[2];
-    const void *gkey[2][17];
-    int gsub[2];
+    // CUDA graph of one dem_step call (even sub-step counts), keyed on what it captures
+    cudaGraphExec_t gexec;
+    const void *gkey[17];
+    int gsub;
     int *bin_count, *bin_list;
     long long nbins;
     int *nbr_n[2], *nbr[2];
     float *hist[2];
-    int cur;                 // which neighbour-list buffer is current
-    int lists_valid;
+    int **lists_dev;         // device copies of {nbr_n[0], nbr_n[1]}, {nbr[0], nbr[1]}, {hist[0], hist[1]}
+    int *state;              // device words (kRebuildReq, kListIdx, kRebuildNow)
+    int lists_valid;         // the device lists belong to the current particle set
+    int force_rebuild;       // the host changed the particles: rebuild at the next call
     long long launches;
 };
+
+// Index of the current neighbour list (device word; synchronises the fluid's stream).
+static int dem_list_index(dem_ctx *d, int *idx) {
+    int h[kStateWords];
+    cudaError_t e = cudaMemcpyAsync(h, d->state, sizeof(h), cudaMemcpyDeviceToHost, d->fl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->fl->stream);
+    *idx = h[kListIdx] & 1;
+    return e == cudaSuccess;
+}
+
+void dem_particles_changed(dem_ctx *d) {
+    if (d) d->force_rebuild = 1;
+}
 
 static void dfree(void **p) { if (*p) cudaFree(*p); *p = NULL; }
 
@@ -601,7 +671,8 @@ void dem_release(dem_ctx *d) {
     dfree((void **)&d->minv);
     dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
     dfree((void **)&d->Vf[0]); dfree((void **)&d->Vf[1]);
-    for (int k = 0; k < 2; ++k) if (d->gexec[k]) cudaGraphExecDestroy(d->gexec[k]);
+    if (d->gexec) cudaGraphExecDestroy(d->gexec);
+    dfree((void **)&d->lists_dev); dfree((void **)&d->state);
     dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     free(d);
@@ -643,6 +714,14 @@ static lbm_status dem_reserve(dem_ctx *d) {
         DCK(cudaMemsetAsync(d->nbr_n[k], 0, (size_t)cap * sizeof(int), fl->stream), "memset");
         DCK(cudaMemsetAsync(d->hist[k], 0, (size_t)cap * kNB * kH * sizeof(float), fl->stream), "memset");
     }
+    if (!d->state) {
+        DCK(cudaMalloc(&d->state, kStateWords * sizeof(int)), "cudaMalloc(DEM state)");
+        DCK(cudaMemsetAsync(d->state, 0, kStateWords * sizeof(int), fl->stream), "memset");
+    }
+    if (!d->lists_dev) DCK(cudaMalloc(&d->lists_dev, 6 * sizeof(int *)), "cudaMalloc(DEM list table)");
+    int *tab[6] = {d->nbr_n[0], d->nbr_n[1], d->nbr[0], d->nbr[1], (int *)d->hist[0], (int *)d->hist[1]};
+    DCK(cudaMemcpyAsync(d->lists_dev, tab, sizeof(tab), cudaMemcpyHostToDevice, fl->stream), "DEM list table");
+    DCK(cudaStreamSynchronize(fl->stream), "sync");
     d->cap_n = cap;
     d->lists_valid = 0;
     return LBM_OK;
@@ -721,44 +800,67 @@ extern "C" lbm_status dem_destroy(dem_ctx *d) {
     return LBM_OK;
 }
 
-// Queue one dem_step call (list rebuild + sub-steps) without touching host-side state: the
-// particle buffers alternate between the fluid context's and the DEM's own each sub-step,
-// and `flip` (an odd count) tells the caller to swap them afterwards.
-static cudaError_t dem_enqueue(dem_ctx *d, int substeps, int cur) {
+// Launch with programmatic dependent launch (the kernel may start while its predecessor
+// in the stream finishes; every DEM kernel begins with dep_wait()).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dep(void (*kern)(KArgs...), unsigned blocks, unsigned threads, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Queue one dem_step call (rebuild decision, FP32 copies, list rebuild when due, sub-steps)
+// without touching host-side state: the particle buffers alternate between the fluid
+// context's and the DEM's own each sub-step, and `flip` (an odd count) tells the caller to
+// swap them afterwards.
+static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
     lbm_ctx *fl = d->fl;
     cudaStream_t s = fl->stream;
     const int n = d->n;
-    const int nx = cur ^ 1;
-    cudaError_t e = cudaMemsetAsync(d->bin_count, 0, (size_t)d->nbins * sizeof(int), s);
+    cudaError_t e = launch_dep(k_dem_decide, (unsigned)((d->nbins + 255) / 256 < 64 ? (d->nbins + 255) / 256 : 64),
+                               256u, s, d->state, d->bin_count, d->nbins);
+    if (e == cudaSuccess)
+        e = launch_dep(k_dem_bin, (unsigned)((n + 127) / 128), 128u, s, d->g, n, (const double *)fl->dX,
+                       (const double *)fl->dR, (const double *)fl->dU, (const double *)fl->dOm, d->Xf[0], d->Vf[0],
+                       d->bin_count, d->bin_list, fl->flags, (const int *)d->state);
+    if (e == cudaSuccess)
+        e = launch_dep(k_dem_nbr, (unsigned)((n + 7) / 8), 256u, s, d->g, n, (const double *)fl->dX,
+                       (const double *)fl->dR, (const float4 *)d->Xf[0], (const int *)d->bin_count,
+                       (const int *)d->bin_list, (int *const *)d->lists_dev, (int *const *)(d->lists_dev + 2),
+                       (float *const *)(d->lists_dev + 4), d->Xref, d->minv, d->ph.density, fl->flags,
+                       (const int *)d->state);
     if (e != cudaSuccess) return e;
-    k_dem_bin<<<(n + 127) / 128, 128, 0, s>>>(d->g, n, fl->dX, fl->dR, fl->dU, fl->dOm, d->Xf[0], d->Vf[0],
-                                               d->bin_count, d->bin_list,
-                                               fl->flags);
-    k_dem_nbr<<<(n + 7) / 8, 256, 0, s>>>(d->g, n, fl->dX, fl->dR, d->Xf[0], d->bin_count, d->bin_list,
-                                           d->nbr_n[cur], d->nbr[cur], d->hist[cur], d->nbr_n[nx], d->nbr[nx],
-                                           d->hist[nx], d->Xref, d->minv, d->ph.density, fl->flags);
     DemBufs b;
     b.n = n;
     b.R = fl->dR;
     b.Ff = fl->dF;
     b.Tf = fl->dT;
     b.Xref = d->Xref;
-    b.nbr_n = d->nbr_n[nx];
-    b.nbr = d->nbr[nx];
-    b.hist = d->hist[nx];
+    for (int k = 0; k < 2; ++k) { b.nbr_n[k] = d->nbr_n[k]; b.nbr[k] = d->nbr[k]; b.hist[k] = d->hist[k]; }
+    b.state = d->state;
     b.minv = d->minv;
     b.flags = fl->flags;
     b.reject = d->reject;
     const int threads = 128;
     const int blocks = (int)(((long long)n * kLPP + threads - 1) / threads);
     double *X[2] = {fl->dX, d->X2}, *U[2] = {fl->dU, d->U2}, *Om[2] = {fl->dOm, d->Om2};
-    for (int k = 0; k < substeps; ++k) {
+    for (int k = 0; k < substeps && e == cudaSuccess; ++k) {
         const int src = k & 1, dst = src ^ 1;
         b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src]; b.Vf = d->Vf[src];
         b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst]; b.Vfo = d->Vf[dst];
-        if (d->g.dim == 2) k_dem_substep<2><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
-        else k_dem_substep<3><<<blocks, threads, 0, s>>>(d->g, d->ph, b);
+        if (d->g.dim == 2) e = launch_dep(k_dem_substep<2>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b);
+        else e = launch_dep(k_dem_substep<3>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -770,11 +872,20 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     if (fl->np != d->n) d->lists_valid = 0;
     lbm_status st = dem_reserve(d);
     if (st != LBM_OK) return st;
-    // no list to carry contact history over from (first call, a new particle count, or a
-    // checkpoint without a DEM section): every pair starts without history
-    if (!d->lists_valid) DCK(cudaMemsetAsync(d->nbr_n[d->cur], 0, (size_t)d->n * sizeof(int), fl->stream), "memset");
     st = dem_setup_bins(d);
     if (st != LBM_OK) return st;
+    if (!d->lists_valid) {
+        // no list to carry contact history over from (first call, a new particle count, or
+        // a checkpoint without a DEM section): every pair starts without history
+        for (int k = 0; k < 2; ++k)
+            DCK(cudaMemsetAsync(d->nbr_n[k], 0, (size_t)d->n * sizeof(int), fl->stream), "memset");
+        d->force_rebuild = 1;
+    }
+    if (d->force_rebuild) {
+        // any nonzero request word rebuilds the list at the start of this call
+        DCK(cudaMemsetAsync(d->state + kRebuildReq, 0xff, sizeof(int), fl->stream), "memset");
+        d->force_rebuild = 0;
+    }
     // largest delta_C of any pair (R <= r_max / 2) plus a margin far above the FP32 error of
     // the position copies
     {
@@ -786,12 +897,16 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
         const double a0 = cbrt(9.0 * kPi * d->p.gamma * Rm * Rm / Es);
         const double dC = d->p.adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * Rm) : 0.0;
         d->reject = (float)(dC + d->g.margin);
+        if (dC >= d->g.skin) {
+            ctx_error(fl, "the neighbour-list skin %g must exceed the largest JKR pull-off separation %g "
+                          "(dem_params.skin)", d->g.skin, dC);
+            return LBM_ERR_ARG;
+        }
     }
-    const int cur = d->cur;
-    const int kernels = 2 + substeps;
+    const int kernels = 3 + substeps;
     // even sub-step counts leave every buffer where it started, so the whole call can be
-    // replayed from a CUDA graph (one per neighbour-list parity), keyed on every pointer
-    // and size it was captured with
+    // replayed from one CUDA graph, keyed on every pointer and size it was captured with
+    // (the list buffers in use are chosen on the device)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     DCK(cudaStreamIsCapturing(fl->stream, &cs), "cudaStreamIsCapturing");
     unsigned rbits;
@@ -802,27 +917,27 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
                            (const void *)(size_t)d->g.bin_cap};
     bool replayed = false;
     if (substeps % 2 == 0 && cs == cudaStreamCaptureStatusNone) {
-        bool same = d->gexec[cur] && d->gsub[cur] == substeps;
-        for (int k = 0; same && k < 17; ++k) same = (d->gkey[cur][k] == key[k]);
+        bool same = d->gexec && d->gsub == substeps;
+        for (int k = 0; same && k < 17; ++k) same = (d->gkey[k] == key[k]);
         if (!same) {
-            if (d->gexec[cur]) { cudaGraphExecDestroy(d->gexec[cur]); d->gexec[cur] = NULL; }
+            if (d->gexec) { cudaGraphExecDestroy(d->gexec); d->gexec = NULL; }
             cudaGraph_t graph = NULL;
             DCK(cudaStreamBeginCapture(fl->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
-            cudaError_t eq = dem_enqueue(d, substeps, cur);
+            cudaError_t eq = dem_enqueue(d, substeps);
             cudaError_t ec = cudaStreamEndCapture(fl->stream, &graph);
             DCK(eq, "DEM kernels (capture)");
             DCK(ec, "cudaStreamEndCapture");
-            cudaError_t ei = cudaGraphInstantiate(&d->gexec[cur], graph, 0);
+            cudaError_t ei = cudaGraphInstantiate(&d->gexec, graph, 0);
             cudaGraphDestroy(graph);
             DCK(ei, "cudaGraphInstantiate");
-            d->gsub[cur] = substeps;
-            for (int k = 0; k < 17; ++k) d->gkey[cur][k] = key[k];
+            d->gsub = substeps;
+            for (int k = 0; k < 17; ++k) d->gkey[k] = key[k];
         }
-        DCK(cudaGraphLaunch(d->gexec[cur], fl->stream), "cudaGraphLaunch");
+        DCK(cudaGraphLaunch(d->gexec, fl->stream), "cudaGraphLaunch");
         replayed = true;
     }
     if (!replayed) {
-        DCK(dem_enqueue(d, substeps, cur), "DEM kernels");
+        DCK(dem_enqueue(d, substeps), "DEM kernels");
         if (substeps & 1) {
             double *t;
             t = fl->dX; fl->dX = d->X2; d->X2 = t;
@@ -830,7 +945,6 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
             t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
         }
     }
-    d->cur = cur ^ 1;
     d->lists_valid = 1;
     d->launches += kernels;
     fl->launches += kernels;
@@ -858,11 +972,13 @@ lbm_status dem_state_save(dem_ctx *d, char *dst) {
     memcpy(dst, h, sizeof(h));
     dst += sizeof(h);
     cudaStream_t s = d->fl->stream;
-    DCK(cudaMemcpyAsync(dst, d->nbr_n[d->cur], n * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM counts");
+    int cur = 0;
+    if (!dem_list_index(d, &cur)) return ctx_cuda(d->fl, cudaGetLastError(), "read DEM state");
+    DCK(cudaMemcpyAsync(dst, d->nbr_n[cur], n * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM counts");
     dst += n * sizeof(int);
-    DCK(cudaMemcpyAsync(dst, d->nbr[d->cur], n * kNB * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM lists");
+    DCK(cudaMemcpyAsync(dst, d->nbr[cur], n * kNB * sizeof(int), cudaMemcpyDeviceToHost, s), "save DEM lists");
     dst += n * kNB * sizeof(int);
-    DCK(cudaMemcpyAsync(dst, d->hist[d->cur], n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, s),
+    DCK(cudaMemcpyAsync(dst, d->hist[cur], n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, s),
         "save DEM history");
     return LBM_OK;
 }
@@ -888,15 +1004,18 @@ lbm_status dem_state_load(dem_ctx *d, const char *src, size_t size) {
     if (st != LBM_OK) return st;
     src += sizeof(h);
     cudaStream_t s = d->fl->stream;
-    DCK(cudaMemcpyAsync(d->nbr_n[d->cur], src, n * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM counts");
+    int cur = 0;
+    if (!dem_list_index(d, &cur)) return ctx_cuda(d->fl, cudaGetLastError(), "read DEM state");
+    DCK(cudaMemcpyAsync(d->nbr_n[cur], src, n * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM counts");
     src += n * sizeof(int);
-    DCK(cudaMemcpyAsync(d->nbr[d->cur], src, n * kNB * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM lists");
+    DCK(cudaMemcpyAsync(d->nbr[cur], src, n * kNB * sizeof(int), cudaMemcpyHostToDevice, s), "load DEM lists");
     src += n * kNB * sizeof(int);
-    DCK(cudaMemcpyAsync(d->hist[d->cur], src, n * kNB * kH * sizeof(float), cudaMemcpyHostToDevice, s),
+    DCK(cudaMemcpyAsync(d->hist[cur], src, n * kNB * kH * sizeof(float), cudaMemcpyHostToDevice, s),
         "load DEM history");
     DCK(cudaStreamSynchronize(s), "sync");
     d->n = (int)n;
     d->lists_valid = 1;
+    d->force_rebuild = 1;    // the restored list is carried over into a list of the restored positions
     return LBM_OK;
 }
 
@@ -920,13 +1039,15 @@ extern "C" lbm_status dem_get_contacts(dem_ctx *d, int *pairs, double *hist, int
     *nout = 0;
     if (!d->lists_valid || d->n == 0) return ctx_check_flags(fl);
     const int n = d->n;
+    int cur = 0;
+    if (!dem_list_index(d, &cur)) return ctx_cuda(fl, cudaGetLastError(), "read DEM state");
     int *hn = (int *)malloc((size_t)n * sizeof(int));
     int *hb = (int *)malloc((size_t)n * kNB * sizeof(int));
     float *hh = (float *)malloc((size_t)n * kNB * kH * sizeof(float));
     if (!hn || !hb || !hh) { free(hn); free(hb); free(hh); return LBM_ERR_OOM; }
-    cudaError_t e = cudaMemcpyAsync(hn, d->nbr_n[d->cur], (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d->nbr[d->cur], (size_t)n * kNB * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hh, d->hist[d->cur], (size_t)n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, fl->stream);
+    cudaError_t e = cudaMemcpyAsync(hn, d->nbr_n[cur], (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d->nbr[cur], (size_t)n * kNB * sizeof(int), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hh, d->hist[cur], (size_t)n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, fl->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(fl->stream);
     if (e != cudaSuccess) { free(hn); free(hb); free(hh); return ctx_cuda(fl, e, "copy contacts"); }
     int k = 0;
