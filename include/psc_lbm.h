@@ -203,6 +203,49 @@ lbm_status dem_get_contacts(dem_ctx *dem, int *pairs, double *hist, int cap, int
  * out[2] bin/neighbour-list overflows, out[3] skin violations, out[4] particles. */
 lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
 
+/* ------------------------------------------------------------- slab decomposition --- */
+/* The lattice cut into slabs along its slowest axis (y for D2Q9, z for D3Q19), the domain
+ * decomposition by which the step shards: the update of a cell (Eq. 1-14) reads only its
+ * neighbours, so a slab needs from the others only the populations that stream across its
+ * faces (Eq. 1: the directions with e_s = +1 over its lower face, e_s = -1 over its upper one)
+ * and gives each particle its share of the force and torque sums of Eq. 14.
+ *
+ * lbm_decomp_layout (pure host function): the rows each slab owns, own[k] .. own[k+1] - 1
+ * (own has nslab + 1 entries; cuts on whole tile rows, 8 for D2Q9, 2 for D3Q19), and the
+ * ghost layers its lattice holds below and above them (one tile row thick on a face shared
+ * with another slab -- also across a periodic axis -- and 0 at a wall of the lattice). After
+ * every step the populations with e_s = +1 of the last owned row below each face are copied
+ * into the ghost row just above it, and those with e_s = -1 of the first owned row above the
+ * face into the ghost row just below it. Returns 0, or -1 when a slab would own fewer rows
+ * than a tile holds (or the lattice or nslab is invalid). */
+int lbm_decomp_layout(int lattice, int n_s, int periodic_s, int nslab, int *own, int *ghost_lo, int *ghost_hi);
+
+/* Which slabs hold which particle (pure host function): for slab k and particle i (centre
+ * coordinate c[i] along the slab axis, radius[i]), img[k * n + i] is the image m in
+ * {-1, 0, 1} whose centre c + m n_s puts the particle's shell (reach r + h + 1) over some of
+ * the slab's owned rows, or -99 when none does (one slab: every particle, m = 0). Returns
+ * 0, or -1 when the layout is invalid or a slab owns fewer than 2 (r + h) + 2 rows. */
+int lbm_decomp_assign(int lattice, int n_s, int periodic_s, int nslab, double shell_h, int n, const double *c,
+                      const double *radius, int *img);
+
+/* A decomposed lattice: nslab slab contexts (all on the current device, stepped one after
+ * the other on one stream) with the parameters of p for the whole lattice. Particles are
+ * given to every slab whose owned rows their shell (r + h of Table 1) can reach, as the
+ * periodic image next to that slab, and their force and torque are the sums of the slabs'
+ * parts; each slab must own at least 2 (r + h) + 2 rows (LBM_ERR_ARG otherwise). The
+ * populations and forces equal those of one context over the whole lattice (populations
+ * bit for bit: every cell sums the same candidates in the same order). Host arrays only. */
+typedef struct lbm_decomp lbm_decomp;
+lbm_status lbm_decomp_create(const lbm_params *p, int nslab, lbm_decomp **out);
+lbm_status lbm_decomp_destroy(lbm_decomp *d);
+lbm_status lbm_decomp_set_particles(lbm_decomp *d, int n, const double *X, const double *U, const double *Omega,
+                                    const double *radius);
+lbm_status lbm_decomp_set_populations(lbm_decomp *d, const double *f);   /* whole lattice, as lbm_set_populations */
+lbm_status lbm_decomp_get_populations(lbm_decomp *d, double *f);
+lbm_status lbm_decomp_step(lbm_decomp *d, int nsteps);
+lbm_status lbm_decomp_get_forces(lbm_decomp *d, double *F, double *T);  /* n x 3 each, totals per particle */
+const char *lbm_decomp_last_error(const lbm_decomp *d);                  /* never NULL */
+
 /* -------------------------------------------------- stepping without device allocation --- */
 /* The paper has no counterpart to this entry point; it is a service for callers that may
  * not allocate GPU memory themselves or let a library do it: for example a host program

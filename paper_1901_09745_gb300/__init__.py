@@ -113,6 +113,16 @@ def lib():
         "dem_get_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "dem_get_info": ([vp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
         "lbm_psc_step_noalloc": ([C.POINTER(LbmParams), vp, vp, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
+        "lbm_decomp_layout": ([C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip], C.c_int),
+        "lbm_decomp_assign": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, ip], C.c_int),
+        "lbm_decomp_create": ([C.POINTER(LbmParams), C.c_int, C.POINTER(C.c_void_p)], C.c_int),
+        "lbm_decomp_destroy": ([vp], C.c_int),
+        "lbm_decomp_set_particles": ([vp, C.c_int, vp, vp, vp, vp], C.c_int),
+        "lbm_decomp_set_populations": ([vp, vp], C.c_int),
+        "lbm_decomp_get_populations": ([vp, vp], C.c_int),
+        "lbm_decomp_step": ([vp, C.c_int], C.c_int),
+        "lbm_decomp_get_forces": ([vp, vp, vp], C.c_int),
+        "lbm_decomp_last_error": ([vp], C.c_char_p),
         "lbm_noalloc_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -445,3 +455,116 @@ def psc_drag(ctx, f0, X, radius, F, nsteps, checkpoint_every):
             return g * dX, g * dF
 
     return _PscDrag.apply(X, F)
+
+
+# ----------------------------------------------------------------------- slab decomposition
+NOT_HELD = -99
+
+
+def lbm_decomp_layout(lattice, n_s, periodic_s, nslab):
+    """(own, ghost_lo, ghost_hi): the rows each slab owns (own[k] .. own[k+1] - 1) and its
+    ghost layers below and above (see the header)."""
+    own = (C.c_int * (nslab + 1))()
+    glo = (C.c_int * max(nslab, 1))()
+    ghi = (C.c_int * max(nslab, 1))()
+    if lib().lbm_decomp_layout(int(lattice), int(n_s), int(bool(periodic_s)), int(nslab), own, glo, ghi) != 0:
+        raise ValueError("no slab layout for %d rows in %d slabs" % (n_s, nslab))
+    return list(own), list(glo)[:nslab], list(ghi)[:nslab]
+
+
+def lbm_decomp_assign(lattice, n_s, periodic_s, nslab, c, radius, shell_h=1.0):
+    """(nslab, n) int array: the periodic image m of each particle a slab holds, or NOT_HELD."""
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64).reshape(-1))
+    r = np.ascontiguousarray(np.asarray(radius, dtype=np.float64).reshape(-1))
+    img = np.zeros((nslab, c.size), dtype=np.int32)
+    st = lib().lbm_decomp_assign(int(lattice), int(n_s), int(bool(periodic_s)), int(nslab), float(shell_h), c.size,
+                                 c.ctypes.data_as(C.POINTER(C.c_double)), r.ctypes.data_as(C.POINTER(C.c_double)),
+                                 img.ctypes.data_as(C.POINTER(C.c_int)))
+    if st != 0:
+        raise ValueError("no particle assignment (layout invalid or a slab thinner than a shell)")
+    return img
+
+
+class Decomp:
+    """Owner of one ``lbm_decomp`` handle."""
+
+    def __init__(self, handle, params, nslab):
+        self.handle, self.params, self.nslab, self.np = handle, params, nslab, 0
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.lbm_decomp_destroy(h)
+
+    @property
+    def shape(self):
+        return (self.params.nz, self.params.ny, self.params.nx)
+
+
+def _dcheck(d, status):
+    if status != LBM_OK:
+        msg = lib().lbm_decomp_last_error(d.handle if d is not None else None)
+        raise LbmError(status, msg.decode() if msg else "")
+
+
+def lbm_decomp_create(lattice, nx, ny, nz, nslab, bc=(0, 0, 0), tau=0.8, body_force=(0.0, 0.0, 0.0), storage="f32",
+                      psc=LBM_PSC_MODIFIED, shell_h=1.0, dev_scale=0.0, tile_cap=0, stream=None):
+    p = LbmParams()
+    p.lattice = int(lattice)
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    for a in range(3):
+        p.bc[a] = int(bc[a])
+        p.body_force[a] = float(body_force[a])
+    p.tau = float(tau)
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.psc, p.shell_h, p.dev_scale, p.tile_cap = int(psc), float(shell_h), float(dev_scale), int(tile_cap)
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    p.stream = C.c_void_p(stream) if stream else None
+    h = C.c_void_p()
+    st = lib().lbm_decomp_create(C.byref(p), int(nslab), C.byref(h))
+    if st != LBM_OK:
+        raise LbmError(st, lib().lbm_decomp_last_error(None).decode())
+    return Decomp(h, p, int(nslab))
+
+
+def lbm_decomp_destroy(d):
+    if d.handle:
+        lib().lbm_decomp_destroy(d.handle)
+        d.handle = None
+
+
+def lbm_decomp_set_particles(d, X, U, Om, radius):
+    X, U, Om = (np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1, 3)) for a in (X, U, Om))
+    r = np.ascontiguousarray(np.asarray(radius, dtype=np.float64).reshape(-1))
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)
+    _dcheck(d, lib().lbm_decomp_set_particles(d.handle, r.size, vp(X), vp(U), vp(Om), vp(r)))
+    d.np = r.size
+
+
+def lbm_decomp_set_populations(d, f):
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float64))
+    _dcheck(d, lib().lbm_decomp_set_populations(d.handle, f.ctypes.data_as(C.c_void_p)))
+
+
+def lbm_decomp_get_populations(d):
+    nz, ny, nx = d.shape
+    f = np.zeros((d.params.lattice, nz, ny, nx))
+    _dcheck(d, lib().lbm_decomp_get_populations(d.handle, f.ctypes.data_as(C.c_void_p)))
+    return f
+
+
+def lbm_decomp_step(d, nsteps=1):
+    _dcheck(d, lib().lbm_decomp_step(d.handle, int(nsteps)))
+
+
+def lbm_decomp_get_forces(d):
+    F = np.zeros((d.np, 3))
+    T = np.zeros((d.np, 3))
+    _dcheck(d, lib().lbm_decomp_get_forces(d.handle, F.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p)))
+    return F, T

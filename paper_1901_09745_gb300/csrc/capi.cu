@@ -185,6 +185,8 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     for (int a = 0; a < 3; ++a) {
         g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
         g.inv_n[a] = 1.0 / g.n[a];
+        g.act_lo[a] = 0;
+        g.act_hi[a] = g.n[a];
     }
     ctx->ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     Phys &ph = ctx->ph;

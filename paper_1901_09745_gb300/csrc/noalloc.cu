@@ -88,6 +88,8 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
         g.wrap_img[a] = (a < (is2d ? 2 : 3)) && g.periodic[a];
         g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
         g.inv_n[a] = 1.0 / g.n[a];
+        g.act_lo[a] = 0;
+        g.act_hi[a] = g.n[a];
     }
     if (g.nt[1] > 65535 || g.nt[2] > 65535) return fail(LBM_ERR_ARG, "ny or nz too large for the tile grid");
     Phys ph;

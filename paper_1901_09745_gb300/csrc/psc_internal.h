@@ -16,6 +16,8 @@ struct Geom {
     int t[3];            // tile extent in cells (32 x 8 x 1 for D2Q9, 32 x 4 x 2 for D3Q19)
     int nt[3];           // tiles per axis
     double inv_n[3];     // 1 / n per axis (no FP64 division on the device)
+    int act_lo[3], act_hi[3];   // cells updated: act_lo <= x < act_hi per axis ([0, n) except in
+                                // a slab of a decomposed lattice, whose ghost layers are read only)
 };
 
 // Physical parameters (FP64 on the host; kernels convert to their compute type).

@@ -60,6 +60,14 @@ template <typename T> __host__ PhysT<T> make_phys(const Phys &ph) {
     return k;
 }
 
+// Is cell (x, y, z) one this context updates (inside the lattice and, in a slab of a
+// decomposed lattice, outside its ghost layers)?
+__device__ __forceinline__ bool cell_active(const Geom &g, const int x, const int y, const int z) {
+    return (unsigned)(x - g.act_lo[0]) < (unsigned)(g.act_hi[0] - g.act_lo[0]) &&
+           (unsigned)(y - g.act_lo[1]) < (unsigned)(g.act_hi[1] - g.act_lo[1]) &&
+           (unsigned)(z - g.act_lo[2]) < (unsigned)(g.act_hi[2] - g.act_lo[2]);
+}
+
 __device__ __forceinline__ float  rint_t(float v) { return rintf(v); }
 __device__ __forceinline__ double rint_t(double v) { return rint(v); }
 __device__ __forceinline__ float  sqrt_t(float v) { return sqrtf(v); }
@@ -462,7 +470,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
     const int lane = tid & 31, warp = tid >> 5;
     const int x0 = tx * L::TX, y0 = ty * L::TY, z0 = tz * L::TZ;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    const bool active = x < g.n[0] && y < g.n[1] && z < g.n[2];
+    const bool active = cell_active(g, x, y, z);
     const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
     const long long N = g.ncell;
 

@@ -190,8 +190,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     const PairCells<L> pc(lane, warp);
     const int xA = x0 + pc.xA, xB = x0 + pc.xB;
     const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
-    const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
-    const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
+    const bool actA = cell_active(g, xA, yA, zA);
+    const bool actB = cell_active(g, xB, yB, zB);
     const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
     const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
     const long long N = g.ncell;
@@ -452,8 +452,8 @@ __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__
     const PairCells<L> pc(lane, warp);
     const int xA = x0 + pc.xA, xB = x0 + pc.xB;
     const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
-    const bool actA = xA < g.n[0] && yA < g.n[1] && zA < g.n[2];
-    const bool actB = xB < g.n[0] && yB < g.n[1] && zB < g.n[2];
+    const bool actA = cell_active(g, xA, yA, zA);
+    const bool actB = cell_active(g, xB, yB, zB);
     const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
     const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
     const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
