@@ -184,7 +184,8 @@ lbm_status dem_create(const dem_params *p, lbm_ctx *fluid, dem_ctx **out);
 lbm_status dem_destroy(dem_ctx *dem);
 
 /* Advance `substeps` DEM sub-steps of dt_dem (Eq. 21-29): contact detection (a pair enters
- * contact at delta_N >= 0 and stays while delta_N > -delta_C), JKR / Hertz normal force,
+ * contact at delta_N >= 0 and stays while delta_N > -delta_C; likewise a particle and the
+ * nearer wall of each non-periodic axis), JKR / Hertz normal force,
  * sliding, twisting and rolling resistance, semi-implicit Euler motion. The hydrodynamic
  * force and torque of the last lbm_step stay fixed over the sub-steps (Sec. 2.5). The new
  * positions, velocities and spins replace the fluid context's particle state. */
@@ -198,6 +199,12 @@ lbm_status dem_get_particles(dem_ctx *dem, double *X, double *U, double *Omega, 
  * xyz; hist may be NULL). Host memory. LBM_ERR_OVERFLOW if more than cap pairs (*n still
  * receives the count). */
 lbm_status dem_get_contacts(dem_ctx *dem, int *pairs, double *hist, int cap, int *n);
+
+/* Contacts with the walls (the planes at -1/2 and n - 1/2 of every non-periodic axis, met as
+ * a half-space of the particles' material at rest: the law above with R = r, m* = m) after
+ * the last sub-step, as (particle, axis) pairs sorted by particle, and their history (7
+ * doubles each, as for pairs; hist may be NULL). LBM_ERR_OVERFLOW beyond cap. */
+lbm_status dem_get_wall_contacts(dem_ctx *dem, int *pw, double *hist, int cap, int *n);
 
 /* Counters: out[0] DEM kernels launched, out[1] contact solves that did not converge,
  * out[2] bin/neighbour-list overflows, out[3] skin violations, out[4] particles. */

@@ -118,7 +118,7 @@ def _extra_signatures(L):
     L.ora_jkr_contact_radius.restype = C.c_double
     L.ora_jkr_force.argtypes = [C.c_double, C.c_double, C.c_double]
     L.ora_jkr_force.restype = C.c_double
-    L.ora_dem_step.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, ip, ip, dp, C.c_int]
+    L.ora_dem_step.argtypes = [pp, C.c_int, dp, dp, dp, dp, dp, dp, C.c_int, ip, ip, dp, C.c_int, ip, dp]
     L.ora_dem_step.restype = C.c_int
     L.ora_pairs_within.argtypes = [pp, C.c_int, dp, dp, C.c_double, ip, C.c_int]
     L.ora_pairs_within.restype = C.c_int
@@ -156,9 +156,17 @@ class DemState:
         self.pairs = np.zeros((self.cap, 2), dtype=np.int32)
         self.hist = np.zeros((self.cap, NH))
         self.ncontact = 0
+        # wall contacts (non-periodic axes): flag and spring history per particle and axis
+        self.wflag = np.zeros((n, 3), dtype=np.int32)
+        self.whist = np.zeros((n, 3, NH))
 
     def contacts(self):
         return self.pairs[: self.ncontact].copy(), self.hist[: self.ncontact].copy()
+
+    def wall_contacts(self):
+        """(k, 2) array of (particle, axis) in contact with a wall, sorted, and their histories."""
+        idx = np.argwhere(self.wflag != 0).astype(np.int32)
+        return idx, np.array([self.whist[i, a] for i, a in idx]).reshape(-1, NH)
 
 
 def dem_step(p, st, Ff=None, Tf=None, substeps=1):
@@ -167,7 +175,8 @@ def dem_step(p, st, Ff=None, Tf=None, substeps=1):
     Tf = np.zeros((n, 3)) if Tf is None else _f64(Tf).reshape(n, 3)
     nc = C.c_int(st.ncontact)
     rc = lib().ora_dem_step(C.byref(p), n, _d(st.X), _d(st.U), _d(st.Om), _d(st.r), _d(Ff), _d(Tf),
-                            int(substeps), C.byref(nc), _i(st.pairs), _d(st.hist), st.cap)
+                            int(substeps), C.byref(nc), _i(st.pairs), _d(st.hist), st.cap, _i(st.wflag),
+                            _d(st.whist))
     st.ncontact = nc.value
     _check(rc, "dem_step")
     return st

@@ -37,6 +37,13 @@
  *     law of a sphere of the same radius): m = rho_p pi r^2, I = 1/2 m r^2.
  *  J8 Hertz (adhesive = 0, the paper's non-adhesive comparison): F_ne = 4/3 E* sqrt(R)
  *     delta^(3/2), a = sqrt(R delta), F_C = 0 in Eq. 29, no rolling resistance.
+ *  W1 walls (the packing of Sec. 3.5 settles onto a wall): every non-periodic axis a < dim
+ *     has the fluid's halfway bounce-back walls, planes at -1/2 and n_a - 1/2. A particle
+ *     meets the nearer of the two as a half-space of the same material that does not move:
+ *     the contact law above with R = r_i (1/R = 1/r_i + 1/infinity), m* = m_i, the wall's
+ *     velocity and spin zero, n the unit normal from the centre towards the plane and
+ *     delta_N = r_i - (distance from the centre to the plane); the same life cycle (J2) and
+ *     a spring history of its own.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -287,12 +294,110 @@ static int contact(const ora_dem_params *p, int i, int j, const double *X, const
     return ok ? DEM_OK : DEM_ERR_SOLVE;
 }
 
+/* W1: the wall of axis a nearer to particle i: unit normal n towards it and the overlap
+ * delta_N = r_i - (distance from the centre to the plane) */
+static double wall_overlap(const ora_dem_params *p, const double *X, const double *r, int i, int a, double *n)
+{
+    double dist;
+    int b;
+    for (b = 0; b < 3; ++b) n[b] = 0.0;
+    if (X[3 * i + a] < 0.5 * (p->n[a] - 1)) {     /* lower wall, plane at -1/2 */
+        dist = X[3 * i + a] + 0.5;
+        n[a] = -1.0;
+    } else {                                       /* upper wall, plane at n_a - 1/2 */
+        dist = ((double)p->n[a] - 0.5) - X[3 * i + a];
+        n[a] = 1.0;
+    }
+    return r[i] - dist;
+}
+
+/* Force and torque of particle i's contact with the wall of axis a (W1); hist its history. */
+static int wall_contact(const ora_dem_params *p, int i, int a, const double *X, const double *U,
+                        const double *Om, const double *r, double *hist, double *fi, double *ti)
+{
+    double n[3], R, Es, FC, a0, dC, dn, ac, Fne, mi, Ii, kN, etaN, kT, etaT, Gs;
+    double arm_i[3], w1[3], vij[3], vn, vt[3], Fn, Ft[3], Fscrit, mag, Omt, Mt, Mtcrit, Mr[3], tq[3];
+    double *xs = hist, *xt = hist + 3, *xr = hist + 4;
+    int b, ok = 1;
+    const double dt = p->dt;
+
+    dn = wall_overlap(p, X, r, i, a, n);
+    R = r[i];
+    Es = p->E / (2.0 * (1.0 - p->poisson * p->poisson));
+    if (p->adhesive) {
+        FC = 3.0 * PI * p->gamma * R;
+        a0 = cbrt(9.0 * PI * p->gamma * R * R / Es);
+        dC = a0 * a0 / (2.0 * cbrt(6.0) * R);
+        ac = ora_jkr_contact_radius(dn, a0, R, &ok);
+        Fne = ora_jkr_force(ac, a0, FC);
+    } else {
+        double dp = dn > 0.0 ? dn : 0.0;
+        FC = 0.0; a0 = 0.0; dC = 0.0;
+        ac = sqrt(R * dp);
+        Fne = 4.0 / 3.0 * Es * sqrt(R) * pow(dp, 1.5);
+    }
+    mass_inertia(p, r[i], &mi, &Ii);
+    kN = 2.0 * Es * ac;
+    etaN = p->alpha_n * sqrt(mi * kN);            /* m* = m_i against an immovable wall */
+    Gs = p->E / (4.0 * (2.0 - p->poisson) * (1.0 + p->poisson));
+    kT = p->k_t_scale * 8.0 * Gs * ac;
+    etaT = p->eta_t_scale * etaN;
+
+    /* velocity of i's contact point relative to the wall (at rest) */
+    for (b = 0; b < 3; ++b) arm_i[b] = r[i] * n[b];
+    cross3(&Om[3 * i], arm_i, w1);
+    for (b = 0; b < 3; ++b) vij[b] = U[3 * i + b] + w1[b];
+    vn = dot3(vij, n);
+    for (b = 0; b < 3; ++b) vt[b] = vij[b] - vn * n[b];
+    Fn = Fne + etaN * vn;
+
+    Fscrit = p->mu_f * fabs(Fne + 2.0 * FC);
+    rotate_into_plane(xs, n);
+    for (b = 0; b < 3; ++b) xs[b] += vt[b] * dt;
+    for (b = 0; b < 3; ++b) Ft[b] = -kT * xs[b] - etaT * vt[b];
+    mag = sqrt(dot3(Ft, Ft));
+    if (mag > Fscrit) {
+        for (b = 0; b < 3; ++b) Ft[b] *= Fscrit / mag;
+        if (kT > 0.0) for (b = 0; b < 3; ++b) xs[b] = -Ft[b] / kT;
+    }
+
+    Omt = dot3(&Om[3 * i], n);
+    xt[0] += Omt * dt;
+    Mt = -(kT * ac * ac / 2.0) * xt[0] - (etaT * ac * ac / 2.0) * Omt;
+    Mtcrit = 3.0 * PI * ac * Fscrit / 16.0;
+    if (fabs(Mt) > Mtcrit) {
+        Mt = (Mt > 0.0 ? 1.0 : -1.0) * Mtcrit;
+        if (kT * ac * ac > 0.0) xt[0] = -Mt / (kT * ac * ac / 2.0);
+    }
+
+    for (b = 0; b < 3; ++b) Mr[b] = 0.0;
+    if (p->adhesive) {
+        double xa = ac / a0, kr, Mrcrit, vL[3];
+        kr = 4.0 * FC * pow(xa, 1.5);
+        Mrcrit = kr * p->theta_crit * R;
+        rotate_into_plane(xr, n);
+        cross3(n, &Om[3 * i], vL);
+        for (b = 0; b < 3; ++b) xr[b] += R * vL[b] * dt;
+        cross3(n, xr, tq);
+        for (b = 0; b < 3; ++b) Mr[b] = kr * tq[b];
+        mag = sqrt(dot3(Mr, Mr));
+        if (mag > Mrcrit) {
+            for (b = 0; b < 3; ++b) { Mr[b] *= Mrcrit / mag; xr[b] *= Mrcrit / mag; }
+        }
+    }
+    for (b = 0; b < 3; ++b) fi[b] = -Fn * n[b] + Ft[b];
+    cross3(arm_i, Ft, tq);
+    for (b = 0; b < 3; ++b) ti[b] = tq[b] + Mt * n[b] + Mr[b];
+    (void)Ii; (void)dC;
+    return ok ? DEM_OK : DEM_ERR_SOLVE;
+}
+
 /* substeps DEM sub-steps with the hydrodynamic force Ff and torque Tf frozen (Sec. 2.5).
  * Contacts (pairs, hist) in and out: sorted canonical pairs and their spring history;
  * *ncontact holds the count. X, U, Om are updated in place. */
 int ora_dem_step(const ora_dem_params *p, int np, double *X, double *U, double *Om,
                  const double *r, const double *Ff, const double *Tf, int substeps,
-                 int *ncontact, int *pairs, double *hist, int cap)
+                 int *ncontact, int *pairs, double *hist, int cap, int *wflag, double *whist)
 {
     int s, k, i, a, rc = DEM_OK;
     int *npairs = (int *)malloc(sizeof(int) * 2 * (size_t)(cap > 0 ? cap : 1));
@@ -316,6 +421,33 @@ int ora_dem_step(const ora_dem_params *p, int np, double *X, double *U, double *
             for (a = 0; a < 3; ++a) {
                 Fc[3 * pi + a] += fi[a]; Mc[3 * pi + a] += ti[a];
                 Fc[3 * pj + a] += fj[a]; Mc[3 * pj + a] += tj[a];
+            }
+        }
+        /* W1: contacts with the walls of the non-periodic axes (after the pairs) */
+        for (i = 0; i < np && wflag; ++i) {
+            int ax;
+            for (ax = 0; ax < p->dim; ++ax) {
+                double n[3], fi[3], ti[3], dn, R, Es, FC, a0, dC;
+                double *h = &whist[NH * (3 * (size_t)i + ax)];
+                int was = wflag[3 * i + ax], on, hh;
+                if (p->periodic[ax]) continue;
+                dn = wall_overlap(p, X, r, i, ax, n);
+                R = r[i];
+                Es = p->E / (2.0 * (1.0 - p->poisson * p->poisson));
+                a0 = p->adhesive ? cbrt(9.0 * PI * p->gamma * R * R / Es) : 0.0;
+                dC = p->adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * R) : 0.0;
+                (void)FC;
+                on = p->adhesive ? (dn >= 0.0 || (was && dn > -dC)) : (dn > 0.0);
+                wflag[3 * i + ax] = on;
+                if (!on) {
+                    for (hh = 0; hh < NH; ++hh) h[hh] = 0.0;
+                    continue;
+                }
+                {
+                    int c = wall_contact(p, i, ax, X, U, Om, r, h, fi, ti);
+                    if (c != DEM_OK) rc = c;
+                }
+                for (a = 0; a < 3; ++a) { Fc[3 * i + a] += fi[a]; Mc[3 * i + a] += ti[a]; }
             }
         }
         /* Eq. 21 with semi-implicit Euler (J7) */

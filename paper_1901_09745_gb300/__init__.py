@@ -112,6 +112,7 @@ def lib():
         "dem_get_contacts": ([vp, vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "dem_get_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "dem_get_info": ([vp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
+        "dem_get_wall_contacts": ([vp, vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_psc_step_noalloc": ([C.POINTER(LbmParams), vp, vp, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
         "lbm_decomp_layout": ([C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip], C.c_int),
         "lbm_decomp_assign": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, ip], C.c_int),
@@ -391,6 +392,18 @@ def dem_get_contacts(dem, cap=None):
                                 hist.ctypes.data_as(C.c_void_p), cap, C.byref(n))
     _check(dem.fluid, st)
     return pairs[: n.value].copy(), hist[: n.value].copy()
+
+
+def dem_get_wall_contacts(dem, cap=None):
+    """(k, 2) array of (particle, axis) in contact with a wall, and their histories (k, 7)."""
+    n = C.c_int()
+    cap = cap or max(16, 3 * dem.fluid.np)
+    pw = np.zeros((cap, 2), dtype=np.int32)
+    hist = np.zeros((cap, 7))
+    st = lib().dem_get_wall_contacts(dem.handle, pw.ctypes.data_as(C.c_void_p), hist.ctypes.data_as(C.c_void_p),
+                                     cap, C.byref(n))
+    _check(dem.fluid, st)
+    return pw[: n.value].copy(), hist[: n.value].copy()
 
 
 def dem_get_info(dem):

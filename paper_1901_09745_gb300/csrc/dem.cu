@@ -75,6 +75,7 @@ struct DemBufs {
     const int *nbr_n[2], *nbr[2];   // neighbour counts and slots [n][kNB] of both lists
     float *hist[2];                 // [n][kNB][kH] of both lists
     int *state;                     // DemState words (the current list is state[kListIdx])
+    float *whist;                   // [n][3][kH] history of each particle's wall contacts, per axis
     const double *minv;             // [n][2]: 1/m, 1/I
     int *flags;                     // [1] solve failures, [2] list overflow, [3] skin exceeded
     float reject;                   // pairs with an FP32 overlap below -reject cannot touch
@@ -328,11 +329,13 @@ __device__ __forceinline__ float jkr_s(float t, int *fail, float s_prev) {
 // has decided whether the pair is in contact (exactly, see k_dem_substep) and passes the
 // unit normal n (from i towards j) and the overlap delta_N in FP32. hist is this view's copy
 // of the pair history; returns 0 and clears it when not in contact.
+// Rf and ms are the contact's effective radius and mass (Eq. 25: 1/R = 1/r_i + 1/r_j,
+// m* = m_i m_j / (m_i + m_j); against a wall R = r_i, m* = m_i, and rjf = 0 puts j's contact
+// point on the wall, which does not move).
 __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, const float *n, const float dnf,
-                             const float rif, const float rjf, float imi, float imj, const float *Ui,
+                             const float rif, const float rjf, const float Rf, const float ms, const float *Ui,
                              const float *Uj, const float *omi, const float *omj, float *h,
                              float *fo, float *to, int *fail) {
-    const float Rf = rif * rjf / (rif + rjf);
     const float Es = ph.Es;
     float FC = 0.0f, a0 = 0.0f;
     if (ph.adhesive) {
@@ -357,7 +360,6 @@ __device__ bool contact_on_i(const DemPhys &ph, int dim, const bool contact, con
         ac = sqrtf(Rf * dp);
         Fne = (4.0f / 3.0f) * Es * sqrtf(Rf) * dp * sqrtf(dp);
     }
-    const float ms = 1.0f / (imi + imj);        // m* = m_i m_j / (m_i + m_j)
     const float kN = 2.0f * Es * ac;
     const float etaN = ph.alpha_n * sqrtf(ms * kN);
     const float kT = ph.kt_scale * 8.0f * ph.Gs * ac;
@@ -564,7 +566,9 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             float fo[3], to[3];
             const float ujf[3] = {vj0.x, vj0.y, vj0.z};
             const float ojf[3] = {vj0.w, vj1.x, vj1.y};
-            if (contact_on_i(ph, dim, contact, nv, dnf, pif.w, pj.w, imi, imj, uif, ujf, oif, ojf, hl, fo, to, &fail)) {
+            const float Rij = pif.w * pj.w / (pif.w + pj.w), msij = 1.0f / (imi + imj);
+            if (contact_on_i(ph, dim, contact, nv, dnf, pif.w, pj.w, Rij, msij, uif, ujf, oif, ojf, hl, fo, to,
+                             &fail)) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (used(a)) acc[a] += (double)fo[a];
@@ -575,6 +579,53 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                 hp4[0] = make_float4(hl[0], hl[1], hl[2], hl[3]);
                 hp4[1] = make_float4(hl[4], hl[5], hl[6], hl[7]);
             }
+        }
+    }
+    // contacts with the walls of the non-periodic axes (the fluid's halfway bounce-back
+    // planes at -1/2 and n - 1/2): lane `sub` takes axis `sub`; the nearer wall is a half-space
+    // of the same material at rest (R = r_i, m* = m_i). The overlap and the decision are
+    // formed in FP64 with IEEE-rounded operations, as for the pairs.
+    if (valid && sub < dim && !g.periodic[sub]) {
+        const int a = sub;
+        const double lo_plane = 0.5 * (double)(g.n[a] - 1);
+        const bool lower = xi[a] < lo_plane;
+        const double dist = lower ? __dadd_rn(xi[a], 0.5) : __dsub_rn((double)g.n[a] - 0.5, xi[a]);
+        const double dn = __dsub_rn(ri, dist);
+        float4 *wp4 = reinterpret_cast<float4 *>(b.whist + ((size_t)i * 3 + a) * kH);
+        const float4 w0 = wp4[0], w1 = wp4[1];
+        const bool was = w1.w != 0.0f;
+        bool contact;
+        if (!ph.adhesive) {
+            contact = dn > 0.0;
+        } else if (dn >= 0.0) {
+            contact = true;
+        } else if (!was) {
+            contact = false;
+        } else {
+            const double a064 = cbrt(9.0 * kPi * (double)ph.gamma * ri * ri / (double)ph.Es);
+            contact = dn > -(a064 * a064 * ph.dc_coef / ri);
+        }
+        if (contact || was) {
+            float nv[3] = {0.0f, 0.0f, 0.0f};
+            nv[a] = lower ? -1.0f : 1.0f;
+            float hl[kH] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            float fo[3], to[3];
+            const float zero[3] = {0.0f, 0.0f, 0.0f};
+            const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
+            const float uif[3] = {vi0.x, vi0.y, vi0.z};
+            const float oif[3] = {vi0.w, vi1.x, vi1.y};
+            const float rif = (float)ri;
+            const float msw = 1.0f / (float)b.minv[2 * i];
+            if (contact_on_i(ph, dim, contact, nv, (float)dn, rif, 0.0f, rif, msw, uif, zero, oif, zero, hl, fo, to,
+                             &fail)) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (used(c)) acc[c] += (double)fo[c];
+                    if (used(3 + c)) acc[3 + c] += (double)to[c];
+                }
+            }
+            wp4[0] = make_float4(hl[0], hl[1], hl[2], hl[3]);
+            wp4[1] = make_float4(hl[4], hl[5], hl[6], hl[7]);
         }
     }
     // combine the kLPP partial sums (fixed butterfly order)
@@ -643,6 +694,7 @@ struct dem_ctx {
     long long nbins;
     int *nbr_n[2], *nbr[2];
     float *hist[2];
+    float *whist;            // [cap][3][kH] wall-contact history per particle and axis
     int **lists_dev;         // device copies of {nbr_n[0], nbr_n[1]}, {nbr[0], nbr[1]}, {hist[0], hist[1]}
     int *state;              // device words (kRebuildReq, kListIdx, kRebuildNow)
     int lists_valid;         // the device lists belong to the current particle set
@@ -672,7 +724,7 @@ void dem_release(dem_ctx *d) {
     dfree((void **)&d->Xf[0]); dfree((void **)&d->Xf[1]);
     dfree((void **)&d->Vf[0]); dfree((void **)&d->Vf[1]);
     if (d->gexec) cudaGraphExecDestroy(d->gexec);
-    dfree((void **)&d->lists_dev); dfree((void **)&d->state);
+    dfree((void **)&d->lists_dev); dfree((void **)&d->state); dfree((void **)&d->whist);
     dfree((void **)&d->bin_count); dfree((void **)&d->bin_list);
     for (int k = 0; k < 2; ++k) { dfree((void **)&d->nbr_n[k]); dfree((void **)&d->nbr[k]); dfree((void **)&d->hist[k]); }
     free(d);
@@ -707,6 +759,9 @@ static lbm_status dem_reserve(dem_ctx *d) {
     DCK(cudaMalloc(&d->U2, v), "cudaMalloc(DEM U)");
     DCK(cudaMalloc(&d->Om2, v), "cudaMalloc(DEM Omega)");
     DCK(cudaMalloc(&d->Xref, v), "cudaMalloc(DEM Xref)");
+    dfree((void **)&d->whist);
+    DCK(cudaMalloc(&d->whist, (size_t)cap * 3 * kH * sizeof(float)), "cudaMalloc(wall history)");
+    DCK(cudaMemsetAsync(d->whist, 0, (size_t)cap * 3 * kH * sizeof(float), fl->stream), "memset");
     for (int k = 0; k < 2; ++k) {
         DCK(cudaMalloc(&d->nbr_n[k], (size_t)cap * sizeof(int)), "cudaMalloc(neighbour counts)");
         DCK(cudaMalloc(&d->nbr[k], (size_t)cap * kNB * sizeof(int)), "cudaMalloc(neighbour lists)");
@@ -847,6 +902,7 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
     b.Xref = d->Xref;
     for (int k = 0; k < 2; ++k) { b.nbr_n[k] = d->nbr_n[k]; b.nbr[k] = d->nbr[k]; b.hist[k] = d->hist[k]; }
     b.state = d->state;
+    b.whist = d->whist;
     b.minv = d->minv;
     b.flags = fl->flags;
     b.reject = d->reject;
@@ -879,6 +935,7 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
         // a checkpoint without a DEM section): every pair starts without history
         for (int k = 0; k < 2; ++k)
             DCK(cudaMemsetAsync(d->nbr_n[k], 0, (size_t)d->n * sizeof(int), fl->stream), "memset");
+        DCK(cudaMemsetAsync(d->whist, 0, (size_t)d->n * 3 * kH * sizeof(float), fl->stream), "memset");
         d->force_rebuild = 1;
     }
     if (d->force_rebuild) {
@@ -954,15 +1011,16 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
 
 // ---------------------------------------------------------------- checkpoint section
 // Layout: {magic, n, kNB, kH} as int64, then the current list: counts (n int32), slots
-// (n x kNB int32), history (n x kNB x kH float). The next dem_step rebuilds the list from
-// the positions and carries the history over from this one, so a run resumed from it
-// continues exactly as the saved run did.
-static const long long kDemMagic = 0x50534344454d3031LL;   // "PSCDEM01"
+// (n x kNB int32), history (n x kNB x kH float), then the wall-contact history (n x 3 x kH
+// float). The next dem_step rebuilds the list from the positions and carries the history
+// over from this one, so a run resumed from it continues as the saved run did.
+static const long long kDemMagic = 0x50534344454d3032LL;   // "PSCDEM02"
 
 size_t dem_state_bytes(const dem_ctx *d) {
     if (!d || !d->lists_valid || d->n <= 0) return 0;
     const size_t n = (size_t)d->n;
-    return 4 * sizeof(long long) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float);
+    return 4 * sizeof(long long) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float) +
+           n * 3 * kH * sizeof(float);
 }
 
 lbm_status dem_state_save(dem_ctx *d, char *dst) {
@@ -980,6 +1038,8 @@ lbm_status dem_state_save(dem_ctx *d, char *dst) {
     dst += n * kNB * sizeof(int);
     DCK(cudaMemcpyAsync(dst, d->hist[cur], n * kNB * kH * sizeof(float), cudaMemcpyDeviceToHost, s),
         "save DEM history");
+    dst += n * kNB * kH * sizeof(float);
+    DCK(cudaMemcpyAsync(dst, d->whist, n * 3 * kH * sizeof(float), cudaMemcpyDeviceToHost, s), "save wall history");
     return LBM_OK;
 }
 
@@ -996,7 +1056,8 @@ lbm_status dem_state_load(dem_ctx *d, const char *src, size_t size) {
         return LBM_ERR_ARG;
     }
     const size_t n = (size_t)h[1];
-    if (size < sizeof(h) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float)) {
+    if (size < sizeof(h) + n * sizeof(int) + n * kNB * sizeof(int) + n * kNB * kH * sizeof(float) +
+                   n * 3 * kH * sizeof(float)) {
         ctx_error(d->fl, "DEM checkpoint section truncated");
         return LBM_ERR_ARG;
     }
@@ -1012,6 +1073,8 @@ lbm_status dem_state_load(dem_ctx *d, const char *src, size_t size) {
     src += n * kNB * sizeof(int);
     DCK(cudaMemcpyAsync(d->hist[cur], src, n * kNB * kH * sizeof(float), cudaMemcpyHostToDevice, s),
         "load DEM history");
+    src += n * kNB * kH * sizeof(float);
+    DCK(cudaMemcpyAsync(d->whist, src, n * 3 * kH * sizeof(float), cudaMemcpyHostToDevice, s), "load wall history");
     DCK(cudaStreamSynchronize(s), "sync");
     d->n = (int)n;
     d->lists_valid = 1;
@@ -1069,6 +1132,39 @@ extern "C" lbm_status dem_get_contacts(dem_ctx *d, int *pairs, double *hist, int
     free(hn); free(hb); free(hh);
     *nout = k;
     if (st != LBM_OK) { ctx_error(fl, "contact buffer holds %d pairs, %d needed", cap, k); return st; }
+    return ctx_check_flags(fl);
+}
+
+// Wall contacts of the last sub-step as (particle, axis) pairs sorted by particle, with the
+// history of each (7 doubles: sliding spring xyz, twist, rolling spring xyz).
+extern "C" lbm_status dem_get_wall_contacts(dem_ctx *d, int *pw, double *hist, int cap, int *nout) {
+    if (!d || !nout) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    *nout = 0;
+    if (!d->lists_valid || d->n == 0 || !d->whist) return ctx_check_flags(fl);
+    const size_t cnt = (size_t)d->n * 3 * kH;
+    float *hw = (float *)malloc(cnt * sizeof(float));
+    if (!hw) return LBM_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(hw, d->whist, cnt * sizeof(float), cudaMemcpyDeviceToHost, fl->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(fl->stream);
+    if (e != cudaSuccess) { free(hw); return ctx_cuda(fl, e, "copy wall history"); }
+    int k = 0;
+    lbm_status st = LBM_OK;
+    for (int i = 0; i < d->n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const float *h = hw + ((size_t)i * 3 + a) * kH;
+            if (h[7] == 0.0f) continue;
+            if (k < cap) {
+                if (pw) { pw[2 * k] = i; pw[2 * k + 1] = a; }
+                if (hist) for (int q = 0; q < 7; ++q) hist[7 * (size_t)k + q] = (double)h[q];
+            } else {
+                st = LBM_ERR_OVERFLOW;
+            }
+            ++k;
+        }
+    free(hw);
+    *nout = k;
+    if (st != LBM_OK) { ctx_error(fl, "wall contact buffer holds %d entries, %d needed", cap, k); return st; }
     return ctx_check_flags(fl);
 }
 

@@ -143,3 +143,45 @@ def test_coupled_fluid_forces_drive_dem(P):
     assert np.array_equal(pg, st.contacts()[0])
     assert rel_l2(Ug - w["U"], st.U - w["U"]) <= 1e-4
     assert rel_l2((Og - w["Om"])[:, 2], (st.Om - w["Om"])[:, 2]) <= 1e-4
+
+
+@pytest.mark.parametrize("adhesive", [1, 0])
+def test_wall_contacts_match_the_oracle(P, adhesive):
+    """Spheres falling onto the bottom wall of a box with walls in z (periodic in x and y),
+    three LBM-step-sized calls of 10 sub-steps with gravity: particle-particle and wall
+    contact lists bit for bit, velocities, spins and positions within 1e-4."""
+    import synth
+    rng = np.random.default_rng(31)
+    L, n = 36, 30
+    r = rng.uniform(1.5, 2.5, n)
+    X = np.zeros((n, 3))
+    X[:, :2] = synth.rsa_pack(rng, (L, L), r, (True, True), gap=0.05)     # a layer without overlaps
+    X[:, 2] = -0.5 + r + rng.uniform(-0.1, 0.12, n)        # some already pressed into the wall
+    U = np.zeros((n, 3)); U[:, 2] = -rng.uniform(0, 3e-3, n); U[:, :2] = rng.normal(0, 1e-3, (n, 2))
+    Om = rng.normal(0, 1e-3, (n, 3))
+    g = (0.0, 0.0, -2e-4)
+    prm = dict(DEM, gamma=2e-3 if adhesive else 2e-4)
+    ctx = P.lbm_create(19, L, L, L, bc=(0, 0, 1), tau=0.8, storage="f32")
+    P.lbm_set_particles(ctx, X, U, Om, r)
+    dem = P.dem_create(ctx, dt_dem=0.1, adhesive=adhesive, skin=2.0, gravity=g, **prm)
+    for _ in range(3):
+        P.dem_step(dem, 10)
+    Xg, Ug, Og = P.dem_get_particles(dem)
+    pg, _ = P.dem_get_contacts(dem)
+    wg, whg = P.dem_get_wall_contacts(dem)
+    info = P.dem_get_info(dem)
+    P.dem_destroy(dem)
+    P.lbm_destroy(ctx)
+    p = O.make_dem_params(dt=0.1, adhesive=adhesive, dim=3, n=(L, L, L), periodic=(1, 1, 0), gravity=g, **prm)
+    st = O.DemState(X, U, Om, r)
+    for _ in range(3):
+        O.dem_step(p, st, substeps=10)
+    wo, who = st.wall_contacts()
+    assert info["solve_failures"] == 0 and info["overflows"] == 0
+    assert len(wo) >= 5
+    assert np.array_equal(wg, wo), "wall contact lists differ"
+    assert np.array_equal(pg, st.contacts()[0])
+    assert rel_l2(Ug - U, st.U - U) <= 1e-4
+    assert rel_l2(Og - Om, st.Om - Om) <= 1e-4
+    assert rel_l2(Xg - X, st.X - X) <= 1e-4
+    assert rel_l2(whg, who) <= 1e-3

@@ -257,3 +257,72 @@ def test_rolling_and_twisting_resist_and_cap():
     Fs = 0.3 * abs(O.jkr_force(a, a0, FC) + 2 * FC)
     assert ti[0] == pytest.approx(-3 * math.pi * a * Fs / 16, rel=1e-9)
     assert tj[0] == pytest.approx(-ti[0], rel=1e-12)
+
+
+# ------------------------------------------------------------- walls (Sec. 3.5 packing)
+def _wall_params(adhesive, alpha_n=0.0, dt=2e-3, gamma=2e-4, n=(32, 32, 40), periodic=(1, 1, 0)):
+    return O.make_dem_params(E=2.0, poisson=0.3, gamma=gamma, adhesive=adhesive, alpha_n=alpha_n, dt=dt, dim=3,
+                             n=n, periodic=periodic)
+
+
+@pytest.mark.parametrize("side", ["lower", "upper"])
+def test_hertz_sphere_on_a_wall_closed_form(side):
+    """A sphere pressed by delta into a wall (plane at -1/2 or n - 1/2) is pushed away with
+    the Hertz force 4/3 E* sqrt(r) delta^(3/2) (R = r for a sphere on a plane, reading of the
+    wall as a half-space of the same material), and nothing else moves it."""
+    p = _wall_params(0)
+    r, d = 3.0, 0.05
+    z = -0.5 + r - d if side == "lower" else 40 - 0.5 - r + d
+    st = O.DemState([[10.0, 11.0, z]], [[0, 0, 0]], [[0, 0, 0]], [r])
+    O.dem_step(p, st, substeps=1)
+    m = p.density * 4 / 3 * math.pi * r ** 3
+    Es = 2.0 / (2 * (1 - 0.3 ** 2))
+    F = 4 / 3 * Es * math.sqrt(r) * d ** 1.5
+    sign = 1.0 if side == "lower" else -1.0
+    assert st.U[0, 2] == pytest.approx(sign * p.dt * F / m, rel=1e-12)
+    assert st.U[0, 0] == 0.0 and st.U[0, 1] == 0.0 and np.all(st.Om == 0.0)
+    assert st.wflag[0, 2] == 1 and st.wflag[0, 0] == 0 and st.wflag[0, 1] == 0
+
+
+def test_jkr_sphere_touching_a_wall_jumps_on_with_eight_ninths():
+    """JKR on a wall: at delta = 0 the sphere is pulled in with 8/9 F_C, F_C = 3 pi gamma r."""
+    gamma, r = 2e-3, 3.0
+    p = _wall_params(1, gamma=gamma)
+    st = O.DemState([[10.0, 11.0, -0.5 + r]], [[0, 0, 0]], [[0, 0, 0]], [r])
+    O.dem_step(p, st, substeps=1)
+    m = p.density * 4 / 3 * math.pi * r ** 3
+    FC = 3 * math.pi * gamma * r
+    assert st.U[0, 2] == pytest.approx(-p.dt * 8 / 9 * FC / m, rel=1e-9)
+
+
+def test_elastic_bounce_off_a_wall_returns_the_speed():
+    """Hertz without damping: the sphere leaves the wall with the speed it came with, and
+    the contact ends (no history left)."""
+    p = _wall_params(0, dt=5e-3)
+    r, v = 3.0, -2e-2
+    st = O.DemState([[10.0, 11.0, -0.5 + r + 0.02]], [[0, 0, v]], [[0, 0, 0]], [r])
+    touched = False
+    for _ in range(400):
+        O.dem_step(p, st, substeps=100)
+        touched |= bool(st.wflag[0, 2])
+        if touched and not st.wflag[0, 2]:
+            break
+    assert touched and not st.wflag[0, 2] and np.all(st.whist == 0.0)
+    assert st.U[0, 2] == pytest.approx(-v, rel=2e-3)
+
+
+def test_sphere_resting_on_a_wall_under_gravity_settles_at_the_hertz_overlap():
+    """Damped Hertz contact with gravity: the sphere comes to rest where the wall force
+    carries its weight, m g = 4/3 E* sqrt(r) delta^(3/2)."""
+    g = 2e-4
+    p = O.make_dem_params(E=2.0, poisson=0.3, adhesive=0, alpha_n=1.5, dt=2e-2, dim=3, n=(32, 32, 40),
+                          periodic=(1, 1, 0), gravity=(0, 0, -g))
+    r = 3.0
+    st = O.DemState([[10.0, 11.0, -0.5 + r + 0.01]], [[0, 0, 0]], [[0, 0, 0]], [r])
+    for _ in range(200):
+        O.dem_step(p, st, substeps=200)
+    m = p.density * 4 / 3 * math.pi * r ** 3
+    Es = 2.0 / (2 * (1 - 0.3 ** 2))
+    d = (m * g / (4 / 3 * Es * math.sqrt(r))) ** (2 / 3)
+    assert abs(st.U[0, 2]) < 1e-9
+    assert (-0.5 + r) - st.X[0, 2] == pytest.approx(d, rel=1e-4)
