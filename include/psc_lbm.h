@@ -55,7 +55,19 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_D2Q9 = 9, LBM_D3Q19 = 19 };
-enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1 };
+/* Faces of each axis. LBM_BC_OPEN: both faces open, a population entering through one is
+ * the value the face cell itself would have pulled along the face (zero normal gradient).
+ * LBM_BC_INFLOW (one axis a at most; x or y for D2Q9): the low face is a velocity inlet, the
+ * high face a constant-pressure outlet. On the inlet face the populations that enter
+ * (e_a = +1) are f_i = f_{-i} + 6 w_i rho e_i.u_in, the non-equilibrium part of the opposite
+ * population bounced back, with rho fixed by the known populations so that the face cell
+ * moves at u_in = lbm_params.inflow along a: rho (1 - u_a) = sum_{e_a=0} f + 2 sum_{e_a=-1} f.
+ * On the outlet face those that enter (e_a = -1) take the same form at rho = 1 and u = u_a
+ * along a, 1 + u_a = sum_{e_a=0} f + 2 sum_{e_a=+1} f. A population whose source also lies
+ * beyond a wall bounces back at the wall instead. (The paper names these boundaries for its
+ * drag test, Sec. 3.2, without formulas; this is the reading taken.) For the DEM every
+ * non-periodic axis is walled. */
+enum { LBM_BC_PERIODIC = 0, LBM_BC_BOUNCEBACK = 1, LBM_BC_OPEN = 2, LBM_BC_INFLOW = 3 };
 /* Population storage. Compute is FP64 for LBM_F64 and FP32 for the others. Every form
  * stores deviations f_i - w_i from the lattice weights. */
 enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16_DEV = 2, LBM_BF16_DEV = 3 };
@@ -65,7 +77,8 @@ enum { LBM_PSC_MODIFIED = 0, LBM_PSC_ORIGINAL = 1 };
 typedef struct {
     int lattice;            /* LBM_D2Q9 | LBM_D3Q19 (Sec. 2.1) */
     int nx, ny, nz;         /* lattice extent; nz = 1 for D2Q9 */
-    int bc[3];              /* per axis: LBM_BC_PERIODIC | LBM_BC_BOUNCEBACK (Sec. 2.2) */
+    int bc[3];              /* per axis: LBM_BC_PERIODIC | LBM_BC_BOUNCEBACK (Sec. 2.2) | LBM_BC_OPEN |
+                               LBM_BC_INFLOW (Sec. 3.2) */
     double tau;             /* relaxation parameter tau > 1/2 (Eq. 2); nu = (tau - 1/2)/3 */
     double body_force[3];   /* macroscopic body force F of Eq. 4 */
     int storage;            /* LBM_F64 | LBM_F32 | LBM_F16_DEV | LBM_BF16_DEV */
@@ -75,6 +88,7 @@ typedef struct {
                                <= 0 selects 4096 for FP16 and 1 for BF16 */
     int tile_cap;           /* candidate particles kept per lattice tile (<= 0: 64) */
     void *stream;           /* cudaStream_t to queue work on; NULL: the library makes one */
+    double inflow[3];       /* velocity imposed on the LBM_BC_INFLOW face (|u_a| < 0.3) */
 } lbm_params;
 
 /* Create a fluid at rest, f_i = f_i^eq(rho = 1, u = 0) = w_i (Eq. 3), with no particles.
@@ -132,7 +146,7 @@ lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F);
  * and the body force (dJdF, 3), by a hand-written reverse of the collide-stream step (the
  * paper has no adjoint; this is a derived quantity of Eq. 1-18). The particles must be
  * static (U = Omega = 0: LBM_ERR_UNSUPPORTED otherwise), storage FP32 or FP64, the
- * modified scheme, and every tile's candidates within tile_cap. Runs the T forward steps
+ * modified scheme, periodic or wall axes only, and every tile's candidates within tile_cap. Runs the T forward steps
  * (the context ends at step T as after lbm_step(ctx, T)), keeping a checkpoint every
  * checkpoint_every steps, then the reverse sweep, re-running each segment forward. The
  * gradient is exact for the discrete step except at the clamps of Table 1 (eps = 0 or 1,

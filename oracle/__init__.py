@@ -27,12 +27,15 @@ class Params(C.Structure):
         ("body_force", C.c_double * 3),
         ("psc", C.c_int),
         ("shell_h", C.c_double),
+        ("inflow", C.c_double * 3),
     ]
 
 
 def make_params(lattice, nx, ny, nz=1, bc=(0, 0, 0), tau=0.8, body_force=(0.0, 0.0, 0.0),
-                psc=0, shell_h=1.0):
+                psc=0, shell_h=1.0, inflow=(0.0, 0.0, 0.0)):
     p = Params()
+    for a in range(3):
+        p.inflow[a] = float(inflow[a])
     p.lattice = lattice
     p.nx, p.ny, p.nz = nx, ny, nz
     for a in range(3):

@@ -36,6 +36,17 @@
  *   R10 x_n - X_p is the minimum image along periodic axes.
  *   R12 walls are halfway (link) bounce-back, half a spacing beyond the first and last
  *       node of a wall axis; cell centres sit at integer coordinates 0..n-1.
+ *   B1  the inlet, outlet and open boundaries of the drag test (Sec. 3.2), named there
+ *       without formulas: a population f_i(x, t+1) whose source x - e_i lies beyond an open
+ *       face (or the outlet) takes the post-collision value at the source moved back onto
+ *       the face (zero gradient across it). The inlet is a velocity inlet: on its face the
+ *       unknown populations (source beyond the inlet) are the opposite ones plus the
+ *       difference of their equilibria (Eq. 3), f_i = f_{-i} + 6 w_i rho e_i.u_in, with
+ *       rho the density for which the face cell moves at u_in across the face:
+ *       rho (1 - u_in,a) = sum over e_a = 0 of f + 2 sum over e_a = -1 of f (a the inlet
+ *       axis). The outlet (the paper's constant pressure) takes the same form at rho = 1
+ *       with u = u_a along a, 1 + u_a = sum over e_a = 0 of f + 2 sum over e_a = +1 of f.
+ *       A wall beyond any face of the source takes precedence, then the inlet and outlet.
  *   Original PSC (Eq. 7-9, 11) with several particles in a cell: the collision adds
  *   sum_s B(eps_s) Omega^s(u_s), B_n = sum_s B(eps_s) (Eq. 8), and each particle's force
  *   is weighted by the cell's total B_n (Eq. 11).
@@ -58,11 +69,14 @@
 typedef struct {
     int lattice;           /* 9 = D2Q9, 19 = D3Q19 */
     int nx, ny, nz;        /* nz = 1 for D2Q9 */
-    int bc[3];             /* per axis: 0 periodic, 1 halfway bounce-back walls */
+    int bc[3];             /* per axis: 0 periodic, 1 halfway bounce-back walls, 2 open faces,
+                              3 velocity inlet (low face) and constant-pressure outlet (high
+                              face); reading B1 */
     double tau;            /* relaxation parameter (dt = 1) */
     double body_force[3];  /* macroscopic body force F of Eq. 4 */
     int psc;               /* 0 = modified (Eq. 12-14), 1 = original (Eq. 7-9, 11) */
     double shell_h;        /* h of Table 1 */
+    double inflow[3];      /* inlet velocity of axes with bc 3 */
 } ora_params;
 
 /* ---------------------------------------------------------------- O1: lattices --- */
@@ -428,24 +442,93 @@ int ora_step(const ora_params *p, double *f, int np, const double *X, const doub
     }
 
     /* streaming (push): f_i(x + e_i, t+1) = f_i^+(x, t); a link that leaves through a
-     * wall returns to its own cell in the opposite direction, f_{-i}(x, t+1) = f_i^+ */
+     * wall returns to its own cell in the opposite direction, f_{-i}(x, t+1) = f_i^+; one
+     * that leaves through an open face or the inlet leaves the lattice */
     for (c = 0; c < ncell; ++c) {
         int xc[3] = {(int)(c % n[0]), (int)((c / n[0]) % n[1]), (int)(c / ((long)n[0] * n[1]))};
         for (i = 0; i < L.q; ++i) {
-            int dst[3], wall = 0;
+            int dst[3], wall = 0, leaves = 0;
             long dc;
             for (a = 0; a < 3; ++a) {
                 dst[a] = xc[a] + L.e[i][a];
                 if (dst[a] < 0 || dst[a] >= n[a]) {
                     if (p->bc[a] == 0) dst[a] = (dst[a] + n[a]) % n[a];
-                    else wall = 1;
+                    else if (p->bc[a] == 1) wall = 1;
+                    else leaves = 1;
                 }
             }
             if (wall) {
                 f[L.opp[i] * ncell + c] = fpost[i * ncell + c];
-            } else {
+            } else if (!leaves) {
                 dc = ((long)dst[2] * n[1] + dst[1]) * n[0] + dst[0];
                 f[i * ncell + dc] = fpost[i * ncell + c];
+            }
+        }
+    }
+    /* the populations that come in through an open face or the inlet (B1): those whose
+     * source x - e_i lies beyond such a face and beyond no wall */
+    for (c = 0; c < ncell; ++c) {
+        int xc[3] = {(int)(c % n[0]), (int)((c / n[0]) % n[1]), (int)(c / ((long)n[0] * n[1]))};
+        for (i = 0; i < L.q; ++i) {
+            int src[3], wall = 0, inlet = 0, outside = 0;
+            for (a = 0; a < 3; ++a) {
+                src[a] = xc[a] - L.e[i][a];
+                if (src[a] >= 0 && src[a] < n[a]) continue;
+                if (p->bc[a] == 0) { src[a] = (src[a] + n[a]) % n[a]; continue; }
+                if (p->bc[a] == 1) { wall = 1; continue; }
+                outside = 1;
+                if (p->bc[a] == 3) inlet = 1;           /* the inlet or the outlet: below */
+                src[a] = src[a] < 0 ? 0 : n[a] - 1;     /* onto the face */
+            }
+            if (wall || !outside || inlet) continue;
+            {
+                long sc = ((long)src[2] * n[1] + src[1]) * n[0] + src[0];
+                f[i * ncell + c] = fpost[i * ncell + sc];
+            }
+        }
+    }
+    /* the velocity inlet and the constant-pressure outlet (B1): on the inlet face (x_a = 0)
+     * and the outlet face (x_a = n_a - 1), the populations whose source lies beyond that face
+     * and beyond no wall. The inlet takes rho from the known populations and u = u_in; the
+     * outlet takes rho = 1 and u = u_a along a, u_a from the known populations. */
+    for (a = 0; a < 3; ++a) {
+        int side;
+        if (p->bc[a] != 3) continue;
+        for (side = 0; side < 2; ++side) {
+            const int face = side ? n[a] - 1 : 0, in_dir = side ? -1 : 1;
+            for (c = 0; c < ncell; ++c) {
+                int xc[3] = {(int)(c % n[0]), (int)((c / n[0]) % n[1]), (int)(c / ((long)n[0] * n[1]))};
+                double known = 0.0, rho, u[3];
+                int b;
+                if (xc[a] != face) continue;
+                /* known: e_a = 0 once, e_a pointing out of the lattice through this face twice */
+                for (i = 0; i < L.q; ++i) {
+                    if (L.e[i][a] == 0) known += f[i * ncell + c];
+                    else if (L.e[i][a] == -in_dir) known += 2.0 * f[i * ncell + c];
+                }
+                if (!side) {
+                    /* rho (1 - u_a) = known */
+                    rho = known / (1.0 - p->inflow[a]);
+                    for (b = 0; b < 3; ++b) u[b] = p->inflow[b];
+                } else {
+                    /* rho = 1: 1 + u_a = known */
+                    rho = 1.0;
+                    for (b = 0; b < 3; ++b) u[b] = 0.0;
+                    u[a] = known - 1.0;
+                }
+                for (i = 0; i < L.q; ++i) {
+                    int wall = 0;
+                    double eu = 0.0;
+                    if (L.e[i][a] != in_dir) continue;
+                    for (b = 0; b < 3; ++b) {
+                        int sb = xc[b] - L.e[i][b];
+                        if (b != a && (sb < 0 || sb >= n[b]) && p->bc[b] == 1) wall = 1;
+                    }
+                    if (wall) continue;
+                    for (b = 0; b < 3; ++b) eu += L.e[i][b] * u[b];
+                    /* f_i - f_{-i} = f^eq_i - f^eq_{-i} = 6 w_i rho e_i.u (Eq. 3) */
+                    f[i * ncell + c] = f[L.opp[i] * ncell + c] + 6.0 * L.w[i] * rho * eu;
+                }
             }
         }
     }

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(_HERE), "include", "psc_lbm.h")
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 LBM_ERR_UNSTABLE, LBM_ERR_OVERFLOW, LBM_ERR_TIMEOUT, DEM_ERR_NO_CONVERGENCE = 5, 6, 7, 8
 LBM_D2Q9, LBM_D3Q19 = 9, 19
-LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK = 0, 1
+LBM_BC_PERIODIC, LBM_BC_BOUNCEBACK, LBM_BC_OPEN, LBM_BC_INFLOW = 0, 1, 2, 3
 LBM_F64, LBM_F32, LBM_F16_DEV, LBM_BF16_DEV = 0, 1, 2, 3
 LBM_PSC_MODIFIED, LBM_PSC_ORIGINAL = 0, 1
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16_DEV, "bf16": LBM_BF16_DEV}
@@ -54,6 +54,7 @@ class LbmParams(C.Structure):
         ("dev_scale", C.c_double),
         ("tile_cap", C.c_int),
         ("stream", C.c_void_p),
+        ("inflow", C.c_double * 3),
     ]
 
 
@@ -194,8 +195,10 @@ class Lbm:
 # ------------------------------------------------------------------------ the C calls
 def lbm_create(lattice, nx, ny, nz=1, bc=(0, 0, 0), tau=0.8, body_force=(0.0, 0.0, 0.0),
                storage="f32", psc=LBM_PSC_MODIFIED, shell_h=1.0, dev_scale=0.0, tile_cap=0,
-               stream=None):
+               stream=None, inflow=(0.0, 0.0, 0.0)):
     p = LbmParams()
+    for a in range(3):
+        p.inflow[a] = float(inflow[a])
     p.lattice = int(lattice)
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     for a in range(3):

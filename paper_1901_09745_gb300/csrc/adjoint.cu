@@ -62,7 +62,7 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
     const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
     T d[Q];
-    pull_q<L, T>(gt, g, x, y, z, cell, interior, active, ph.sc, d);
+    pull_q<L, T>(gt, g, x, y, z, cell, interior, active, ph.sc, d, ph);
     T drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -278,7 +278,7 @@ cudaError_t launch_adjoint_t(const void *gt, const void *lam_in, void *lam_out, 
     }
     dim3 grid(g.nt[0], g.nt[1], g.nt[2]);
     dim3 block(L::TX, L::TY, L::TZ);
-    kern<<<grid, block, smem, s>>>((const T *)gt, (const T *)lam_in, (T *)lam_out, g, make_phys<T>(ph), tl, pd,
+    kern<<<grid, block, smem, s>>>((const T *)gt, (const T *)lam_in, (T *)lam_out, g, make_phys<T>(ph, L::Q), tl, pd,
                                    (T)invT, dJdX, dFpart);
     return cudaGetLastError();
 }
@@ -313,6 +313,11 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
         return LBM_ERR_UNSUPPORTED;
     }
     if (ctx->p.psc != LBM_PSC_MODIFIED) { ctx_error(ctx, "the adjoint supports the modified PSC scheme"); return LBM_ERR_UNSUPPORTED; }
+    for (int a = 0; a < 3; ++a)
+        if (ctx->p.bc[a] != LBM_BC_PERIODIC && ctx->p.bc[a] != LBM_BC_BOUNCEBACK) {
+            ctx_error(ctx, "the adjoint supports periodic and wall axes only");
+            return LBM_ERR_UNSUPPORTED;
+        }
     const int n = ctx->np;
     const int K = checkpoint_every;
     const int nseg = (nsteps + K - 1) / K;

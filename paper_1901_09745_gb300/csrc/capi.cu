@@ -135,8 +135,22 @@ static lbm_status validate(const lbm_params *p) {
     }
     if (p->lattice == LBM_D2Q9 && p->nz != 1) { ctx_error(NULL, "D2Q9 needs nz = 1, got %d", p->nz); return LBM_ERR_ARG; }
     for (int a = 0; a < 3; ++a)
-        if (p->bc[a] != LBM_BC_PERIODIC && p->bc[a] != LBM_BC_BOUNCEBACK) {
-            ctx_error(NULL, "bc[%d] must be LBM_BC_PERIODIC or LBM_BC_BOUNCEBACK, got %d", a, p->bc[a]);
+        if (p->bc[a] < LBM_BC_PERIODIC || p->bc[a] > LBM_BC_INFLOW) {
+            ctx_error(NULL, "bc[%d] must be LBM_BC_PERIODIC, _BOUNCEBACK, _OPEN or _INFLOW, got %d", a, p->bc[a]);
+            return LBM_ERR_ARG;
+        }
+    {
+        int ninlet = 0;
+        for (int a = 0; a < 3; ++a) ninlet += (p->bc[a] == LBM_BC_INFLOW);
+        const int dimp = (p->lattice == LBM_D2Q9) ? 2 : 3;
+        if (ninlet > 1 || (dimp == 2 && (p->bc[2] == LBM_BC_INFLOW || p->bc[2] == LBM_BC_OPEN))) {
+            ctx_error(NULL, "at most one axis may be LBM_BC_INFLOW, and z of a D2Q9 lattice must be periodic or bounce-back");
+            return LBM_ERR_ARG;
+        }
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(p->inflow[a]) || fabs(p->inflow[a]) > 0.3) {
+            ctx_error(NULL, "inflow velocity components must be finite and below 0.3 in magnitude");
             return LBM_ERR_ARG;
         }
     if (!(p->tau > 0.5) || !isfinite(p->tau)) { ctx_error(NULL, "tau must exceed 1/2 (nu = (tau - 1/2)/3 > 0), got %g", p->tau); return LBM_ERR_ARG; }
@@ -179,7 +193,13 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     Geom &g = ctx->g;
     g.n[0] = p->nx; g.n[1] = p->ny; g.n[2] = p->nz;
     g.ncell = (long long)p->nx * p->ny * p->nz;
-    for (int a = 0; a < 3; ++a) { g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC); g.wrap_img[a] = 0; }
+    for (int a = 0; a < 3; ++a) {
+        g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC);
+        g.wrap_img[a] = 0;
+        g.face_lo[a] = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
+                     : p->bc[a] == LBM_BC_OPEN ? FACE_OPEN : FACE_INFLOW;
+        g.face_hi[a] = (g.face_lo[a] == FACE_INFLOW) ? FACE_OUTLET : g.face_lo[a];
+    }
     if (ctx->dim == 2) { g.t[0] = D2Q9::TX; g.t[1] = D2Q9::TY; g.t[2] = D2Q9::TZ; }
     else { g.t[0] = D3Q19::TX; g.t[1] = D3Q19::TY; g.t[2] = D3Q19::TZ; }
     for (int a = 0; a < 3; ++a) {
@@ -195,6 +215,10 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     ph.shell_h = ctx->p.shell_h;
     ph.scale = ctx->p.dev_scale;
     ph.psc = p->psc;
+    for (int a = 0; a < 3; ++a) ph.inflow[a] = p->inflow[a];
+    ph.inflow_axis = -1;
+    for (int a = 0; a < 3; ++a)
+        if (p->bc[a] == LBM_BC_INFLOW) ph.inflow_axis = a;
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess && p->stream) {

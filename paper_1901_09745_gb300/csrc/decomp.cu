@@ -167,6 +167,10 @@ extern "C" lbm_status lbm_decomp_create(const lbm_params *p, int nslab, lbm_deco
     d->ns = n[d->sax];
     d->periodic = (p->bc[d->sax] == LBM_BC_PERIODIC);
     d->P = nslab;
+    if (p->bc[d->sax] != LBM_BC_PERIODIC && p->bc[d->sax] != LBM_BC_BOUNCEBACK) {
+        free(d);
+        return dfail(NULL, LBM_ERR_UNSUPPORTED, "the slab axis must be periodic or walled");
+    }
     snprintf(d->err, sizeof(d->err), "no error");
     if (lbm_decomp_layout(p->lattice, d->ns, d->periodic, nslab, d->own, d->glo, d->ghi) != 0) {
         dfail(NULL, LBM_ERR_ARG, "cannot cut %d rows into %d slabs of at least one tile row", d->ns, nslab);

@@ -58,7 +58,12 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     if (p->nx < 1 || p->ny < 1 || p->nz < 1 || (p->lattice == LBM_D2Q9 && p->nz != 1))
         return fail(LBM_ERR_ARG, "invalid lattice extent");
     for (int a = 0; a < 3; ++a)
-        if (p->bc[a] != LBM_BC_PERIODIC && p->bc[a] != LBM_BC_BOUNCEBACK) return fail(LBM_ERR_ARG, "invalid bc");
+        if (p->bc[a] < LBM_BC_PERIODIC || p->bc[a] > LBM_BC_INFLOW || !isfinite(p->inflow[a]) ||
+            fabs(p->inflow[a]) > 0.3)
+            return fail(LBM_ERR_ARG, "invalid bc or inflow velocity");
+    if ((p->bc[0] == LBM_BC_INFLOW) + (p->bc[1] == LBM_BC_INFLOW) + (p->bc[2] == LBM_BC_INFLOW) > 1 ||
+        (p->lattice == LBM_D2Q9 && (p->bc[2] == LBM_BC_INFLOW || p->bc[2] == LBM_BC_OPEN)))
+        return fail(LBM_ERR_ARG, "at most one inflow axis, and z of a D2Q9 lattice periodic or bounce-back");
     if (!(p->tau > 0.5) || !isfinite(p->tau)) return fail(LBM_ERR_ARG, "tau must exceed 1/2");
     if (p->storage < LBM_F64 || p->storage > LBM_BF16_DEV) return fail(LBM_ERR_ARG, "unknown storage");
     if (p->psc != LBM_PSC_MODIFIED && p->psc != LBM_PSC_ORIGINAL) return fail(LBM_ERR_ARG, "unknown psc mode");
@@ -83,6 +88,9 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     g.t[2] = is2d ? D2Q9::TZ : D3Q19::TZ;
     for (int a = 0; a < 3; ++a) {
         g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC);
+        g.face_lo[a] = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
+                     : p->bc[a] == LBM_BC_OPEN ? FACE_OPEN : FACE_INFLOW;
+        g.face_hi[a] = (g.face_lo[a] == FACE_INFLOW) ? FACE_OUTLET : g.face_lo[a];
         // radii are device data here, so every periodic axis takes the per-cell minimum image
         // (always exact; only the cost of a few extra instructions)
         g.wrap_img[a] = (a < (is2d ? 2 : 3)) && g.periodic[a];
@@ -99,6 +107,10 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     ph.scale = (p->storage == LBM_F16_DEV) ? (p->dev_scale > 0.0 ? p->dev_scale : 4096.0)
              : (p->storage == LBM_BF16_DEV && p->dev_scale > 0.0) ? p->dev_scale : 1.0;
     ph.psc = p->psc;
+    for (int a = 0; a < 3; ++a) ph.inflow[a] = p->inflow[a];
+    ph.inflow_axis = -1;
+    for (int a = 0; a < 3; ++a)
+        if (p->bc[a] == LBM_BC_INFLOW) ph.inflow_axis = a;
 
     // carve the fixed array: counts | stats | flags | lists | tile order | f(r) | packed tile blocks
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];

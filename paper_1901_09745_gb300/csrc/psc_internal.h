@@ -18,7 +18,12 @@ struct Geom {
     double inv_n[3];     // 1 / n per axis (no FP64 division on the device)
     int act_lo[3], act_hi[3];   // cells updated: act_lo <= x < act_hi per axis ([0, n) except in
                                 // a slab of a decomposed lattice, whose ghost layers are read only)
+    int face_lo[3], face_hi[3]; // what lies beyond each face (FaceKind): a population whose source
+                                // x - e_i is beyond it wraps, bounces back, is clamped to the
+                                // lattice (open face) or is set by the velocity inlet or
+                                // the constant-pressure outlet
 };
+enum FaceKind { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_OPEN = 2, FACE_INFLOW = 3, FACE_OUTLET = 4 };
 
 // Physical parameters (FP64 on the host; kernels convert to their compute type).
 struct Phys {
@@ -27,6 +32,8 @@ struct Phys {
     double shell_h;      // h of Table 1
     double scale;        // stored value = scale * (f_i - w_i); 1 except for FP16/BF16
     int psc;             // 0 modified (Eq. 12-14), 1 original (Eq. 7-9, 11)
+    double inflow[3];    // velocity imposed on the inlet face
+    int inflow_axis;     // axis whose low face is the inlet, -1 when there is none
 };
 
 // Per-tile candidate lists built by the binning kernel: count[tile] particles whose

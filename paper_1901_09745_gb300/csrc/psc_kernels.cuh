@@ -47,9 +47,12 @@ template <typename T> struct PhysT {
     T F[3];         // body force
     T h;            // Table 1 shell half-width
     float2 sc;      // (scale, 1/scale) of the stored deviations
+    int inax;       // axis whose low face is an inlet (-1: none)
+    T inua;         // inlet velocity along that axis
+    T ineu[19];     // 6 w_i (e_i . u_in): f^eq_i - f^eq_{-i} of Eq. 3 at rho = 1
 };
 
-template <typename T> __host__ PhysT<T> make_phys(const Phys &ph) {
+template <typename T> __host__ PhysT<T> make_phys(const Phys &ph, const int lattice = 19) {
     PhysT<T> k;
     k.omega = (T)(1.0 / ph.tau);
     k.tmh = (T)(ph.tau - 0.5);
@@ -57,7 +60,66 @@ template <typename T> __host__ PhysT<T> make_phys(const Phys &ph) {
     for (int a = 0; a < 3; ++a) k.F[a] = (T)ph.body_force[a];
     k.h = (T)ph.shell_h;
     k.sc = make_float2((float)ph.scale, (float)(1.0 / ph.scale));
+    const double *u = ph.inflow;
+    k.inax = ph.inflow_axis;
+    k.inua = (T)(ph.inflow_axis >= 0 ? u[ph.inflow_axis] : 0.0);   // the inlet is a low face
+    for (int i = 0; i < 19; ++i) {
+        double eu = 0.0, w = 0.0;
+        if (lattice == 9 && i < 9) { eu = D2Q9::ex(i) * u[0] + D2Q9::ey(i) * u[1]; w = weight<D2Q9>(i); }
+        else if (lattice == 19) { eu = D3Q19::ex(i) * u[0] + D3Q19::ey(i) * u[1] + D3Q19::ez(i) * u[2]; w = weight<D3Q19>(i); }
+        k.ineu[i] = (T)(6.0 * w * eu);
+    }
     return k;
+}
+
+// Velocity inlet (reading of Sec. 3.2's "constant flow with velocity U0"): on the inlet face
+// the populations coming in (e_a = +1 along the inlet axis a) are not known from a
+// neighbour; they take the non-equilibrium part of the opposite population, f_i = f_{-i} +
+// f^eq_i(rho, u_in) - f^eq_{-i}(rho, u_in) = f_{-i} + 6 w_i rho e_i.u_in, with the density that
+// gives the face cell the velocity u_in along a: rho (1 - u_a) = sum_{e_a = 0} f + 2 sum_{e_a = -1} f.
+// df holds deviations (scaled by s when RAW); the directions in `fill` (those whose source
+// lies beyond the inlet and beyond no wall) are overwritten.
+template <class L, bool RAW, typename T>
+__device__ __forceinline__ void inflow_nebb(T *df, const PhysT<T> &ph, const float2 sc, const unsigned fill) {
+    const int a = ph.inax;
+    T sd = (T)0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int ea = (a == 0) ? L::ex(i) : ((a == 1) ? L::ey(i) : L::ez(i));
+        if (ea == 0) sd += df[i];
+        else if (ea == -1) sd += (T)2 * df[i];
+    }
+    const T s = RAW ? (T)sc.x : (T)1;
+    // sum_{e_a = 0} w + 2 sum_{e_a = -1} w = 1, so the deviations give rho directly
+    const T rho = ((T)1 + sd / s) / ((T)1 - ph.inua);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        if (fill & (1u << i)) df[i] = df[opp<L>(i)] + s * rho * ph.ineu[i];
+    }
+}
+
+// Constant-pressure outlet (reading of Sec. 3.2's outlet), on the high face of the inlet axis
+// a: the populations coming in (e_a = -1) are unknown; the density is held at 1 and the
+// velocity across the face follows from the known ones, 1 + u_a = sum_{e_a = 0} f +
+// 2 sum_{e_a = +1} f; the unknown ones are f_i = f_{-i} + 6 w_i e_{i,a} u_a (the difference of
+// the equilibria of Eq. 3 at rho = 1, u = u_a along a).
+template <class L, bool RAW, typename T>
+__device__ __forceinline__ void outlet_nebb(T *df, const PhysT<T> &ph, const float2 sc, const unsigned fill) {
+    const int a = ph.inax;
+    T sd = (T)0;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int ea = (a == 0) ? L::ex(i) : ((a == 1) ? L::ey(i) : L::ez(i));
+        if (ea == 0) sd += df[i];
+        else if (ea == 1) sd += (T)2 * df[i];
+    }
+    // sum_{e_a = 0} w + 2 sum_{e_a = +1} w = 1: the scaled deviation sum is s u_a
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const int ea = (a == 0) ? L::ex(i) : ((a == 1) ? L::ey(i) : L::ez(i));
+        if (fill & (1u << i)) df[i] = df[opp<L>(i)] + (T)(6.0 * weight<L>(i)) * (T)ea * sd;
+    }
+    (void)sc;
 }
 
 // Is cell (x, y, z) one this context updates (inside the lattice and, in a slab of a
@@ -81,22 +143,51 @@ __device__ __forceinline__ double dist_t(double v) { return sqrt(v); }
 // Population i of cell (x, y, z) after streaming: the value the neighbour x - e_i stored
 // in the previous step, or, when x - e_i lies beyond a wall, the value this cell stored in
 // the opposite direction (halfway bounce-back, Eq. 6).
+// Beyond an open face the source is clamped onto the face (zero gradient); through an
+// inlet or the outlet face the population is unknown (returned as 0, `from_inlet` or
+// `from_outlet` set) and is filled in by inflow_nebb or outlet_nebb once all are pulled. A
+// wall takes precedence over the inlet and outlet faces, these over open faces.
 template <class L, typename S>
 __device__ __forceinline__ typename Store<S>::T
 pull_one(const S *__restrict__ fin, const Geom &g, int x, int y, int z, long long cell, int i,
-         float2 sc) {
+         float2 sc, bool &from_inlet, bool &from_outlet) {
     int s[3] = {x - L::ex(i), y - L::ey(i), z - L::ez(i)};
-    bool bounce = false;
+    bool bounce = false, inflow = false, outflow = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (s[a] < 0 || s[a] >= g.n[a]) {
-            if (g.periodic[a]) s[a] += (s[a] < 0) ? g.n[a] : -g.n[a];
-            else bounce = true;
+            const int kind = (s[a] < 0) ? g.face_lo[a] : g.face_hi[a];
+            if (kind == FACE_PERIODIC) s[a] += (s[a] < 0) ? g.n[a] : -g.n[a];
+            else if (kind == FACE_WALL) bounce = true;
+            else if (kind == FACE_OPEN) s[a] = (s[a] < 0) ? 0 : g.n[a] - 1;
+            else if (kind == FACE_INFLOW) inflow = true;
+            else outflow = true;
         }
     }
     if (bounce) return Store<S>::ld(fin, (long long)opp<L>(i) * g.ncell + cell, sc);
+    from_inlet = inflow;
+    from_outlet = outflow && !inflow;
+    if (inflow || outflow) return (typename Store<S>::T)0;
     long long src = (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2]);
     return Store<S>::ld(fin, (long long)i * g.ncell + src, sc);
+}
+
+// All Q populations of cell (x, y, z) after streaming, one pull_one per direction, the
+// unknown ones at an inlet filled in.
+template <class L, typename S>
+__device__ __forceinline__ void pull_all(const S *__restrict__ fin, const Geom &g, int x, int y, int z,
+                                         long long cell, const PhysT<typename Store<S>::T> &ph,
+                                         typename Store<S>::T *df) {
+    unsigned fill = 0u, fillo = 0u;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        bool in = false, out = false;
+        df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc, in, out);
+        if (in) fill |= 1u << i;
+        if (out) fillo |= 1u << i;
+    }
+    if (fill) inflow_nebb<L, false>(df, ph, ph.sc, fill);
+    if (fillo) outlet_nebb<L, false>(df, ph, ph.sc, fillo);
 }
 
 // Warp sum of NV values per lane (NV a power of two <= 32) in NV - 1 + 5 - log2(NV) shuffles
@@ -184,7 +275,7 @@ __device__ __forceinline__ long long src_index(const NbrIdx &nb, const int i, co
 template <class L, typename S, bool RAW = false>
 __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g, int x, int y, int z,
                                        long long cell, bool interior, bool active, float2 sc,
-                                       typename Store<S>::T *df) {
+                                       typename Store<S>::T *df, const PhysT<typename Store<S>::T> &ph) {
     constexpr int Q = L::Q;
     using T = typename Store<S>::T;
     const long long N = g.ncell;
@@ -203,30 +294,45 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
         for (int i = 0; i < Q; ++i) df[i] = (T)0;
         return;
     }
-    // source x - e: from the -1 neighbour when e = +1 (m), from the +1 neighbour when e = -1 (p)
+    // source x - e: from the -1 neighbour when e = +1 (m), from the +1 neighbour when e = -1 (p);
+    // per face its kind: wrap (periodic), wall flag, offset 0 (open: clamped onto the face),
+    // inflow flag
     long long oxm = -1, oxp = 1, oym = -sy, oyp = sy, ozm = -sz, ozp = sz;
-    bool wxm = false, wxp = false, wym = false, wyp = false, wzm = false, wzp = false;
-    if (x == 0) { if (g.periodic[0]) oxm = g.n[0] - 1; else wxm = true; }
-    if (x == g.n[0] - 1) { if (g.periodic[0]) oxp = -(long long)(g.n[0] - 1); else wxp = true; }
-    if (y == 0) { if (g.periodic[1]) oym = (long long)(g.n[1] - 1) * sy; else wym = true; }
-    if (y == g.n[1] - 1) { if (g.periodic[1]) oyp = -(long long)(g.n[1] - 1) * sy; else wyp = true; }
+    unsigned wall_m = 0u, in_m = 0u, out_m = 0u;      // bits 0..5: faces xm xp ym yp zm zp
+    unsigned fill = 0u, fillo = 0u;       // directions coming in through the inlet, the outlet
+    auto face = [&](const int kind, long long &off, const long long wrap, const unsigned bit) {
+        if (kind == FACE_PERIODIC) off = wrap;
+        else if (kind == FACE_WALL) wall_m |= bit;
+        else if (kind == FACE_OPEN) off = 0;
+        else if (kind == FACE_INFLOW) in_m |= bit;
+        else out_m |= bit;
+    };
+    if (x == 0) face(g.face_lo[0], oxm, g.n[0] - 1, 1u);
+    if (x == g.n[0] - 1) face(g.face_hi[0], oxp, -(long long)(g.n[0] - 1), 2u);
+    if (y == 0) face(g.face_lo[1], oym, (long long)(g.n[1] - 1) * sy, 4u);
+    if (y == g.n[1] - 1) face(g.face_hi[1], oyp, -(long long)(g.n[1] - 1) * sy, 8u);
     if (L::D == 3) {
-        if (z == 0) { if (g.periodic[2]) ozm = (long long)(g.n[2] - 1) * sz; else wzm = true; }
-        if (z == g.n[2] - 1) { if (g.periodic[2]) ozp = -(long long)(g.n[2] - 1) * sz; else wzp = true; }
+        if (z == 0) face(g.face_lo[2], ozm, (long long)(g.n[2] - 1) * sz, 16u);
+        if (z == g.n[2] - 1) face(g.face_hi[2], ozp, -(long long)(g.n[2] - 1) * sz, 32u);
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         long long off = 0;
-        bool wall = false;
-        if (L::ex(i) == 1) { off += oxm; wall |= wxm; }
-        if (L::ex(i) == -1) { off += oxp; wall |= wxp; }
-        if (L::ey(i) == 1) { off += oym; wall |= wym; }
-        if (L::ey(i) == -1) { off += oyp; wall |= wyp; }
-        if (L::ez(i) == 1) { off += ozm; wall |= wzm; }
-        if (L::ez(i) == -1) { off += ozp; wall |= wzp; }
+        unsigned dm = 0u;        // the faces the source of direction i lies beyond (if any)
+        if (L::ex(i) == 1) { off += oxm; dm |= 1u; }
+        if (L::ex(i) == -1) { off += oxp; dm |= 2u; }
+        if (L::ey(i) == 1) { off += oym; dm |= 4u; }
+        if (L::ey(i) == -1) { off += oyp; dm |= 8u; }
+        if (L::ez(i) == 1) { off += ozm; dm |= 16u; }
+        if (L::ez(i) == -1) { off += ozp; dm |= 32u; }
+        const bool wall = (wall_m & dm) != 0u;
         const long long idx = wall ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
-        df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
+        if (!wall && (in_m & dm)) { df[i] = (T)0; fill |= 1u << i; }      // filled in below
+        else if (!wall && (out_m & dm)) { df[i] = (T)0; fillo |= 1u << i; }
+        else df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
     }
+    if (fill) inflow_nebb<L, RAW, T>(df, ph, sc, fill);
+    if (fillo) outlet_nebb<L, RAW, T>(df, ph, sc, fillo);
 }
 
 // ------------------------------------------------------------------- candidate records
@@ -496,8 +602,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
         for (int i = 0; i < Q; ++i)
             df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
     } else if (active) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
+        pull_all<L, S>(fin, g, x, y, z, cell, ph, df);
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = (T)0;
@@ -794,9 +899,11 @@ __global__ void k_gather(const S *__restrict__ fin, Geom g, PhysT<typename Store
     const int y = (int)((cell / g.n[0]) % g.n[1]);
     const int z = (int)(cell / ((long long)g.n[0] * g.n[1]));
     double drho = 0, j[3] = {0, 0, 0};
+    typename Store<S>::T df[L::Q];
+    pull_all<L, S>(fin, g, x, y, z, cell, ph, df);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const double d = (double)pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
+        const double d = (double)df[i];
         if (f_out) f_out[(long long)i * g.ncell + cell] = weight<L>(i) + d;
         drho += d;
         j[0] += L::ex(i) * d; j[1] += L::ey(i) * d; j[2] += L::ez(i) * d;
@@ -821,16 +928,19 @@ __global__ void k_set(const double *__restrict__ f, S *__restrict__ fout, Geom g
     for (int i = 0; i < L::Q; ++i) {
         const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
         int d[3];
-        bool wall = false;
+        bool wall = false, leaves = false;
         for (int a = 0; a < 3; ++a) {
             d[a] = xc[a] + e[a];
             if (d[a] < 0 || d[a] >= g.n[a]) {
-                if (g.periodic[a]) d[a] += (d[a] < 0) ? g.n[a] : -g.n[a];
-                else wall = true;
+                const int kind = (d[a] < 0) ? g.face_lo[a] : g.face_hi[a];
+                if (kind == FACE_PERIODIC) d[a] += (d[a] < 0) ? g.n[a] : -g.n[a];
+                else if (kind == FACE_WALL) wall = true;
+                else leaves = true;
             }
         }
         double v;
         if (wall) v = f[(long long)opp<L>(i) * g.ncell + cell];
+        else if (leaves) v = f[(long long)i * g.ncell + cell];     // leaves the lattice: never pulled
         else v = f[(long long)i * g.ncell + d[0] + (long long)g.n[0] * (d[1] + (long long)g.n[1] * d[2])];
         Store<S>::st(fout, (long long)i * g.ncell + cell, (typename Store<S>::T)(v - weight<L>(i)), ph.sc);
     }
@@ -896,7 +1006,7 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     }
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     dim3 block(L::TX, L::TY, L::TZ);
-    const PhysT<T> pt = make_phys<T>(ph);
+    const PhysT<T> pt = make_phys<T>(ph, L::Q);
     const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
     auto fkern = hasF ? k_fluid_pair<L, S, true> : k_fluid_pair<L, S, false>;
     const dim3 pblock(32, kPWarps);
@@ -968,8 +1078,8 @@ cudaError_t launch_gather_storage(int lattice, const void *fin, double *f_out, d
     using T = typename Store<S>::T;
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
-    if (lattice == 9) k_gather<D2Q9, S><<<blocks, threads, 0, s>>>((const S *)fin, g, make_phys<T>(ph), f_out, rho, u);
-    else k_gather<D3Q19, S><<<blocks, threads, 0, s>>>((const S *)fin, g, make_phys<T>(ph), f_out, rho, u);
+    if (lattice == 9) k_gather<D2Q9, S><<<blocks, threads, 0, s>>>((const S *)fin, g, make_phys<T>(ph, 9), f_out, rho, u);
+    else k_gather<D3Q19, S><<<blocks, threads, 0, s>>>((const S *)fin, g, make_phys<T>(ph, 19), f_out, rho, u);
     return cudaGetLastError();
 }
 
@@ -979,8 +1089,8 @@ cudaError_t launch_set_storage(int lattice, const double *f, void *fout, const G
     using T = typename Store<S>::T;
     const int threads = 256;
     const unsigned blocks = (unsigned)((g.ncell + threads - 1) / threads);
-    if (lattice == 9) k_set<D2Q9, S><<<blocks, threads, 0, s>>>(f, (S *)fout, g, make_phys<T>(ph));
-    else k_set<D3Q19, S><<<blocks, threads, 0, s>>>(f, (S *)fout, g, make_phys<T>(ph));
+    if (lattice == 9) k_set<D2Q9, S><<<blocks, threads, 0, s>>>(f, (S *)fout, g, make_phys<T>(ph, 9));
+    else k_set<D3Q19, S><<<blocks, threads, 0, s>>>(f, (S *)fout, g, make_phys<T>(ph, 19));
     return cudaGetLastError();
 }
 

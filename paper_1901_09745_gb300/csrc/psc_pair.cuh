@@ -139,8 +139,8 @@ __device__ __forceinline__ void pull_pair(const S *__restrict__ fin, const Geom 
         }
         return;
     }
-    pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da);
-    pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db);
+    pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da, ph);
+    pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db, ph);
 }
 
 // Store of velocity i at the lane's two cells (values already scaled for 16-bit storage).

@@ -15,7 +15,7 @@ def rel_l2(a, b):
 def oracle_params(case):
     return O.make_params(case["lattice"], *case["n"], bc=case["bc"], tau=case["tau"],
                          body_force=case["body_force"], psc=case.get("psc", 0),
-                         shell_h=case.get("shell_h", 1.0))
+                         shell_h=case.get("shell_h", 1.0), inflow=case.get("inflow", (0.0, 0.0, 0.0)))
 
 
 def perturbed_state(case, seed, amp=1e-3):
@@ -38,7 +38,8 @@ def run_oracle(case, f0, steps):
 def run_gpu(P, case, f0, steps, storage="f32", tile_cap=0):
     ctx = P.lbm_create(case["lattice"], *case["n"], bc=case["bc"], tau=case["tau"],
                        body_force=case["body_force"], storage=storage, psc=case.get("psc", 0),
-                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap)
+                       shell_h=case.get("shell_h", 1.0), tile_cap=tile_cap,
+                       inflow=case.get("inflow", (0.0, 0.0, 0.0)))
     if f0 is not None:
         P.lbm_set_populations(ctx, f0)
     if len(case["r"]):

@@ -497,3 +497,42 @@ def test_ergun_packed_bed_at_low_reynolds_number():
     r16 = _ergun_ratio(16, 1500)
     assert 0.70 < r12 < r16 < 1.05
     assert r16 > 0.85
+
+
+# ------------------------------------------------ inlet / outlet / open faces (Sec. 3.2)
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_uniform_stream_is_a_fixed_point_of_inlet_outlet_and_open_faces(lattice):
+    """Reading B1 of the drag test's boundaries: with the velocity inlet and the
+    constant-pressure outlet (non-equilibrium bounce-back at u_in, at rho = 1), the side
+    faces zero-gradient, the uniform stream f = f^eq(1, u_in) is left unchanged by collision
+    and streaming, exactly: for it the inlet's mass balance gives rho = 1, the outlet's
+    u_a = u_in, and f_{-i} + 6 w_i e_i.u_in = f^eq_i (a wrong sign or factor in either, a
+    wrong face, or a population dropped or doubled at a face would change it)."""
+    u_in = (0.04, 0.0, 0.0)
+    n = (24, 14, 1) if lattice == 9 else (20, 10, 12)
+    bc = (3, 2, 0) if lattice == 9 else (3, 2, 2)
+    p = O.make_params(lattice, *n, bc=bc, tau=0.7, inflow=u_in)
+    f = O.equilibrium(p, 1.0, u_in).copy()
+    f0 = f.copy()
+    for _ in range(5):
+        O.step(p, f, np.zeros((0, 3)))
+    assert np.max(np.abs(f - f0)) < 1e-15
+
+
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_open_faces_carry_a_stream_in_and_out(lattice):
+    """From rest, the inlet drives the fluid: once the start-up sound waves, which both faces
+    reflect, have died out by viscosity, the whole box streams at u_in (the inlet fixes the
+    velocity of its face), uniform in space, at the outlet's density 1 (the outlet fixes the
+    density of its face). A short box and nu = 1/6 damp the slowest wave by e^-10 in the run."""
+    u_in = (0.03, 0.0, 0.0)
+    n = (16, 6, 1) if lattice == 9 else (16, 6, 6)
+    bc = (3, 2, 0) if lattice == 9 else (3, 2, 2)
+    p = O.make_params(lattice, *n, bc=bc, tau=1.0, inflow=u_in)
+    f = O.equilibrium(p, 1.0, (0, 0, 0)).copy()
+    for _ in range(6000):
+        O.step(p, f, np.zeros((0, 3)))
+    rho, u = O.macro(p, f)
+    assert np.max(np.abs(u[..., 0] - u_in[0])) < 2e-3 * u_in[0]
+    assert np.max(np.abs(u[..., 1:])) < 2e-3 * u_in[0]
+    assert np.max(np.abs(rho - 1.0)) < 1e-4
