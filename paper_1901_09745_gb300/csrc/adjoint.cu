@@ -47,7 +47,7 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
     const int lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * L::TX, y0 = blockIdx.y * L::TY, z0 = blockIdx.z * L::TZ;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    const bool active = cell_active(g, x, y, z);
+    const bool active = cell_active<L>(g, x, y, z);
     const long long tile = blockIdx.x + (long long)g.nt[0] * (blockIdx.y + (long long)g.nt[1] * blockIdx.z);
     const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
     const long long N = g.ncell;
@@ -62,7 +62,7 @@ k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict_
                           (L::D == 2 || (z0 >= 1 && z0 + L::TZ < g.n[2]));
     const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
     T d[Q];
-    pull_q<L, T>(gt, g, x, y, z, cell, interior, active, ph.sc, d, ph);
+    pull_q<L, T>(gt, g, x, y, z, cell, interior, active, ph.sc, d);
     T drho = 0, j[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < Q; ++i) {

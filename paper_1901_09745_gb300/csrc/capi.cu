@@ -193,20 +193,20 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     Geom &g = ctx->g;
     g.n[0] = p->nx; g.n[1] = p->ny; g.n[2] = p->nz;
     g.ncell = (long long)p->nx * p->ny * p->nz;
+    g.faces = 0;
+    g.act0 = 0;
+    g.act1 = (ctx->dim == 2) ? g.n[1] : g.n[2];
     for (int a = 0; a < 3; ++a) {
         g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC);
         g.wrap_img[a] = 0;
-        g.face_lo[a] = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
+        const int lo = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
                      : p->bc[a] == LBM_BC_OPEN ? FACE_OPEN : FACE_INFLOW;
-        g.face_hi[a] = (g.face_lo[a] == FACE_INFLOW) ? FACE_OUTLET : g.face_lo[a];
+        set_face_kind(g, a, 0, lo);
+        set_face_kind(g, a, 1, lo == FACE_INFLOW ? FACE_OUTLET : lo);
     }
-    if (ctx->dim == 2) { g.t[0] = D2Q9::TX; g.t[1] = D2Q9::TY; g.t[2] = D2Q9::TZ; }
-    else { g.t[0] = D3Q19::TX; g.t[1] = D3Q19::TY; g.t[2] = D3Q19::TZ; }
     for (int a = 0; a < 3; ++a) {
-        g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
+        g.nt[a] = (g.n[a] + tile_ext(ctx->dim, a) - 1) / tile_ext(ctx->dim, a);
         g.inv_n[a] = 1.0 / g.n[a];
-        g.act_lo[a] = 0;
-        g.act_hi[a] = g.n[a];
     }
     ctx->ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     Phys &ph = ctx->ph;
@@ -296,7 +296,7 @@ static Tiles ctx_tiles(lbm_ctx *ctx) {
 // the widest particle shell does not fit well inside half the box.
 void ctx_update_wrap(lbm_ctx *ctx) {
     for (int a = 0; a < 3; ++a) {
-        double need = ctx->g.t[a] + 2.0 * (ctx->rmax + ctx->p.shell_h) + 2.0;
+        double need = tile_ext(ctx->dim, a) + 2.0 * (ctx->rmax + ctx->p.shell_h) + 2.0;
         const int w = (a < ctx->dim && ctx->g.periodic[a] && ctx->g.n[a] < need) ? 1 : 0;
         if (w != ctx->g.wrap_img[a]) ctx->gen += 1;     // the step's kernels take Geom by value
         ctx->g.wrap_img[a] = w;

@@ -4,7 +4,7 @@
 //
 // Each slab is an ordinary context over its own rows plus, on every face that is not a
 // wall of the lattice, a ghost layer of one tile's thickness (so the slab's tiles line up
-// with the whole lattice's). Only the owned rows are updated (Geom::act_lo/act_hi); the
+// with the whole lattice's). Only the owned rows are updated (Geom::act0/act1); the
 // ghost rows are read by the pull of the owned rows next to them. After every step the
 // populations that cross each face -- the directions with e_s = +1 going up, e_s = -1 going
 // down (3 of 9 in D2Q9, 5 of 19 in D3Q19) -- are copied from the owned row beside the face
@@ -204,8 +204,8 @@ extern "C" lbm_status lbm_decomp_create(const lbm_params *p, int nslab, lbm_deco
             return st;
         }
         lbm_ctx *c = d->slab[k];
-        c->g.act_lo[d->sax] = d->glo[k];
-        c->g.act_hi[d->sax] = d->glo[k] + (d->own[k + 1] - d->own[k]);
+        c->g.act0 = d->glo[k];                     // the slab axis is the slowest axis
+        c->g.act1 = d->glo[k] + (d->own[k + 1] - d->own[k]);
         c->gen += 1;
     }
     *out = d;

@@ -83,21 +83,20 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     Geom g;
     g.n[0] = p->nx; g.n[1] = p->ny; g.n[2] = p->nz;
     g.ncell = (long long)p->nx * p->ny * p->nz;
-    g.t[0] = is2d ? D2Q9::TX : D3Q19::TX;
-    g.t[1] = is2d ? D2Q9::TY : D3Q19::TY;
-    g.t[2] = is2d ? D2Q9::TZ : D3Q19::TZ;
+    g.faces = 0;
+    g.act0 = 0;
+    g.act1 = is2d ? g.n[1] : g.n[2];
     for (int a = 0; a < 3; ++a) {
         g.periodic[a] = (p->bc[a] == LBM_BC_PERIODIC);
-        g.face_lo[a] = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
+        const int lo = p->bc[a] == LBM_BC_PERIODIC ? FACE_PERIODIC : p->bc[a] == LBM_BC_BOUNCEBACK ? FACE_WALL
                      : p->bc[a] == LBM_BC_OPEN ? FACE_OPEN : FACE_INFLOW;
-        g.face_hi[a] = (g.face_lo[a] == FACE_INFLOW) ? FACE_OUTLET : g.face_lo[a];
+        set_face_kind(g, a, 0, lo);
+        set_face_kind(g, a, 1, lo == FACE_INFLOW ? FACE_OUTLET : lo);
         // radii are device data here, so every periodic axis takes the per-cell minimum image
         // (always exact; only the cost of a few extra instructions)
         g.wrap_img[a] = (a < (is2d ? 2 : 3)) && g.periodic[a];
-        g.nt[a] = (g.n[a] + g.t[a] - 1) / g.t[a];
+        g.nt[a] = (g.n[a] + tile_ext(is2d ? 2 : 3, a) - 1) / tile_ext(is2d ? 2 : 3, a);
         g.inv_n[a] = 1.0 / g.n[a];
-        g.act_lo[a] = 0;
-        g.act_hi[a] = g.n[a];
     }
     if (g.nt[1] > 65535 || g.nt[2] > 65535) return fail(LBM_ERR_ARG, "ny or nz too large for the tile grid");
     Phys ph;

@@ -75,7 +75,7 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
             if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; len[ax] = 1; continue; }
             const double X = xw[ax];
             const int lo = (int)ceil(X - r - h), hi = (int)floor(X + r + h);
-            nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], g.t[ax], g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
+            nr[ax] = axis_tile_ranges(lo, hi, g.n[ax], tile_ext(dim, ax), g.nt[ax], g.periodic[ax], ra[ax], rb[ax]);
             len[ax] = 0;
             for (int k = 0; k < nr[ax]; ++k) len[ax] += rb[ax][k] - ra[ax][k] + 1;
         }
@@ -94,12 +94,12 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
                     const int ty = axis_tile(kyz % len[1], nr[1], ra[1], rb[1]);
                     const int tz = axis_tile(kyz / len[1], nr[2], ra[2], rb[2]);
                     tile[q] = -1;
-                    const int org[3] = {tx * g.t[0], ty * g.t[1], tz * g.t[2]};
+                    const int org[3] = {tx * tile_ext(dim, 0), ty * tile_ext(dim, 1), tz * tile_ext(dim, 2)};
                     float d2 = 0.0f;
 #pragma unroll
                     for (int ax = 0; ax < 3; ++ax) {
                         if (ax >= dim) break;
-                        const float gap = axis_gap(xp[ax], (float)org[ax], (float)min(org[ax] + g.t[ax], g.n[ax]) - 1.0f,
+                        const float gap = axis_gap(xp[ax], (float)org[ax], (float)min(org[ax] + tile_ext(dim, ax), g.n[ax]) - 1.0f,
                                                    (float)g.n[ax], g.periodic[ax]);
                         d2 += gap * gap;
                     }

@@ -11,19 +11,34 @@ namespace psc {
 struct Geom {
     int n[3];            // nx, ny, nz
     long long ncell;     // nx * ny * nz
-    int periodic[3];     // 1 = periodic axis, 0 = halfway bounce-back walls
+    int periodic[3];     // 1 = periodic axis, 0 = another face kind (see faces)
     int wrap_img[3];     // 1 = periodic axis short enough to need a per-cell minimum image
-    int t[3];            // tile extent in cells (32 x 8 x 1 for D2Q9, 32 x 4 x 2 for D3Q19)
-    int nt[3];           // tiles per axis
+    int nt[3];           // tiles per axis (tile extent: tile_ext)
+    int faces;           // what lies beyond each face, a FaceKind in 3 bits per face (face_kind):
+                         // a population whose source x - e_i is beyond it wraps, bounces back,
+                         // is clamped to the lattice (open face) or is set by the velocity inlet
+                         // or the constant-pressure outlet
     double inv_n[3];     // 1 / n per axis (no FP64 division on the device)
-    int act_lo[3], act_hi[3];   // cells updated: act_lo <= x < act_hi per axis ([0, n) except in
-                                // a slab of a decomposed lattice, whose ghost layers are read only)
-    int face_lo[3], face_hi[3]; // what lies beyond each face (FaceKind): a population whose source
-                                // x - e_i is beyond it wraps, bounces back, is clamped to the
-                                // lattice (open face) or is set by the velocity inlet or
-                                // the constant-pressure outlet
+    int act0, act1;      // cells updated along the slowest axis (y for D2Q9, z for D3Q19):
+                         // act0 <= coordinate < act1 ([0, n) except in a slab of a decomposed
+                         // lattice, whose ghost layers are read only)
 };
+// The kernels take Geom by value next to their other parameters; it is kept this compact
+// on purpose (each field added to it measured a few per cent on the collide-stream kernels).
 enum FaceKind { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_OPEN = 2, FACE_INFLOW = 3, FACE_OUTLET = 4 };
+// Kind of the low (hi = 0) or high (hi = 1) face of axis a.
+__host__ __device__ inline int face_kind(const Geom &g, const int a, const int hi) {
+    return (g.faces >> (6 * a + 3 * hi)) & 7;
+}
+__host__ inline void set_face_kind(Geom &g, const int a, const int hi, const int kind) {
+    const int sh = 6 * a + 3 * hi;
+    g.faces = (g.faces & ~(7 << sh)) | (kind << sh);
+}
+// Tile extent along axis ax: 32 x 8 x 1 cells for D2Q9, 32 x 4 x 2 for D3Q19 (one tile is
+// one thread block of the single-cell kernels).
+__host__ __device__ inline int tile_ext(const int dim, const int ax) {
+    return dim == 2 ? (ax == 0 ? 32 : (ax == 1 ? 8 : 1)) : (ax == 0 ? 32 : (ax == 1 ? 4 : 2));
+}
 
 // Physical parameters (FP64 on the host; kernels convert to their compute type).
 struct Phys {

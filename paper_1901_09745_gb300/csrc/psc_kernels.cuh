@@ -123,11 +123,11 @@ __device__ __forceinline__ void outlet_nebb(T *df, const PhysT<T> &ph, const flo
 }
 
 // Is cell (x, y, z) one this context updates (inside the lattice and, in a slab of a
-// decomposed lattice, outside its ghost layers)?
+// decomposed lattice, outside its ghost layers along the slowest axis; act1 <= n there)?
+template <class L>
 __device__ __forceinline__ bool cell_active(const Geom &g, const int x, const int y, const int z) {
-    return (unsigned)(x - g.act_lo[0]) < (unsigned)(g.act_hi[0] - g.act_lo[0]) &&
-           (unsigned)(y - g.act_lo[1]) < (unsigned)(g.act_hi[1] - g.act_lo[1]) &&
-           (unsigned)(z - g.act_lo[2]) < (unsigned)(g.act_hi[2] - g.act_lo[2]);
+    if (L::D == 2) return x < g.n[0] && (unsigned)(y - g.act0) < (unsigned)(g.act1 - g.act0);
+    return x < g.n[0] && y < g.n[1] && (unsigned)(z - g.act0) < (unsigned)(g.act1 - g.act0);
 }
 
 __device__ __forceinline__ float  rint_t(float v) { return rintf(v); }
@@ -142,21 +142,40 @@ __device__ __forceinline__ double dist_t(double v) { return sqrt(v); }
 
 // Population i of cell (x, y, z) after streaming: the value the neighbour x - e_i stored
 // in the previous step, or, when x - e_i lies beyond a wall, the value this cell stored in
-// the opposite direction (halfway bounce-back, Eq. 6).
-// Beyond an open face the source is clamped onto the face (zero gradient); through an
-// inlet or the outlet face the population is unknown (returned as 0, `from_inlet` or
-// `from_outlet` set) and is filled in by inflow_nebb or outlet_nebb once all are pulled. A
-// wall takes precedence over the inlet and outlet faces, these over open faces.
+// the opposite direction (halfway bounce-back, Eq. 6). Periodic and wall faces only.
 template <class L, typename S>
 __device__ __forceinline__ typename Store<S>::T
 pull_one(const S *__restrict__ fin, const Geom &g, int x, int y, int z, long long cell, int i,
-         float2 sc, bool &from_inlet, bool &from_outlet) {
+         float2 sc) {
+    int s[3] = {x - L::ex(i), y - L::ey(i), z - L::ez(i)};
+    bool bounce = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (s[a] < 0 || s[a] >= g.n[a]) {
+            if (g.periodic[a]) s[a] += (s[a] < 0) ? g.n[a] : -g.n[a];
+            else bounce = true;
+        }
+    }
+    if (bounce) return Store<S>::ld(fin, (long long)opp<L>(i) * g.ncell + cell, sc);
+    long long src = (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2]);
+    return Store<S>::ld(fin, (long long)i * g.ncell + src, sc);
+}
+
+// The same for every face kind: beyond an open face the source is clamped onto the face
+// (zero gradient); beyond the inlet or the outlet face the population is unknown (returned
+// as 0, `from_inlet` or `from_outlet` set) and is filled in by inflow_nebb or outlet_nebb
+// once all are pulled. A wall takes precedence over the inlet and outlet faces, these over
+// open faces.
+template <class L, typename S>
+__device__ __forceinline__ typename Store<S>::T
+pull_one_faces(const S *__restrict__ fin, const Geom &g, int x, int y, int z, long long cell, int i,
+               float2 sc, bool &from_inlet, bool &from_outlet) {
     int s[3] = {x - L::ex(i), y - L::ey(i), z - L::ez(i)};
     bool bounce = false, inflow = false, outflow = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (s[a] < 0 || s[a] >= g.n[a]) {
-            const int kind = (s[a] < 0) ? g.face_lo[a] : g.face_hi[a];
+            const int kind = face_kind(g, a, s[a] < 0 ? 0 : 1);
             if (kind == FACE_PERIODIC) s[a] += (s[a] < 0) ? g.n[a] : -g.n[a];
             else if (kind == FACE_WALL) bounce = true;
             else if (kind == FACE_OPEN) s[a] = (s[a] < 0) ? 0 : g.n[a] - 1;
@@ -182,7 +201,7 @@ __device__ __forceinline__ void pull_all(const S *__restrict__ fin, const Geom &
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
         bool in = false, out = false;
-        df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc, in, out);
+        df[i] = pull_one_faces<L, S>(fin, g, x, y, z, cell, i, ph.sc, in, out);
         if (in) fill |= 1u << i;
         if (out) fillo |= 1u << i;
     }
@@ -275,7 +294,7 @@ __device__ __forceinline__ long long src_index(const NbrIdx &nb, const int i, co
 template <class L, typename S, bool RAW = false>
 __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g, int x, int y, int z,
                                        long long cell, bool interior, bool active, float2 sc,
-                                       typename Store<S>::T *df, const PhysT<typename Store<S>::T> &ph) {
+                                       typename Store<S>::T *df) {
     constexpr int Q = L::Q;
     using T = typename Store<S>::T;
     const long long N = g.ncell;
@@ -295,44 +314,31 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
         return;
     }
     // source x - e: from the -1 neighbour when e = +1 (m), from the +1 neighbour when e = -1 (p);
-    // per face its kind: wrap (periodic), wall flag, offset 0 (open: clamped onto the face),
-    // inflow flag
+    // periodic and wall faces only (contexts with open, inlet or outlet faces step with
+    // k_collide_faces)
     long long oxm = -1, oxp = 1, oym = -sy, oyp = sy, ozm = -sz, ozp = sz;
-    unsigned wall_m = 0u, in_m = 0u, out_m = 0u;      // bits 0..5: faces xm xp ym yp zm zp
-    unsigned fill = 0u, fillo = 0u;       // directions coming in through the inlet, the outlet
-    auto face = [&](const int kind, long long &off, const long long wrap, const unsigned bit) {
-        if (kind == FACE_PERIODIC) off = wrap;
-        else if (kind == FACE_WALL) wall_m |= bit;
-        else if (kind == FACE_OPEN) off = 0;
-        else if (kind == FACE_INFLOW) in_m |= bit;
-        else out_m |= bit;
-    };
-    if (x == 0) face(g.face_lo[0], oxm, g.n[0] - 1, 1u);
-    if (x == g.n[0] - 1) face(g.face_hi[0], oxp, -(long long)(g.n[0] - 1), 2u);
-    if (y == 0) face(g.face_lo[1], oym, (long long)(g.n[1] - 1) * sy, 4u);
-    if (y == g.n[1] - 1) face(g.face_hi[1], oyp, -(long long)(g.n[1] - 1) * sy, 8u);
+    bool wxm = false, wxp = false, wym = false, wyp = false, wzm = false, wzp = false;
+    if (x == 0) { if (g.periodic[0]) oxm = g.n[0] - 1; else wxm = true; }
+    if (x == g.n[0] - 1) { if (g.periodic[0]) oxp = -(long long)(g.n[0] - 1); else wxp = true; }
+    if (y == 0) { if (g.periodic[1]) oym = (long long)(g.n[1] - 1) * sy; else wym = true; }
+    if (y == g.n[1] - 1) { if (g.periodic[1]) oyp = -(long long)(g.n[1] - 1) * sy; else wyp = true; }
     if (L::D == 3) {
-        if (z == 0) face(g.face_lo[2], ozm, (long long)(g.n[2] - 1) * sz, 16u);
-        if (z == g.n[2] - 1) face(g.face_hi[2], ozp, -(long long)(g.n[2] - 1) * sz, 32u);
+        if (z == 0) { if (g.periodic[2]) ozm = (long long)(g.n[2] - 1) * sz; else wzm = true; }
+        if (z == g.n[2] - 1) { if (g.periodic[2]) ozp = -(long long)(g.n[2] - 1) * sz; else wzp = true; }
     }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         long long off = 0;
-        unsigned dm = 0u;        // the faces the source of direction i lies beyond (if any)
-        if (L::ex(i) == 1) { off += oxm; dm |= 1u; }
-        if (L::ex(i) == -1) { off += oxp; dm |= 2u; }
-        if (L::ey(i) == 1) { off += oym; dm |= 4u; }
-        if (L::ey(i) == -1) { off += oyp; dm |= 8u; }
-        if (L::ez(i) == 1) { off += ozm; dm |= 16u; }
-        if (L::ez(i) == -1) { off += ozp; dm |= 32u; }
-        const bool wall = (wall_m & dm) != 0u;
+        bool wall = false;
+        if (L::ex(i) == 1) { off += oxm; wall |= wxm; }
+        if (L::ex(i) == -1) { off += oxp; wall |= wxp; }
+        if (L::ey(i) == 1) { off += oym; wall |= wym; }
+        if (L::ey(i) == -1) { off += oyp; wall |= wyp; }
+        if (L::ez(i) == 1) { off += ozm; wall |= wzm; }
+        if (L::ez(i) == -1) { off += ozp; wall |= wzp; }
         const long long idx = wall ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
-        if (!wall && (in_m & dm)) { df[i] = (T)0; fill |= 1u << i; }      // filled in below
-        else if (!wall && (out_m & dm)) { df[i] = (T)0; fillo |= 1u << i; }
-        else df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
+        df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
     }
-    if (fill) inflow_nebb<L, RAW, T>(df, ph, sc, fill);
-    if (fillo) outlet_nebb<L, RAW, T>(df, ph, sc, fillo);
 }
 
 // ------------------------------------------------------------------- candidate records
@@ -550,7 +556,7 @@ template <class L, typename T> constexpr int psc_min_blocks() {
 // shuffles; partial sums meet in shared memory and are added in a fixed order, one FP64
 // atomic per particle and component per tile. Tiles with more candidates than the block
 // holds take the same path chunk by chunk over all particles (exact, slow, rare).
-template <class L, typename S, int PSC>
+template <class L, typename S, int PSC, bool FACES = false>
 __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restrict__ fin, S *__restrict__ fout,
                                          const Geom &g, const PhysT<typename Store<S>::T> &ph, const Tiles &tl,
                                          const Parts &pd, int *flags, typename Store<S>::T *srec,
@@ -562,21 +568,23 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
     const int cap = tl.cap;
     T *part = srec + (size_t)cap * RW;                     // [kWarps][cap][NC] warp partials
 
-    const int cnt = tl.count[tile];
-    if (cnt == 0) return;                                   // plain-fluid tile: k_fluid_pair does it
+    // (without particles the tile lists may not exist: only the faces kernel gets here then)
+    const int cnt = (FACES && pd.n == 0) ? 0 : tl.count[tile];
+    if (cnt == 0 && !FACES) return;                        // plain-fluid tile: k_fluid_pair does it
     const unsigned txy = tile / (unsigned)g.nt[0];          // 32-bit: tiles < 2^31 (host check)
     const int tx = (int)(tile - txy * (unsigned)g.nt[0]);
     const int ty = (int)(txy % (unsigned)g.nt[1]);
     const int tz = (int)(txy / (unsigned)g.nt[1]);
     const bool ovf = cnt > cap;
     const int nchunk = ovf ? (pd.n + cap - 1) / cap : 1;
-    const T *recs = reinterpret_cast<const T *>(tl.blocks) + (size_t)tile * block_elems<T>(cap) + head_elems<T>();
+    const T *recs = (FACES && cnt == 0) ? nullptr
+                  : reinterpret_cast<const T *>(tl.blocks) + (size_t)tile * block_elems<T>(cap) + head_elems<T>();
 
     const int tid = threadIdx.x + L::TX * (threadIdx.y + L::TY * threadIdx.z);
     const int lane = tid & 31, warp = tid >> 5;
     const int x0 = tx * L::TX, y0 = ty * L::TY, z0 = tz * L::TZ;
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y, z = z0 + threadIdx.z;
-    const bool active = cell_active(g, x, y, z);
+    const bool active = cell_active<L>(g, x, y, z);
     const long long cell = x + (long long)g.n[0] * (y + (long long)g.n[1] * z);
     const long long N = g.ncell;
 
@@ -602,7 +610,12 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
         for (int i = 0; i < Q; ++i)
             df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
     } else if (active) {
-        pull_all<L, S>(fin, g, x, y, z, cell, ph, df);
+        if (FACES) {
+            pull_all<L, S>(fin, g, x, y, z, cell, ph, df);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) df[i] = pull_one<L, S>(fin, g, x, y, z, cell, i, ph.sc);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) df[i] = (T)0;
@@ -889,6 +902,23 @@ k_collide_overflow(const S *__restrict__ fin, S *__restrict__ fout, Geom g, Phys
     }
 }
 
+// Contexts with an open, inlet or outlet face: every tile, with or without candidates, by
+// the single-cell path whose pull classifies each face (persistent blocks over the tiles).
+template <class L, typename S, int PSC>
+__global__ void __launch_bounds__(kThreads, 1)
+k_collide_faces(const S *__restrict__ fin, S *__restrict__ fout, Geom g, PhysT<typename Store<S>::T> ph,
+                Tiles tl, Parts pd, int *flags) {
+    using T = typename Store<S>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_mask[kWarps];
+    const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
+    for (long long it = blockIdx.x; it < ntiles; it += gridDim.x) {
+        psc_tile<L, S, PSC, true>((unsigned)it, fin, fout, g, ph, tl, pd, flags,
+                                  reinterpret_cast<T *>(smem), s_mask);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- gather / set kernels
 template <class L, typename S>
 __global__ void k_gather(const S *__restrict__ fin, Geom g, PhysT<typename Store<S>::T> ph,
@@ -932,7 +962,7 @@ __global__ void k_set(const double *__restrict__ f, S *__restrict__ fout, Geom g
         for (int a = 0; a < 3; ++a) {
             d[a] = xc[a] + e[a];
             if (d[a] < 0 || d[a] >= g.n[a]) {
-                const int kind = (d[a] < 0) ? g.face_lo[a] : g.face_hi[a];
+                const int kind = face_kind(g, a, d[a] < 0 ? 0 : 1);
                 if (kind == FACE_PERIODIC) d[a] += (d[a] < 0) ? g.n[a] : -g.n[a];
                 else if (kind == FACE_WALL) wall = true;
                 else leaves = true;
@@ -1007,6 +1037,20 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
     const long long ntiles = (long long)g.nt[0] * g.nt[1] * g.nt[2];
     dim3 block(L::TX, L::TY, L::TZ);
     const PhysT<T> pt = make_phys<T>(ph, L::Q);
+    bool faces = false;
+    for (int a = 0; a < 3; ++a) faces |= face_kind(g, a, 0) >= FACE_OPEN || face_kind(g, a, 1) >= FACE_OPEN;
+    if (faces) {
+        auto fk = k_collide_faces<L, S, PSC>;
+        if (osmem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+            if (e != cudaSuccess) return e;
+        }
+        unsigned nbf = 0;
+        cudaError_t e = persistent_blocks(fk, osmem, ntiles, nbf, kThreads);
+        if (e != cudaSuccess) return e;
+        fk<<<nbf, block, osmem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+        return cudaGetLastError();
+    }
     const bool hasF = ph.body_force[0] != 0.0 || ph.body_force[1] != 0.0 || ph.body_force[2] != 0.0;
     auto fkern = hasF ? k_fluid_pair<L, S, true> : k_fluid_pair<L, S, false>;
     const dim3 pblock(32, kPWarps);

@@ -139,8 +139,8 @@ __device__ __forceinline__ void pull_pair(const S *__restrict__ fin, const Geom 
         }
         return;
     }
-    pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da, ph);
-    pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db, ph);
+    pull_q<L, S, SC>(fin, g, xA, yA, zA, cellA, false, actA, ph.sc, da);
+    pull_q<L, S, SC>(fin, g, xB, yB, zB, cellB, false, actB, ph.sc, db);
 }
 
 // Store of velocity i at the lane's two cells (values already scaled for 16-bit storage).
@@ -190,8 +190,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     const PairCells<L> pc(lane, warp);
     const int xA = x0 + pc.xA, xB = x0 + pc.xB;
     const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
-    const bool actA = cell_active(g, xA, yA, zA);
-    const bool actB = cell_active(g, xB, yB, zB);
+    const bool actA = cell_active<L>(g, xA, yA, zA);
+    const bool actB = cell_active<L>(g, xB, yB, zB);
     const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
     const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
     const long long N = g.ncell;
@@ -452,8 +452,8 @@ __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__
     const PairCells<L> pc(lane, warp);
     const int xA = x0 + pc.xA, xB = x0 + pc.xB;
     const int yA = y0 + pc.yA, yB = y0 + pc.yB, zA = z0 + pc.zA, zB = z0 + pc.zB;
-    const bool actA = cell_active(g, xA, yA, zA);
-    const bool actB = cell_active(g, xB, yB, zB);
+    const bool actA = cell_active<L>(g, xA, yA, zA);
+    const bool actB = cell_active<L>(g, xB, yB, zB);
     const long long cellA = xA + (long long)g.n[0] * (yA + (long long)g.n[1] * zA);
     const long long cellB = xB + (long long)g.n[0] * (yB + (long long)g.n[1] * zB);
     const bool interior = x0 >= 1 && x0 + L::TX < g.n[0] && y0 >= 1 && y0 + L::TY < g.n[1] &&
