@@ -153,6 +153,18 @@ lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F);
  * sum eps = 1), where the one-sided derivative inside the unclamped region is used.
  * Memory: about (T / checkpoint_every + checkpoint_every + 2) population buffers.
  * J, dJdX and dJdF go to device memory when on_device, else host (synchronises). */
+/* The two halves of lbm_adjoint_drag, for callers that want J now and the gradient only
+ * later, if at all (an autograd forward and backward). lbm_adjoint_forward runs the T
+ * forward steps with the checkpoints and returns J and a token; the checkpoints stay in
+ * the context's adjoint workspace. lbm_adjoint_backward(token) runs the reverse sweep over
+ * them and returns dJdX and dJdF; it may be called again with the same token. It fails
+ * with LBM_ERR_ARG when a later lbm_adjoint_forward took the workspace (another token) or
+ * when the particles or the body force changed since the forward (lbm_set_particles,
+ * lbm_set_body_force, lbm_load_state, dem_step); lbm_step in between does not matter. The
+ * requirements and memory are those of lbm_adjoint_drag. */
+lbm_status lbm_adjoint_forward(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J, long long *token,
+                               int on_device);
+lbm_status lbm_adjoint_backward(lbm_ctx *ctx, long long token, double *dJdX, double *dJdF, int on_device);
 lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J, double *dJdX,
                             double *dJdF, int on_device);
 

@@ -105,6 +105,8 @@ def lib():
         "lbm_kernel_timing": ([vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
         "lbm_set_body_force": ([vp, vp], C.c_int),
         "lbm_adjoint_drag": ([vp, C.c_int, C.c_int, vp, vp, vp, C.c_int], C.c_int),
+        "lbm_adjoint_forward": ([vp, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
+        "lbm_adjoint_backward": ([vp, C.c_longlong, vp, vp, C.c_int], C.c_int),
     }
     optional = {
         "dem_create": ([C.POINTER(DemParams), vp, C.POINTER(C.c_void_p)], C.c_int),
@@ -446,10 +448,32 @@ def lbm_adjoint_drag(ctx, nsteps, checkpoint_every):
     return float(J[0]), dX[: ctx.np].copy(), dF
 
 
+def lbm_adjoint_forward(ctx, nsteps, checkpoint_every):
+    """(J, token): the forward half of lbm_adjoint_drag (see the header)."""
+    J = np.zeros(1)
+    tok = C.c_longlong()
+    _check(ctx, lib().lbm_adjoint_forward(ctx.handle, int(nsteps), int(checkpoint_every),
+                                          J.ctypes.data_as(C.c_void_p), C.byref(tok), 0))
+    return float(J[0]), tok.value
+
+
+def lbm_adjoint_backward(ctx, token):
+    """(dJ/dX (n, 3), dJ/dF (3,)): the reverse sweep over the checkpoints of the forward
+    half that returned ``token``."""
+    dX = np.zeros((max(ctx.np, 1), 3))
+    dF = np.zeros(3)
+    _check(ctx, lib().lbm_adjoint_backward(ctx.handle, C.c_longlong(int(token)), dX.ctypes.data_as(C.c_void_p),
+                                           dF.ctypes.data_as(C.c_void_p), 0))
+    return dX[: ctx.np].copy(), dF
+
+
 def psc_drag(ctx, f0, X, radius, F, nsteps, checkpoint_every):
-    """Differentiable time-averaged drag: a torch scalar J(X, F) whose backward pass uses the
-    library's adjoint. ``ctx`` is a context whose particles are static; ``f0`` (numpy,
-    pre-collision populations) is the initial state of every evaluation."""
+    """Differentiable time-averaged drag: a torch scalar J(X, F). The forward pass runs the
+    library's forward half (T steps with checkpoints); the backward pass, only when a
+    gradient is asked for, runs the reverse sweep over those checkpoints. ``ctx`` is a
+    context whose particles are static; ``f0`` (numpy, pre-collision populations) is the
+    initial state of every evaluation. Each evaluation takes the context's adjoint
+    workspace, so the backward of an earlier evaluation after a later forward raises."""
     import torch
 
     class _PscDrag(torch.autograd.Function):
@@ -460,15 +484,16 @@ def psc_drag(ctx, f0, X, radius, F, nsteps, checkpoint_every):
             Xn = Xt.detach().cpu().numpy()
             z = np.zeros_like(Xn)
             lbm_set_particles(ctx, Xn, z, z, np.asarray(radius, dtype=np.float64))
-            J, dX, dF = lbm_adjoint_drag(ctx, nsteps, checkpoint_every)
-            actx.save_for_backward(torch.as_tensor(dX, dtype=Xt.dtype, device=Xt.device),
-                                   torch.as_tensor(dF, dtype=Ft.dtype, device=Ft.device))
+            J, token = lbm_adjoint_forward(ctx, nsteps, checkpoint_every)
+            actx.token = token
+            actx.meta = (Xt.dtype, Xt.device, Ft.dtype, Ft.device)
             return torch.as_tensor(J, dtype=Xt.dtype, device=Xt.device)
 
         @staticmethod
         def backward(actx, g):
-            dX, dF = actx.saved_tensors
-            return g * dX, g * dF
+            dX, dF = lbm_adjoint_backward(ctx, actx.token)
+            xd, xdev, fd, fdev = actx.meta
+            return (g * torch.as_tensor(dX, dtype=xd, device=xdev), g * torch.as_tensor(dF, dtype=fd, device=fdev))
 
     return _PscDrag.apply(X, F)
 

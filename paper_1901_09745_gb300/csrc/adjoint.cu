@@ -304,8 +304,46 @@ using namespace psc;
         if (st_ != LBM_OK) { status = st_; goto done; }         \
     } while (0)
 
-extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J,
-                                       double *dJdX, double *dJdF, int on_device) {
+// Workspace of the adjoint, kept by the context between calls: checkpoints [nseg], segment
+// states [K], two adjoint fields, gradients + J, scratch forces and torques, per-block
+// partials of dJ/dF.
+struct AdjSpace {
+    char *ckpt, *seg, *lam[2];
+    double *dJX, *dJF, *dJ, *sF, *sT, *dFpart;
+    size_t pop, popa, v3, need;
+    long long nblk;
+    int nseg;
+};
+
+static AdjSpace adj_layout(const lbm_ctx *ctx, int nsteps, int K) {
+    AdjSpace a;
+    const int n = ctx->np;
+    a.nseg = (nsteps + K - 1) / K;
+    a.pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
+    a.v3 = (size_t)(n > 0 ? n : 1) * 3 * sizeof(double);
+    const size_t v3a = (a.v3 + 255) & ~(size_t)255;
+    a.popa = (a.pop + 255) & ~(size_t)255;      // buffer stride, 256-byte aligned
+    a.nblk = (long long)ctx->g.nt[0] * ctx->g.nt[1] * ctx->g.nt[2];
+    const size_t fpa = ((size_t)a.nblk * 3 * sizeof(double) + 255) & ~(size_t)255;
+    a.need = a.popa * ((size_t)a.nseg + (size_t)K + 2) + 3 * v3a + 256 + fpa;
+    char *base = (char *)ctx->adj;
+    a.ckpt = base;
+    a.seg = a.ckpt + a.popa * (size_t)a.nseg;
+    a.lam[0] = a.seg + a.popa * (size_t)K;
+    a.lam[1] = a.seg + a.popa * (size_t)(K + 1);
+    a.dJX = (double *)(a.lam[1] + a.popa);
+    a.dJF = a.dJX + 3 * (size_t)(n > 0 ? n : 1);
+    a.dJ = a.dJF + 3;
+    a.sF = (double *)((char *)a.dJX + v3a + 256);
+    a.sT = (double *)((char *)a.sF + v3a);
+    a.dFpart = (double *)((char *)a.sT + v3a);
+    return a;
+}
+
+// Forward half: T steps from the context's state with a checkpoint every K, J summed on the
+// device. Leaves the checkpoints and the tile lists for lbm_adjoint_backward.
+extern "C" lbm_status lbm_adjoint_forward(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J,
+                                          long long *token, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 1 || checkpoint_every < 1) { ctx_error(ctx, "nsteps and checkpoint_every must be >= 1"); return LBM_ERR_ARG; }
     if (ctx->p.storage != LBM_F32 && ctx->p.storage != LBM_F64) {
@@ -320,14 +358,11 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
         }
     const int n = ctx->np;
     const int K = checkpoint_every;
-    const int nseg = (nsteps + K - 1) / K;
-    const size_t pop = (size_t)ctx->g.ncell * ctx->q * ctx->elem;
-    const size_t v3 = (size_t)(n > 0 ? n : 1) * 3 * sizeof(double);
     lbm_status status = LBM_OK;
-    Parts scratch_parts;
-    Tiles tl;
+    ctx->adj_ready = 0;
     // static, non-moving particles only (u_s = 0)
     if (n > 0) {
+        const size_t v3 = (size_t)n * 3 * sizeof(double);
         double *h = (double *)malloc(2 * v3);
         if (!h) return LBM_ERR_OOM;
         cudaError_t e = cudaMemcpyAsync(h, ctx->dU, v3, cudaMemcpyDeviceToHost, ctx->stream);
@@ -339,42 +374,28 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
         if (e != cudaSuccess) return ctx_cuda(ctx, e, "read particle velocities");
         if (moving) { ctx_error(ctx, "the adjoint is for static particles (U = Omega = 0)"); return LBM_ERR_UNSUPPORTED; }
     }
-    // one workspace, kept by the context between calls: checkpoints [nseg], segment states
-    // [K], two adjoint fields, gradients + J, scratch forces and torques
-    const size_t v3a = (v3 + 255) & ~(size_t)255;
-    const size_t popa = (pop + 255) & ~(size_t)255;      // buffer stride, 256-byte aligned
-    const long long nblk = (long long)ctx->g.nt[0] * ctx->g.nt[1] * ctx->g.nt[2];
-    const size_t fpa = ((size_t)nblk * 3 * sizeof(double) + 255) & ~(size_t)255;
-    const size_t need = popa * ((size_t)nseg + (size_t)K + 2) + 3 * v3a + 256 + fpa;
-    if (ctx->adj_cap < need) {
-        if (ctx->adj) cudaFree(ctx->adj);
-        ctx->adj = NULL;
-        ctx->adj_cap = 0;
-        cudaError_t e = cudaMalloc(&ctx->adj, need);
-        if (e != cudaSuccess) { ctx->adj = NULL; return ctx_cuda(ctx, e, "cudaMalloc(adjoint workspace)"); }
-        ctx->adj_cap = need;
-    }
-    char *ckpt = (char *)ctx->adj;
-    char *seg = ckpt + popa * (size_t)nseg;
-    char *lam[2] = {seg + popa * (size_t)K, seg + popa * (size_t)(K + 1)};
-    double *dacc = (double *)(lam[1] + popa);
-    double *sF = (double *)((char *)dacc + v3a + 256);
-    double *sT = (double *)((char *)sF + v3a);
-    double *dFpart = (double *)((char *)sT + v3a);       // [blocks][3] partials of dJ/dF
-    ACK(cudaMemsetAsync(dacc, 0, v3 + 4 * sizeof(double), ctx->stream), "memset gradients");
-    ACK(cudaMemsetAsync(dFpart, 0, fpa, ctx->stream), "memset gradient partials");
-    ACK(cudaMemsetAsync(lam[0], 0, pop, ctx->stream), "memset adjoint");
     {
-        double *dJX = dacc, *dJF = dacc + 3 * (size_t)(n > 0 ? n : 1), *dJ = dJF + 3;
+        const size_t need = adj_layout(ctx, nsteps, K).need;
+        if (ctx->adj_cap < need) {
+            if (ctx->adj) cudaFree(ctx->adj);
+            ctx->adj = NULL;
+            ctx->adj_cap = 0;
+            cudaError_t e = cudaMalloc(&ctx->adj, need);
+            if (e != cudaSuccess) { ctx->adj = NULL; return ctx_cuda(ctx, e, "cudaMalloc(adjoint workspace)"); }
+            ctx->adj_cap = need;
+        }
+    }
+    {
+        const AdjSpace w = adj_layout(ctx, nsteps, K);
+        ACK(cudaMemsetAsync(w.dJX, 0, w.v3 + 4 * sizeof(double), ctx->stream), "memset gradients");
         const double invT = 1.0 / nsteps;
-        // ---- forward rollout with checkpoints, accumulating J
         for (int t = 0; t < nsteps; ++t) {
-            if (t % K == 0) ACK(cudaMemcpyAsync(ckpt + popa * (size_t)(t / K), ctx->f[ctx->cur], pop,
+            if (t % K == 0) ACK(cudaMemcpyAsync(w.ckpt + w.popa * (size_t)(t / K), ctx->f[ctx->cur], w.pop,
                                                 cudaMemcpyDeviceToDevice, ctx->stream), "checkpoint");
             lbm_status st = ctx_step_once(ctx);
             if (st != LBM_OK) { status = st; goto done; }
             if (n > 0) {
-                k_sum_fx<<<1, 256, 0, ctx->stream>>>(ctx->dF, n, invT, dJ);
+                k_sum_fx<<<1, 256, 0, ctx->stream>>>(ctx->dF, n, invT, w.dJ);
                 ACK(cudaGetLastError(), "drag sum");
             }
         }
@@ -388,40 +409,89 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
                 goto done;
             }
         }
+        if (J) ACK(cudaMemcpyAsync(J, w.dJ, sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   ctx->stream), "copy J");
+        ACK(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+done:
+    cudaStreamSynchronize(ctx->stream);
+    if (status == LBM_OK) status = ctx_check_flags(ctx);
+    if (status == LBM_OK) {
+        ctx->adj_T = nsteps;
+        ctx->adj_K = K;
+        ctx->adj_mods = ctx->mods;
+        ctx->adj_ready = 1;
+        ctx->adj_token += 1;
+        if (token) *token = ctx->adj_token;
+    }
+    return status;
+}
+
+// Backward half: the reverse sweep over the checkpoints of the last lbm_adjoint_forward.
+extern "C" lbm_status lbm_adjoint_backward(lbm_ctx *ctx, long long token, double *dJdX, double *dJdF,
+                                           int on_device) {
+    if (!ctx) return LBM_ERR_ARG;
+    if (!ctx->adj_ready || token != ctx->adj_token) {
+        ctx_error(ctx, "no lbm_adjoint_forward with this token holds the adjoint workspace");
+        return LBM_ERR_ARG;
+    }
+    if (ctx->mods != ctx->adj_mods) {
+        ctx_error(ctx, "the particles or the body force changed since lbm_adjoint_forward");
+        return LBM_ERR_ARG;
+    }
+    const int n = ctx->np;
+    const int nsteps = ctx->adj_T, K = ctx->adj_K;
+    lbm_status status = LBM_OK;
+    const AdjSpace w = adj_layout(ctx, nsteps, K);
+    Tiles tl;
+    Parts scratch_parts;
+    ACK(cudaMemsetAsync(w.dJX, 0, w.v3 + 3 * sizeof(double), ctx->stream), "memset gradients");
+    ACK(cudaMemsetAsync(w.dFpart, 0, (size_t)w.nblk * 3 * sizeof(double), ctx->stream), "memset gradient partials");
+    ACK(cudaMemsetAsync(w.lam[0], 0, w.pop, ctx->stream), "memset adjoint");
+    {
+        const double invT = 1.0 / nsteps;
         tl.count = ctx->tile_count; tl.list = ctx->tile_list; tl.cap = ctx->p.tile_cap;
         tl.stats = ctx->tile_stats; tl.blocks = ctx->tile_blocks; tl.order = ctx->tile_order;
         scratch_parts = ctx_parts(ctx);
-        scratch_parts.F = sF;
-        scratch_parts.T = sT;
-        // ---- reverse sweep, segment by segment
+        scratch_parts.F = w.sF;
+        scratch_parts.T = w.sT;
+        // segment by segment: restore the checkpoint, re-run the segment storing its states,
+        // walk it back
         int cur = 0;
-        for (int sidx = nseg - 1; sidx >= 0; --sidx) {
+        for (int sidx = w.nseg - 1; sidx >= 0; --sidx) {
             const int t0 = sidx * K, t1 = (t0 + K < nsteps) ? t0 + K : nsteps;
-            ACK(cudaMemcpyAsync(seg, ckpt + popa * (size_t)sidx, pop, cudaMemcpyDeviceToDevice, ctx->stream),
+            ACK(cudaMemcpyAsync(w.seg, w.ckpt + w.popa * (size_t)sidx, w.pop, cudaMemcpyDeviceToDevice, ctx->stream),
                 "restore checkpoint");
             for (int t = t0 + 1; t < t1; ++t) {
-                ACK(launch_collide_stream(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - 1 - t0),
-                                          seg + popa * (size_t)(t - t0), ctx->g, ctx->ph, tl, scratch_parts,
+                ACK(launch_collide_stream(ctx->p.storage, ctx->q, w.seg + w.popa * (size_t)(t - 1 - t0),
+                                          w.seg + w.popa * (size_t)(t - t0), ctx->g, ctx->ph, tl, scratch_parts,
                                           ctx->flags, ctx->stream, &ctx->ov),
                     "segment recompute");
             }
             for (int t = t1 - 1; t >= t0; --t) {
-                ACK(launch_adjoint(ctx->p.storage, ctx->q, seg + popa * (size_t)(t - t0), lam[cur], lam[cur ^ 1],
-                                   ctx->g, ctx->ph, tl, ctx_parts(ctx), invT, dJX, dFpart, ctx->stream),
+                ACK(launch_adjoint(ctx->p.storage, ctx->q, w.seg + w.popa * (size_t)(t - t0), w.lam[cur], w.lam[cur ^ 1],
+                                   ctx->g, ctx->ph, tl, ctx_parts(ctx), invT, w.dJX, w.dFpart, ctx->stream),
                     "adjoint kernel");
                 cur ^= 1;
             }
         }
-        k_sum_parts<<<1, 256, 0, ctx->stream>>>(dFpart, nblk, dJF);
+        k_sum_parts<<<1, 256, 0, ctx->stream>>>(w.dFpart, w.nblk, w.dJF);
         ACK(cudaGetLastError(), "dJ/dF sum");
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        if (J) ACK(cudaMemcpyAsync(J, dJ, sizeof(double), kind, ctx->stream), "copy J");
-        if (dJdF) ACK(cudaMemcpyAsync(dJdF, dJF, 3 * sizeof(double), kind, ctx->stream), "copy dJ/dF");
-        if (dJdX && n > 0) ACK(cudaMemcpyAsync(dJdX, dJX, (size_t)n * 3 * sizeof(double), kind, ctx->stream), "copy dJ/dX");
+        if (dJdF) ACK(cudaMemcpyAsync(dJdF, w.dJF, 3 * sizeof(double), kind, ctx->stream), "copy dJ/dF");
+        if (dJdX && n > 0) ACK(cudaMemcpyAsync(dJdX, w.dJX, (size_t)n * 3 * sizeof(double), kind, ctx->stream), "copy dJ/dX");
         ACK(cudaStreamSynchronize(ctx->stream), "sync");
     }
 done:
     cudaStreamSynchronize(ctx->stream);
     if (status == LBM_OK) status = ctx_check_flags(ctx);
     return status;
+}
+
+extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J,
+                                       double *dJdX, double *dJdF, int on_device) {
+    long long token = 0;
+    lbm_status st = lbm_adjoint_forward(ctx, nsteps, checkpoint_every, J, &token, on_device);
+    if (st != LBM_OK) return st;
+    return lbm_adjoint_backward(ctx, token, dJdX, dJdF, on_device);
 }

@@ -359,6 +359,7 @@ static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
 extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
                                         const double *Omega, const double *radius, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
+    ctx->mods += 1;
     if (n < 0 || n > (1 << 24)) { ctx_error(ctx, "particle count must be in [0, 2^24], got %d", n); return LBM_ERR_ARG; }
     if (n > 0 && (!X || !U || !Omega || !radius)) { ctx_error(ctx, "particle arrays must not be NULL"); return LBM_ERR_ARG; }
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -634,6 +635,7 @@ extern "C" lbm_status lbm_save_state(lbm_ctx *ctx, void *buf, size_t cap, size_t
 
 extern "C" lbm_status lbm_load_state(lbm_ctx *ctx, const void *buf, size_t size) {
     if (!ctx || !buf) return LBM_ERR_ARG;
+    ctx->mods += 1;
     StateHeader h;
     if (size < sizeof(h)) { ctx_error(ctx, "state buffer too small"); return LBM_ERR_ARG; }
     memcpy(&h, buf, sizeof(h));
@@ -669,6 +671,7 @@ extern "C" lbm_status lbm_set_body_force(lbm_ctx *ctx, const double *F) {
         if (!isfinite(F[a])) { ctx_error(ctx, "body force must be finite"); return LBM_ERR_ARG; }
     for (int a = 0; a < 3; ++a) { ctx->p.body_force[a] = F[a]; ctx->ph.body_force[a] = F[a]; }
     ctx->gen += 1;
+    ctx->mods += 1;
     return LBM_OK;
 }
 

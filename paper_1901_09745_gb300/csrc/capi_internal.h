@@ -39,6 +39,9 @@ struct lbm_ctx {
 
     void *adj;                 // adjoint workspace (checkpoints, segment states, adjoint
     size_t adj_cap;            // fields, gradients), grown on demand, kept until destroy
+    int adj_ready, adj_T, adj_K;   // the last lbm_adjoint_forward: its steps and interval,
+    long long adj_token, adj_mods; // its token, and `mods` when it ran
+    long long mods;            // bumped by every change of the particles or the body force
 
     long long steps;
     long long launches;        // kernels this context has launched

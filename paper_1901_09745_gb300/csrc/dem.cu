@@ -13,7 +13,8 @@
 //                  pair not on it was farther apart than r_i + r_j + skin at the build, and
 //                  neither particle has moved skin/2 since (a sub-step that sees one move
 //                  that far reports it), so it cannot touch.
-//   3. k_dem_substep (x substeps): one warp per particle, one lane per neighbour:
+//   3. k_dem_substep (x substeps): two lanes per particle, each taking every other
+//                  neighbour slot:
 //        contact detection in FP64 with IEEE-rounded operations only (no FMA), so both
 //        ends of a pair and a CPU reference agree bit for bit on delta_N;
 //        the contact law in FP32: JKR normal force (Eq. 26-27) with the contact radius
@@ -436,7 +437,8 @@ __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, doub
     else { *m = rho * (4.0 / 3.0) * kPi * r * r * r; *I = 0.4 * (*m) * r * r; }
 }
 
-constexpr int kLPP = 4;   // lanes per particle in the sub-step kernel
+constexpr int kLPP = 2;   // lanes per particle in the sub-step kernel (c2 coupled step: 1 lane
+                          // 182.9 us, 2 lanes 162.0, 4 lanes 170.2, 8 lanes 206.0)
 
 // One DEM sub-step. kLPP lanes share a particle and split its neighbour slots; their FP64
 // sums are combined with shuffles in a fixed order, then the first lane integrates.
@@ -474,8 +476,10 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             im = b.minv[2 * i];
             iI = b.minv[2 * i + 1];
         }
+        int jn = (sub < nn) ? nbr[i * kNB + sub] : 0;     // the lane's next neighbour, loaded ahead
         for (int s = sub; s < nn; s += kLPP) {
-            const int j = nbr[i * kNB + s];
+            const int j = jn;
+            if (s + kLPP < nn) jn = nbr[i * kNB + s + kLPP];
             float *hp = hist + ((size_t)i * kNB + s) * kH;
             // everything the pair may need, loaded at once (one round trip after j)
             const float4 pj = b.Xf[j];
@@ -582,11 +586,12 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         }
     }
     // contacts with the walls of the non-periodic axes (the fluid's halfway bounce-back
-    // planes at -1/2 and n - 1/2): lane `sub` takes axis `sub`; the nearer wall is a half-space
-    // of the same material at rest (R = r_i, m* = m_i). The overlap and the decision are
-    // formed in FP64 with IEEE-rounded operations, as for the pairs.
-    if (valid && sub < dim && !g.periodic[sub]) {
-        const int a = sub;
+    // planes at -1/2 and n - 1/2): lane `sub` takes axes sub, sub + kLPP, ...; the nearer wall
+    // is a half-space of the same material at rest (R = r_i, m* = m_i). The overlap and the
+    // decision are formed in FP64 with IEEE-rounded operations, as for the pairs.
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {       // unrolled: the per-axis arrays stay in registers
+        if (!valid || a % kLPP != sub || g.periodic[a]) continue;
         const double lo_plane = 0.5 * (double)(g.n[a] - 1);
         const bool lower = xi[a] < lo_plane;
         const double dist = lower ? __dadd_rn(xi[a], 0.5) : __dsub_rn((double)g.n[a] - 0.5, xi[a]);

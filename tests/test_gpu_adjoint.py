@@ -123,9 +123,39 @@ def test_autograd_function_backward(P):
     J = P.psc_drag(ctx, f0, X, case["r"], F, 10, 3)
     (2.0 * J).backward()
     Jr, dX, dF = _gpu_adjoint(P, case, f0, 10, 3)
-    assert float(J) == pytest.approx(Jr, rel=1e-14)
+    assert float(J.detach()) == pytest.approx(Jr, rel=1e-14)
     assert np.allclose(X.grad.numpy(), 2.0 * dX, rtol=1e-12, atol=0)
     assert np.allclose(F.grad.numpy(), 2.0 * dF, rtol=1e-12, atol=0)
+
+
+def test_forward_and_backward_halves(P):
+    """lbm_adjoint_forward + lbm_adjoint_backward give lbm_adjoint_drag's J and gradient;
+    the backward can run twice; a later forward or a change of the particles or the body
+    force makes the old token's backward fail instead of returning a stale gradient."""
+    case = _case(19)
+    f0 = perturbed_state(case, 35, amp=2e-3)
+    Jr, dXr, dFr = _gpu_adjoint(P, case, f0, 9, 4)
+    ctx = P.lbm_create(case["lattice"], *case["n"], bc=case["bc"], tau=case["tau"], body_force=case["body_force"],
+                       storage="f64")
+    P.lbm_set_populations(ctx, f0)
+    P.lbm_set_particles(ctx, case["X"], case["U"], case["Om"], case["r"])
+    J, tok = P.lbm_adjoint_forward(ctx, 9, 4)
+    assert J == pytest.approx(Jr, rel=1e-14)
+    assert P.lbm_get_info(ctx)["steps"] == 9
+    for _ in range(2):
+        dX, dF = P.lbm_adjoint_backward(ctx, tok)
+        assert np.allclose(dX, dXr, rtol=1e-13, atol=1e-18)
+        assert np.allclose(dF, dFr, rtol=1e-13, atol=1e-18)
+    P.lbm_step(ctx, 2)                       # stepping on does not touch the checkpoints
+    dX, _ = P.lbm_adjoint_backward(ctx, tok)
+    assert np.allclose(dX, dXr, rtol=1e-13, atol=1e-18)
+    _, tok2 = P.lbm_adjoint_forward(ctx, 3, 2)
+    with pytest.raises(P.LbmError):
+        P.lbm_adjoint_backward(ctx, tok)
+    P.lbm_set_body_force(ctx, case["body_force"])
+    with pytest.raises(P.LbmError):
+        P.lbm_adjoint_backward(ctx, tok2)
+    P.lbm_destroy(ctx)
 
 
 def test_c4_adjoint_against_gpu_finite_differences():
