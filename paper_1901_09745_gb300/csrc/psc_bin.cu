@@ -157,7 +157,7 @@ long long pack_block_bytes(int rec_double, int cap) {
 
 cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles &tl, const Parts &pd,
                         long long ntiles, cudaStream_t s) {
-    const unsigned blocks = (unsigned)((ntiles + kWarps - 1) / kWarps);
+    const dim3 blocks((unsigned)((g.nt[0] + kWarps - 1) / kWarps), (unsigned)g.nt[1], (unsigned)g.nt[2]);
     if (lattice == 9) {
         if (rec_double) k_pack_tiles<D2Q9, double><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
         else k_pack_tiles<D2Q9, float><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);

@@ -416,9 +416,12 @@ template <class L, typename T>
 __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
     __shared__ int s_id[kWarps][64];
     __shared__ int s_cnt[kWarps];
+    __shared__ uint2 s_ent[kWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long tile = (long long)blockIdx.x * kWarps + warp;
-    const bool valid = tile < ntiles;
+    // grid (nt0 / 8, nt1, nt2): the block's 8 warps take 8 tiles along x, no division
+    const int tx = (int)blockIdx.x * kWarps + warp, ty = (int)blockIdx.y, tz = (int)blockIdx.z;
+    const long long tile = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+    const bool valid = tx < g.nt[0];
     const int cnt = valid ? tl.count[tile] : -1;
     if (lane == 0) s_cnt[warp] = cnt;
     if (valid) {
@@ -427,11 +430,7 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
         if (lane == 0) blk[0] = (T)cnt;
         for (int k = lane; k < m; k += 32) s_id[warp][k] = tl.list[tile * tl.cap + k];
         __syncwarp();
-        const unsigned ut = (unsigned)tile;
-        const unsigned txy = ut / (unsigned)g.nt[0];
-        const int tx = (int)(ut - txy * (unsigned)g.nt[0]);
-        const int ty = (int)(txy % (unsigned)g.nt[1]);
-        const int tz = (int)(txy / (unsigned)g.nt[1]);
+        if (lane == 0) s_ent[warp] = make_uint2((unsigned)tile, (unsigned)ty | ((unsigned)tz << 16));
         for (int k = lane; k < m; k += 32) {
             const int id = s_id[warp][k];
             int rank = 0;
@@ -452,9 +451,7 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
         int bo = no ? atomicAdd(&tl.stats[2], no) : 0;
         for (int w = 0; w < kWarps; ++w) {
             if (s_cnt[w] < 0) continue;
-            const unsigned t = (unsigned)((long long)blockIdx.x * kWarps + w);
-            const unsigned txy = t / (unsigned)g.nt[0];
-            const uint2 ent = make_uint2(t, (txy % (unsigned)g.nt[1]) | ((txy / (unsigned)g.nt[1]) << 16));
+            const uint2 ent = s_ent[w];
             if (s_cnt[w] > 0) tl.order[bp++] = ent;
             else tl.order[ntiles + bf++] = ent;
             if (s_cnt[w] > lim) tl.order[2 * ntiles + bo++] = ent;
