@@ -306,6 +306,15 @@ def run_ours(args, rank, local_rank, world):
                                "GBs": round(byt / (us * 1e-6) / 1e9, 1)}
 
     adjoint = adjoint_timing(P, torch, stream) if (rank == 0 and not args.no_adjoint) else None
+    # where the coupled step's time goes: the step, and the DEM call alone (events on the
+    # context stream, after the timed region)
+    breakdown = None
+    if rank == 0 and use_dem:
+        cpl = coupled_timing(P, torch, stream, w, storage, steps=300)
+        breakdown = {"coupled_us": round(cpl["ms_per_step"] * 1e3, 2),
+                     "dem_call_us": round(cpl["dem_ms_per_call"] * 1e3, 2),
+                     "lbm_step_with_binning_us": round((cpl["ms_per_step"] - cpl["dem_ms_per_call"]) * 1e3, 2),
+                     "dem_substeps": cpl["dem_substeps"], "contacts": cpl["contacts"]}
     peak0, _ = load_peaks()
     d3 = (d3_workloads(P, torch, stream, [v for v in args.d3.split(",") if v], peak0)
           if (rank == 0 and not args.no_d3) else None)
@@ -358,6 +367,8 @@ def run_ours(args, rank, local_rank, world):
     }
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if breakdown is not None:
+        line["breakdown"] = breakdown
     if d3:
         line["workloads"] = d3
     return line

@@ -344,6 +344,7 @@ static AdjSpace adj_layout(const lbm_ctx *ctx, int nsteps, int K) {
 // device. Leaves the checkpoints and the tile lists for lbm_adjoint_backward.
 extern "C" lbm_status lbm_adjoint_forward(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J,
                                           long long *token, int on_device) {
+    NvtxRange nvtx_("lbm_adjoint_forward");
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 1 || checkpoint_every < 1) { ctx_error(ctx, "nsteps and checkpoint_every must be >= 1"); return LBM_ERR_ARG; }
     if (ctx->p.storage != LBM_F32 && ctx->p.storage != LBM_F64) {
@@ -430,6 +431,7 @@ done:
 // Backward half: the reverse sweep over the checkpoints of the last lbm_adjoint_forward.
 extern "C" lbm_status lbm_adjoint_backward(lbm_ctx *ctx, long long token, double *dJdX, double *dJdF,
                                            int on_device) {
+    NvtxRange nvtx_("lbm_adjoint_backward");
     if (!ctx) return LBM_ERR_ARG;
     if (!ctx->adj_ready || token != ctx->adj_token) {
         ctx_error(ctx, "no lbm_adjoint_forward with this token holds the adjoint workspace");

@@ -507,6 +507,7 @@ lbm_status ctx_step_once(lbm_ctx *ctx) {
 }
 
 extern "C" lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
+    NvtxRange nvtx_("lbm_step");
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) { ctx_error(ctx, "nsteps must be >= 0, got %d", nsteps); return LBM_ERR_ARG; }
     for (int s = 0; s < nsteps; ++s) {

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/psc_lbm.h"
 #include "psc_internal.h"
@@ -82,3 +83,12 @@ void dem_state_clear(dem_ctx *dem);
 // The fluid context's particles were replaced by the host: the DEM rebuilds its neighbour
 // list at its next call.
 void dem_particles_changed(dem_ctx *dem);
+
+// NVTX range over one call of the C ABI (visible in Nsight timelines; a no-op when no tool
+// is attached). The no-allocation step takes none.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};

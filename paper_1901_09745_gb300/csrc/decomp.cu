@@ -359,6 +359,7 @@ extern "C" lbm_status lbm_decomp_set_particles(lbm_decomp *d, int n, const doubl
 }
 
 extern "C" lbm_status lbm_decomp_step(lbm_decomp *d, int nsteps) {
+    NvtxRange nvtx_("lbm_decomp_step");
     if (!d) return LBM_ERR_ARG;
     if (nsteps < 0) return dfail(d, LBM_ERR_ARG, "nsteps must be >= 0");
     for (int t = 0; t < nsteps; ++t) {

@@ -926,6 +926,7 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
 }
 
 extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
+    NvtxRange nvtx_("dem_step");
     if (!d) return LBM_ERR_ARG;
     lbm_ctx *fl = d->fl;
     if (substeps < 0) { ctx_error(fl, "substeps must be >= 0"); return LBM_ERR_ARG; }
