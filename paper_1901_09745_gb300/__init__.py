@@ -141,10 +141,15 @@ def lib():
 
 
 def exported_symbols():
-    """Names declared ``lbm_*`` / ``dem_*`` in include/psc_lbm.h."""
+    """Names declared in include/*.h: ``lbm_*`` / ``dem_*`` (psc_lbm.h) and the host test
+    entries ``psc_test_*`` (psc_testing.h)."""
+    import glob
     import re
-    text = open(INCLUDE).read()
-    return sorted(set(re.findall(r"\b((?:lbm|dem)_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for path in glob.glob(os.path.join(os.path.dirname(INCLUDE), "*.h")):
+        with open(path) as fh:
+            names.update(re.findall(r"\b((?:lbm|dem|psc_test)_[a-z_0-9]+)\s*\(", fh.read()))
+    return sorted(names)
 
 
 # ------------------------------------------------------------------ marshalling helpers

@@ -16,8 +16,10 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpsc_lbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code without FP contraction, so the __host__ __device__ helpers that the CPU tests
+# call through testing.cu round as written on both machines (x86 and Arm)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]
+         "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function", "-Xcompiler", "-ffp-contract=off"]
 
 
 def nvcc():
@@ -34,6 +36,7 @@ def sources():
 def _headers_mtime():
     hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     hs.append(os.path.join(os.path.dirname(HERE), "include", "psc_lbm.h"))
+    hs.append(os.path.join(os.path.dirname(HERE), "include", "psc_testing.h"))
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 

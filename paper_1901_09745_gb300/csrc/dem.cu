@@ -32,8 +32,15 @@
 #include <string.h>
 
 #include "capi_internal.h"
+#include "hostdev.cuh"
 
 namespace {
+
+using psc::axis_at;
+using psc::axis_span;
+using psc::contact_sign;
+using psc::ContactSign;
+using psc::jkr_s;
 
 constexpr int kNB = 32;        // neighbour slots per particle (one warp lane each)
 constexpr int kH = 8;          // history floats per slot: xi_s[3], xi_t, xi_r[3], contact flag
@@ -135,16 +142,6 @@ __global__ void k_dem_bin(DemGeom g, int n, const double *X, const double *R, co
     const int slot = atomicAdd(&count[bin], 1);
     if (slot < g.bin_cap) list[bin * g.bin_cap + slot] = i;
     else atomicAdd(&flags[2], 1);
-}
-
-// The distinct bins along one axis around bin b: n of them, the k-th at axis_at(k, ...)
-// (periodic: b - 1, b, b + 1 wrapped, fewer when nb < 3; walls: clipped to the lattice).
-__device__ __forceinline__ void axis_span(int b, int nb, int periodic, int &start, int &n) {
-    if (periodic) { start = b - 1 + nb; n = nb < 3 ? nb : 3; }
-    else { start = b > 0 ? b - 1 : 0; n = (b + 1 < nb ? b + 1 : nb - 1) - start + 1; }
-}
-__device__ __forceinline__ int axis_at(int k, int start, int nb, int periodic) {
-    return periodic ? (start + k) % nb : start + k;
 }
 
 __device__ __forceinline__ void mass_inertia(int dim, double rho, double r, double *m, double *I);
@@ -292,38 +289,6 @@ __device__ __forceinline__ void rotate_into_plane(float *xi, const float *n) {
     for (int a = 0; a < 3; ++a) xi[a] -= dn * n[a];
     const float len1 = sqrtf(dot3f(xi, xi));
     if (len1 > 0.0f) { const float s = len0 / len1; for (int a = 0; a < 3; ++a) xi[a] *= s; }
-}
-
-// JKR contact radius ratio s = sqrt(a/a0) for t = delta R / a0^2 on the stable branch, i.e.
-// the root s >= s_c = 6^(-1/3) of s^4 - (2/3) s - t = 0 (t >= t_c = -s_c/2 at pull-off).
-// Written as s = s_c + e, the linear terms cancel exactly (4 s_c^3 = 2/3) and the equation
-// becomes e^2 (6 s_c^2 + 4 s_c e + e^2) = t - t_c, which stays well conditioned near the
-// pull-off point where the original form loses all digits to cancellation. The left side
-// is increasing and convex for e >= 0, and both starting guesses below lie to the right of
-// the root, so Newton decreases monotonically onto it.
-__device__ __forceinline__ float jkr_s(float t, int *fail, float s_prev) {
-    const float sc = 0.55032120814910446f;            // 6^(-1/3)
-    const float tau = fmaxf(t + 0.5f * sc, 0.0f);      // t - t_c
-    const float c2 = 6.0f * sc * sc, c1 = 4.0f * sc;
-    // the previous sub-step's root when there is one, kept within [e0 / 4, e0] of the cold
-    // guess e0 (which lies right of the root): Newton from the left of the root overshoots
-    // once to the right (by at most about root^2 / start), then decreases monotonically
-    const float e0 = fminf(sqrtf(tau / c2), sqrtf(sqrtf(tau)));
-    float e = (tau > 0.0f && s_prev > sc) ? fminf(fmaxf(s_prev - sc, 0.25f * e0), e0) : e0;
-    if (tau > 0.0f) {
-        int it = 0;
-        for (; it < 40; ++it) {
-            const float h = e * e * (c2 + c1 * e + e * e) - tau;
-            const float dh = e * (2.0f * c2 + 3.0f * c1 * e + 4.0f * e * e);
-            if (!(dh > 0.0f)) break;
-            const float en = fmaxf(e - h / dh, 0.0f);
-            const bool done = fabsf(en - e) <= 4e-7f * e;   // a few ulps: FP32 may cycle by one
-            e = en;
-            if (done) break;
-        }
-        if (it >= 40 || !(e == e)) *fail = 1;
-    }
-    return sc + e;
 }
 
 // One contact seen from particle i (neighbour j): force and torque on i in FP32. The caller
@@ -523,25 +488,13 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
                 }
             }
             // d^2 in FP64 with IEEE-rounded operations (bit-identical at both ends and in a
-            // CPU reference), S = r_i + r_j. delta_N = S - |d| is formed, as the reference
-            // forms it, only for pairs within a few ulps of touching: elsewhere the sign of
-            // d^2 - S^2 (one rounding, so its sign is exact) decides delta_N >= 0 and > 0,
-            // and delta_N itself enters the FP32 contact law as (S^2 - d^2) / (S + |d|).
+            // CPU reference); the contact decision of contact_sign (hostdev.cuh)
             const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])), __dmul_rn(d[2], d[2]));
             const double S = __dadd_rn(ri, rj);
-            const double u = __fma_rn(-S, S, d2);
-            const float d2f = (float)d2, inv = rsqrtf(d2f), uf = (float)u, Sf = (float)S;
-            bool ge0 = uf < 0.0f, gt0 = ge0;
-            float dnf = -uf / (Sf + d2f * inv);
-            double dn = 0.0;
-            bool exact = false;
-            if (fabsf(uf) <= Sf * Sf * 0x1p-47f) {     // |d^2 - S^2| <= ~2^-48 S^2
-                dn = __dsub_rn(S, __dsqrt_rn(d2));
-                exact = true;
-                ge0 = dn >= 0.0;
-                gt0 = dn > 0.0;
-                dnf = (float)dn;
-            }
+            const ContactSign cs = contact_sign(d2, S);
+            const bool ge0 = cs.ge0, gt0 = cs.gt0, exact = cs.exact;
+            const float inv = cs.inv, dnf = cs.dnf;
+            double dn = cs.dn;
             bool contact;
             if (!ph.adhesive) {
                 contact = gt0;

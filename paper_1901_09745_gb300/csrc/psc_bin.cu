@@ -10,44 +10,7 @@
 
 namespace psc {
 
-// Tile ranges along one axis covered by the cell interval [lo, hi] (cell centres within
-// r + h of the particle centre). Periodic axes wrap (at most two pieces, merged when they
-// meet); wall axes clip to the lattice. Returns the number of ranges (0..2).
-__device__ __forceinline__ int axis_tile_ranges(int lo, int hi, int n, int t, int nt, int periodic, int *a,
-                                                int *b) {
-    if (periodic) {
-        if (hi - lo + 1 >= n) { a[0] = 0; b[0] = nt - 1; return 1; }
-        const int A = ((lo % n) + n) % n, B = ((hi % n) + n) % n;
-        if (A <= B) { a[0] = A / t; b[0] = B / t; return 1; }
-        const int thi = A / t, tlo = B / t;
-        if (tlo >= thi) { a[0] = 0; b[0] = nt - 1; return 1; }
-        a[0] = 0; b[0] = tlo; a[1] = thi; b[1] = nt - 1;
-        return 2;
-    }
-    const int A = lo < 0 ? 0 : lo, B = hi > n - 1 ? n - 1 : hi;
-    if (A > B) return 0;
-    a[0] = A / t; b[0] = B / t;
-    return 1;
-}
-
-// The k-th tile (0 <= k < length of all ranges) of one axis.
-__device__ __forceinline__ int axis_tile(int k, int nr, const int *a, const int *b) {
-    const int l0 = b[0] - a[0] + 1;
-    return (nr < 2 || k < l0) ? a[0] + k : a[1] + (k - l0);
-}
-
 constexpr int kBinBatch = 8;   // tiles whose slot atomics one thread has in flight at once
-
-// Distance along one axis from x to the cell centres a..b of a tile (minimum image on a
-// periodic axis of length n).
-__device__ __forceinline__ float axis_gap(float x, float a, float b, float n, int periodic) {
-    float d = fmaxf(fmaxf(a - x, x - b), 0.0f);
-    if (periodic) {
-        d = fminf(d, fmaxf(fmaxf(a - (x + n), (x + n) - b), 0.0f));
-        d = fminf(d, fmaxf(fmaxf(a - (x - n), (x - n) - b), 0.0f));
-    }
-    return d;
-}
 
 __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,7 +32,7 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
         // its images at +-n only, and callers may pass positions any number of periods out
         double xw[3] = {pd.X[3 * p], pd.X[3 * p + 1], dim == 3 ? pd.X[3 * p + 2] : 0.0};
         for (int ax = 0; ax < dim; ++ax)
-            if (g.periodic[ax]) xw[ax] -= (double)g.n[ax] * floor(xw[ax] * g.inv_n[ax]);
+            if (g.periodic[ax]) xw[ax] = wrap_centre(xw[ax], g.n[ax], g.inv_n[ax]);
         const float xp[3] = {(float)xw[0], (float)xw[1], (float)xw[2]};
         for (int ax = 0; ax < 3; ++ax) {
             if (ax >= dim) { nr[ax] = 1; ra[ax][0] = rb[ax][0] = 0; len[ax] = 1; continue; }
@@ -95,15 +58,8 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
                     const int tz = axis_tile(kyz / len[1], nr[2], ra[2], rb[2]);
                     tile[q] = -1;
                     const int org[3] = {tx * tile_ext(dim, 0), ty * tile_ext(dim, 1), tz * tile_ext(dim, 2)};
-                    float d2 = 0.0f;
-#pragma unroll
-                    for (int ax = 0; ax < 3; ++ax) {
-                        if (ax >= dim) break;
-                        const float gap = axis_gap(xp[ax], (float)org[ax], (float)min(org[ax] + tile_ext(dim, ax), g.n[ax]) - 1.0f,
-                                                   (float)g.n[ax], g.periodic[ax]);
-                        d2 += gap * gap;
-                    }
-                    if (d2 <= reach * reach) {
+                    const int ext[3] = {tile_ext(dim, 0), tile_ext(dim, 1), tile_ext(dim, 2)};
+                    if (tile_in_reach(xp, reach, org, ext, g.n, g.periodic, dim)) {
                         tile[q] = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
                         slot[q] = atomicAdd(&tl.count[tile[q]], 1);
                     }

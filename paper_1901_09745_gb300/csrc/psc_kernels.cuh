@@ -31,6 +31,7 @@
 #include <stdint.h>
 
 #include "lattice.cuh"
+#include "hostdev.cuh"
 #include "psc_internal.h"
 
 namespace psc {
@@ -379,16 +380,8 @@ __device__ __forceinline__ void write_record(T *rec, const Geom &g, const Parts 
     for (int a = 0; a < 3; ++a) {
         T rel = (T)0;
         if (a < L::D) {
-            const double x = pd.X[3 * id + a];
-            int shift = org[a];
-            if (g.periodic[a]) {
-                // minimum image with respect to the tile centre; the image is decided in
-                // FP32 (candidates lie far from the half-box distance where it could
-                // differ), and X - (origin + image shift) is one exact FP64 subtraction
-                const float e = (float)x - ((float)org[a] + 0.5f * (float)(ext[a] - 1));
-                shift += g.n[a] * (int)rintf(e * (float)g.inv_n[a]);
-            }
-            rel = (T)(x - (double)shift);
+            // minimum image with respect to the tile centre, one exact FP64 subtraction
+            rel = (T)record_rel(pd.X[3 * id + a], org[a], ext[a], g.n[a], g.inv_n[a], g.periodic[a]);
         }
         rec[R_PX + a] = rel;
     }

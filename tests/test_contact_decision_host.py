@@ -1,14 +1,18 @@
 """The DEM sub-step decides contact without forming delta_N = S - sqrt(d^2) in FP64 except
-within a few ulps of touching (k_dem_substep): the sign of d^2 - S^2, formed by one fused
-multiply-add (a single rounding, so its sign is exact), decides delta_N >= 0 and > 0, and
-the correctly rounded square root is taken only when |d^2 - S^2| <= 2^-47 S^2 (tested in
-FP32). This checks that argument on the host, with the fused operation emulated in exact
-rational arithmetic, against the oracle's rule fl(S - fl(sqrt(d^2))) on pairs placed at,
-just inside and just outside touching."""
+within a few ulps of touching (contact_sign, the kernel's own code compiled for the host):
+the sign of d^2 - S^2, formed by one fused multiply-add (a single rounding, so its sign is
+exact), decides delta_N >= 0 and > 0, and the correctly rounded square root is taken only
+when |d^2 - S^2| <= 2^-47 S^2 (tested in FP32). Checked against the oracle's rule
+fl(S - fl(sqrt(d^2))) on pairs placed at, just inside and just outside touching; the same
+argument with the fused operation emulated in exact rational arithmetic agrees too."""
 import math
 from fractions import Fraction
 
+import ctypes as C
+
 import numpy as np
+
+from host_entries import H  # noqa: F401  (fixture)
 
 
 def _fma(a, b, c):
@@ -31,7 +35,13 @@ def _device(S, d2):
     return ge0, gt0
 
 
-def test_exact_contact_decision_matches_the_oracle_rule():
+def _compiled(Hl, S, d2):
+    ge0, gt0 = C.c_int(), C.c_int()
+    Hl.psc_test_contact_sign(d2, S, C.byref(ge0), C.byref(gt0))
+    return bool(ge0.value), bool(gt0.value)
+
+
+def test_exact_contact_decision_matches_the_oracle_rule(H):
     rng = np.random.default_rng(1701)
     n = 0
     for _ in range(4000):
@@ -45,6 +55,7 @@ def test_exact_contact_decision_matches_the_oracle_rule():
             dist = base + k * math.ulp(base)
             d = direction * dist
             d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]
+            assert _compiled(H, S, d2) == _oracle(S, d2), (ri, rj, k)
             assert _device(S, d2) == _oracle(S, d2), (ri, rj, k)
             n += 1
     assert n > 60000

@@ -1,16 +1,11 @@
 """The DEM neighbour-list kernel walks the bins around a particle's bin b along each axis
-as n bins from a start (axis_span / axis_at in dem.cu): b - 1, b, b + 1 wrapped on a
-periodic axis (fewer when the axis has fewer than three bins) or clipped at walls. This
-checks on the host that the walk visits exactly the distinct neighbouring bins, each once."""
+as n bins from a start (axis_span / axis_at, the kernel's own code compiled for the host):
+b - 1, b, b + 1 wrapped on a periodic axis (fewer when the axis has fewer than three bins)
+or clipped at walls. Checked: the walk visits exactly the distinct neighbouring bins, each
+once."""
+import ctypes as C
 
-
-def _span(b, nb, periodic):
-    if periodic:
-        start, n = b - 1 + nb, min(nb, 3)
-        return [(start + k) % nb for k in range(n)]
-    start = max(b - 1, 0)
-    n = min(b + 1, nb - 1) - start + 1
-    return [start + k for k in range(n)]
+from host_entries import H  # noqa: F401  (fixture)
 
 
 def _distinct_neighbours(b, nb, periodic):
@@ -26,10 +21,12 @@ def _distinct_neighbours(b, nb, periodic):
     return out
 
 
-def test_bin_walk_visits_each_neighbouring_bin_once():
+def test_bin_walk_visits_each_neighbouring_bin_once(H):
+    start, count = C.c_int(), C.c_int()
     for nb in range(1, 12):
         for b in range(nb):
             for periodic in (0, 1):
-                walk = _span(b, nb, periodic)
+                H.psc_test_axis_span(b, nb, periodic, C.byref(start), C.byref(count))
+                walk = [H.psc_test_axis_at(k, start.value, nb, periodic) for k in range(count.value)]
                 assert len(walk) == len(set(walk))
                 assert sorted(walk) == sorted(_distinct_neighbours(b, nb, periodic))

@@ -1,34 +1,13 @@
 """The binning kernel makes a particle a tile's candidate only if the distance from its
 centre to the tile's box of cell centres (minimum image on periodic axes) is at most
-r + h + 0.01 (k_bin, in FP32). This checks on the host, by brute force over the cells,
-that the test never drops a tile holding a cell centre within r + h of the particle
-(where Table 1 can give a non-zero solid fraction), in 2D and 3D, across periodic faces,
-for centres several periods outside the box, and at walls."""
+r + h + 0.01 in FP32 (tile_in_reach, with the centre first wrapped into the box: the
+kernel's own code compiled for the host). Checked by brute force over the cells: the test
+never drops a tile holding a cell centre within r + h of the particle (where Table 1 can
+give a non-zero solid fraction), in 2D and 3D, across periodic faces, for centres several
+periods outside the box, and at walls."""
 import numpy as np
 
-
-def _axis_gap(x, a, b, n, periodic):
-    f = np.float32
-    x, a, b, n = f(x), f(a), f(b), f(n)
-    d = max(max(a - x, x - b), f(0))
-    if periodic:
-        d = min(d, max(max(a - (x + n), (x + n) - b), f(0)))
-        d = min(d, max(max(a - (x - n), (x - n) - b), f(0)))
-    return d
-
-
-def _wrapped(x, n, periodic):
-    # k_bin wraps the centre into [0, n] on periodic axes (FP64) before the FP32 culling
-    return x - n * np.floor(x * (1.0 / n)) if periodic else x
-
-
-def _kept(X, reach, org, tshape, n, periodic, dim):
-    d2 = np.float32(0)
-    for ax in range(dim):
-        x = _wrapped(X[ax], n[ax], periodic[ax])
-        g = _axis_gap(x, org[ax], min(org[ax] + tshape[ax], n[ax]) - 1, n[ax], periodic[ax])
-        d2 += g * g
-    return d2 <= np.float32(reach) * np.float32(reach)
+from host_entries import H, doubles, ints  # noqa: F401  (fixture)
 
 
 def _needed(X, r, h, org, tshape, n, periodic, dim):
@@ -44,7 +23,7 @@ def _needed(X, r, h, org, tshape, n, periodic, dim):
     return bool(np.any(d2 < (r + h) ** 2))
 
 
-def test_tile_culling_keeps_every_tile_a_shell_reaches():
+def test_tile_culling_keeps_every_tile_a_shell_reaches(H):
     rng = np.random.default_rng(77)
     h = 1.0
     checked = 0
@@ -61,13 +40,14 @@ def test_tile_culling_keeps_every_tile_a_shell_reaches():
             for a in range(3):
                 if periodic[a]:
                     X[a] += n[a] * int(rng.integers(-3, 3))
-            reach = np.float32(r + h) + np.float32(0.01)
             nt = [(n[a] + tshape[a] - 1) // tshape[a] for a in range(3)]
+            cX, cn, cp, ce = doubles(*X), ints(*n), ints(*periodic), ints(*tshape)
             for tz in range(nt[2] if dim == 3 else 1):
                 for ty in range(nt[1]):
                     for tx in range(nt[0]):
                         org = (tx * tshape[0], ty * tshape[1], tz * tshape[2])
                         if _needed(X, r, h, org, tshape, n, periodic, dim):
-                            assert _kept(X, reach, org, tshape, n, periodic, dim), (dim, n, periodic, r, X, org)
+                            kept = H.psc_test_tile_in_reach(cX, r + h, ints(*org), ce, cn, cp, dim)
+                            assert kept == 1, (dim, n, periodic, r, X, org)
                             checked += 1
     assert checked > 500
