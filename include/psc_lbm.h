@@ -168,6 +168,17 @@ lbm_status lbm_adjoint_backward(lbm_ctx *ctx, long long token, double *dJdX, dou
 lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_every, double *J, double *dJdX,
                             double *dJdF, int on_device);
 
+/* Bounds-checked build: 1 when this library was compiled with the kernels' index checks
+ * (paper_1901_09745_gb300/build.py, build(checked=True): a separate libpsc_lbm_checked.so,
+ * chosen by the Python binding when PSC_LBM_CHECKED=1), else 0. In such a build every main
+ * global access of the kernels (populations, tiles and their records, particle indices,
+ * DEM neighbour slots) tests its index; an index out of range is replaced by 0 and recorded.
+ * lbm_check_violations synchronises the device and returns in *word the bits recorded since
+ * the previous call (1 population, 2 tile or list slot, 4 particle, 8 record, 16 DEM
+ * neighbour slot; 0 = none), then clears them; LBM_ERR_UNSUPPORTED in an unchecked build. */
+int lbm_checked_build(void);
+lbm_status lbm_check_violations(unsigned int *word);
+
 /* Counters (the first n of): out[0] = steps taken, out[1] = tiles whose candidate list
  * overflowed tile_cap in the last binning (handled by a slower exact path, never an
  * error), out[2] = largest candidate count of a tile in the last binning, out[3] =

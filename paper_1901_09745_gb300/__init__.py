@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libpsc_lbm.so")
+# PSC_LBM_CHECKED=1 selects the bounds-checked build (build.build(checked=True))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpsc_lbm_checked.so" if os.environ.get("PSC_LBM_CHECKED") == "1"
+                        else "libpsc_lbm.so")
 INCLUDE = os.path.join(os.path.dirname(_HERE), "include", "psc_lbm.h")
 
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
@@ -105,6 +107,8 @@ def lib():
         "lbm_kernel_timing": ([vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
         "lbm_set_body_force": ([vp, vp], C.c_int),
         "lbm_adjoint_drag": ([vp, C.c_int, C.c_int, vp, vp, vp, C.c_int], C.c_int),
+        "lbm_checked_build": ([], C.c_int),
+        "lbm_check_violations": ([C.POINTER(C.c_uint)], C.c_int),
         "lbm_adjoint_forward": ([vp, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
         "lbm_adjoint_backward": ([vp, C.c_longlong, vp, vp, C.c_int], C.c_int),
     }
@@ -315,6 +319,21 @@ def lbm_get_info(ctx):
     _check(ctx, lib().lbm_get_info(ctx.handle, out, 6))
     return dict(steps=out[0], overflow_tiles=out[1], max_tile_candidates=out[2], particles=out[3],
                 launches=out[4], collide_stream_launches=out[5])
+
+
+def lbm_checked_build():
+    """True when the loaded library is the bounds-checked build."""
+    return bool(lib().lbm_checked_build())
+
+
+def lbm_check_violations():
+    """Bits of the index checks that failed since the last call (bounds-checked build
+    only; see the header), then cleared."""
+    w = C.c_uint()
+    st = lib().lbm_check_violations(C.byref(w))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_check_violations: not a bounds-checked build" if st == LBM_ERR_UNSUPPORTED else "")
+    return w.value
 
 
 def lbm_kernel_timing(ctx, enable):

@@ -15,6 +15,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpsc_lbm.so")
+# the bounds-checked variant (-DPSC_CHECKED, see psc_internal.h): its own objects and library
+OBJ_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(LIBDIR, "libpsc_lbm_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without FP contraction, so the __host__ __device__ helpers that the CPU tests
 # call through testing.cu round as written on both machines (x86 and Arm)
@@ -40,15 +43,20 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs if os.path.exists(h))
 
 
-def build(force=False, verbose=False, extra=()):
-    os.makedirs(OBJ, exist_ok=True)
+def build(force=False, verbose=False, extra=(), checked=False):
+    """Compile what is stale and link the library; with checked=True the bounds-checked
+    variant (libpsc_lbm_checked.so)."""
+    obj_dir, lib = (OBJ_CHECKED, LIB_CHECKED) if checked else (OBJ, LIB)
+    if checked:
+        extra = tuple(extra) + ("-DPSC_CHECKED",)
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
     hdr = _headers_mtime()
     jobs = []
     for s in sources():
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OBJ, s[:-3] + ".o")
+        obj = os.path.join(obj_dir, s[:-3] + ".o")
         stale = force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr)
         jobs.append((src, obj, stale))
     cmds = [[cc] + ARCH + FLAGS + list(extra) + (["-Xptxas", "-v"] if verbose else []) + ["-c", src, "-o", obj]
@@ -62,15 +70,15 @@ def build(force=False, verbose=False, extra=()):
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(c))
     objs = [o for _, o, _ in jobs]
-    if cmds or force or not os.path.exists(LIB):
-        link = [cc] + ARCH + ["-shared", "-o", LIB + ".tmp"] + objs
+    if cmds or force or not os.path.exists(lib):
+        link = [cc] + ARCH + ["-shared", "-o", lib + ".tmp"] + objs
         r = subprocess.run(link, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(LIB + ".tmp", LIB)
-    return LIB
+        os.replace(lib + ".tmp", lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

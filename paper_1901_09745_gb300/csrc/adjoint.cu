@@ -497,3 +497,6 @@ extern "C" lbm_status lbm_adjoint_drag(lbm_ctx *ctx, int nsteps, int checkpoint_
     if (st != LBM_OK) return st;
     return lbm_adjoint_backward(ctx, token, dJdX, dJdF, on_device);
 }
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_adjoint)

@@ -705,3 +705,39 @@ extern "C" lbm_status lbm_kernel_timing(lbm_ctx *ctx, int enable, double *ms_tot
     ctx->timing = enable > 0 ? enable : 0;
     return LBM_OK;
 }
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_capi)
+
+unsigned int psc_chk_take_adjoint();
+unsigned int psc_chk_take_decomp();
+unsigned int psc_chk_take_dem();
+unsigned int psc_chk_take_noalloc();
+unsigned int psc_chk_take_psc_bf16();
+unsigned int psc_chk_take_psc_bin();
+unsigned int psc_chk_take_psc_f16();
+unsigned int psc_chk_take_psc_f32();
+unsigned int psc_chk_take_psc_f64();
+
+extern "C" int lbm_checked_build(void) {
+#ifdef PSC_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" lbm_status lbm_check_violations(unsigned int *word) {
+    if (!word) return LBM_ERR_ARG;
+    *word = 0u;
+#ifdef PSC_CHECKED
+    if (cudaDeviceSynchronize() != cudaSuccess) return LBM_ERR_CUDA;
+    unsigned int (*const take[])() = {psc_chk_take_capi, psc_chk_take_adjoint, psc_chk_take_decomp, psc_chk_take_dem,
+                                      psc_chk_take_noalloc, psc_chk_take_psc_bf16, psc_chk_take_psc_bin,
+                                      psc_chk_take_psc_f16, psc_chk_take_psc_f32, psc_chk_take_psc_f64};
+    for (auto fn : take) *word |= fn();
+    return LBM_OK;
+#else
+    return LBM_ERR_UNSUPPORTED;
+#endif
+}

@@ -392,3 +392,6 @@ extern "C" lbm_status lbm_decomp_get_forces(lbm_decomp *d, double *F, double *T)
     for (int k = 0; k < d->P; ++k) DST(ctx_check_flags(d->slab[k]), k);
     return LBM_OK;
 }
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_decomp)

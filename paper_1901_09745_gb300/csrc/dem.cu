@@ -433,7 +433,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
         const float uif[3] = {vi0.x, vi0.y, vi0.z};
         const float oif[3] = {vi0.w, vi1.x, vi1.y};
-        const int nn = nbr_n[i];
+        const int nn = (int)PSC_IDX(nbr_n[i], kNB + 1, CHK_NBR);
         if (sub == 0) {
             // the integration's inputs, loaded before the contact loop's stores
 #pragma unroll
@@ -443,7 +443,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         }
         int jn = (sub < nn) ? nbr[i * kNB + sub] : 0;     // the lane's next neighbour, loaded ahead
         for (int s = sub; s < nn; s += kLPP) {
-            const int j = jn;
+            const int j = (int)PSC_IDX(jn, b.n, CHK_PART);
             if (s + kLPP < nn) jn = nbr[i * kNB + s + kLPP];
             float *hp = hist + ((size_t)i * kNB + s) * kH;
             // everything the pair may need, loaded at once (one round trip after j)
@@ -1137,3 +1137,6 @@ extern "C" lbm_status dem_get_info(dem_ctx *d, long long *out, int n) {
     for (int i = 0; i < n && i < 5; ++i) out[i] = vals[i];
     return LBM_OK;
 }
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_dem)

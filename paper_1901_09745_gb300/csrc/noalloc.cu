@@ -179,3 +179,6 @@ extern "C" lbm_status lbm_psc_step_noalloc(const lbm_params *p, const void *f_in
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
     return LBM_OK;
 }
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_noalloc)

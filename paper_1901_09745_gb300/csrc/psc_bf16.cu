@@ -21,3 +21,6 @@ cudaError_t launch_set_bf16(int lattice, const double *f, void *fout, const Geom
 }
 
 }  // namespace psc
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_psc_bf16)

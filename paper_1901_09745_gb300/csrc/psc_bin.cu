@@ -60,7 +60,8 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
                     const int org[3] = {tx * tile_ext(dim, 0), ty * tile_ext(dim, 1), tz * tile_ext(dim, 2)};
                     const int ext[3] = {tile_ext(dim, 0), tile_ext(dim, 1), tile_ext(dim, 2)};
                     if (tile_in_reach(xp, reach, org, ext, g.n, g.periodic, dim)) {
-                        tile[q] = tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz);
+                        tile[q] = PSC_IDX(tx + (long long)g.nt[0] * (ty + (long long)g.nt[1] * tz),
+                                          (long long)g.nt[0] * g.nt[1] * g.nt[2], CHK_TILE);
                         slot[q] = atomicAdd(&tl.count[tile[q]], 1);
                     }
                 }
@@ -132,3 +133,6 @@ cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStrea
 }
 
 }  // namespace psc
+
+// the bounds-check word of this translation unit (see psc_internal.h)
+PSC_CHECK_READER(psc_chk_take_psc_bin)

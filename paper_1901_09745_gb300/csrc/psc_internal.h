@@ -5,6 +5,45 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Bounds-checked build (compiled with -DPSC_CHECKED; build(checked=True)): the kernels test
+// the indices of their main global accesses against the buffer extents. An index out of
+// range is recorded as a bit of one device word per translation unit (no relocatable device
+// code), read and cleared through lbm_check_violations, and replaced by 0, so the run goes on
+// without touching memory outside the buffers (its results are then wrong, and the word
+// says so). Unchecked builds compile the tests out: PSC_IDX(i, ...) is i.
+enum {
+    CHK_POP = 1u,        // population index outside [0, Q N)
+    CHK_TILE = 2u,       // tile index outside [0, tiles) or list slot outside its capacity
+    CHK_PART = 4u,       // particle index outside [0, n)
+    CHK_REC = 8u,        // packed-record word outside the tile's block
+    CHK_NBR = 16u,       // DEM neighbour slot or history index outside its list
+};
+#ifdef PSC_CHECKED
+static __device__ unsigned int psc_chk_word;
+#define PSC_CHECK(cond, bit) do { if (!(cond)) atomicOr(&psc_chk_word, (unsigned)(bit)); } while (0)
+__device__ __forceinline__ long long psc_chk_idx(long long i, long long lim, unsigned bit) {
+    if ((unsigned long long)i >= (unsigned long long)lim) { atomicOr(&psc_chk_word, bit); return 0; }
+    return i;
+}
+#define PSC_IDX(i, lim, bit) psc_chk_idx((long long)(i), (long long)(lim), (unsigned)(bit))
+// an offset from base index b, checked as the index b + off
+#define PSC_OFF(b, off, lim, bit) (PSC_IDX((b) + (off), (lim), (bit)) - (long long)(b))
+// the host reader of this translation unit's word (returns it and clears it)
+#define PSC_CHECK_READER(name)                                                   \
+    unsigned int name() {                                                        \
+        unsigned int v = 0, z = 0;                                               \
+        if (cudaMemcpyFromSymbol(&v, psc_chk_word, sizeof(v)) != cudaSuccess) return 0xffffffffu; \
+        cudaMemcpyToSymbol(psc_chk_word, &z, sizeof(z));                         \
+        return v;                                                                \
+    }
+#else
+#define PSC_CHECK(cond, bit) do { } while (0)
+#define PSC_IDX(i, lim, bit) (i)
+#define PSC_OFF(b, off, lim, bit) (off)
+#define PSC_CHECK_READER(name) \
+    unsigned int name() { return 0u; }
+#endif
+
 namespace psc {
 
 // Lattice geometry and the tiling of the lattice into thread blocks.

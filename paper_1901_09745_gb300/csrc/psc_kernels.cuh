@@ -157,9 +157,9 @@ pull_one(const S *__restrict__ fin, const Geom &g, int x, int y, int z, long lon
             else bounce = true;
         }
     }
-    if (bounce) return Store<S>::ld(fin, (long long)opp<L>(i) * g.ncell + cell, sc);
+    if (bounce) return Store<S>::ld(fin, PSC_IDX((long long)opp<L>(i) * g.ncell + cell, L::Q * g.ncell, CHK_POP), sc);
     long long src = (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2]);
-    return Store<S>::ld(fin, (long long)i * g.ncell + src, sc);
+    return Store<S>::ld(fin, PSC_IDX((long long)i * g.ncell + src, L::Q * g.ncell, CHK_POP), sc);
 }
 
 // The same for every face kind: beyond an open face the source is clamped onto the face
@@ -184,12 +184,12 @@ pull_one_faces(const S *__restrict__ fin, const Geom &g, int x, int y, int z, lo
             else outflow = true;
         }
     }
-    if (bounce) return Store<S>::ld(fin, (long long)opp<L>(i) * g.ncell + cell, sc);
+    if (bounce) return Store<S>::ld(fin, PSC_IDX((long long)opp<L>(i) * g.ncell + cell, L::Q * g.ncell, CHK_POP), sc);
     from_inlet = inflow;
     from_outlet = outflow && !inflow;
     if (inflow || outflow) return (typename Store<S>::T)0;
     long long src = (long long)s[0] + (long long)g.n[0] * ((long long)s[1] + (long long)g.n[1] * s[2]);
-    return Store<S>::ld(fin, (long long)i * g.ncell + src, sc);
+    return Store<S>::ld(fin, PSC_IDX((long long)i * g.ncell + src, L::Q * g.ncell, CHK_POP), sc);
 }
 
 // All Q populations of cell (x, y, z) after streaming, one pull_one per direction, the
@@ -305,7 +305,8 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
-            df[i] = RAW ? Store<S>::ldr(base, o) : Store<S>::ld(base, o, sc);
+            const long long oc = PSC_OFF(cell, o, Q * N, CHK_POP);
+            df[i] = RAW ? Store<S>::ldr(base, oc) : Store<S>::ld(base, oc, sc);
         }
         return;
     }
@@ -338,7 +339,8 @@ __device__ __forceinline__ void pull_q(const S *__restrict__ fin, const Geom &g,
         if (L::ez(i) == 1) { off += ozm; wall |= wzm; }
         if (L::ez(i) == -1) { off += ozp; wall |= wzp; }
         const long long idx = wall ? (long long)opp<L>(i) * N + cell : (long long)i * N + cell + off;
-        df[i] = RAW ? Store<S>::ldr(fin, idx) : Store<S>::ld(fin, idx, sc);
+        const long long ic = PSC_IDX(idx, Q * N, CHK_POP);
+        df[i] = RAW ? Store<S>::ldr(fin, ic) : Store<S>::ld(fin, ic, sc);
     }
 }
 
@@ -425,7 +427,7 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
         __syncwarp();
         if (lane == 0) s_ent[warp] = make_uint2((unsigned)tile, (unsigned)ty | ((unsigned)tz << 16));
         for (int k = lane; k < m; k += 32) {
-            const int id = s_id[warp][k];
+            const int id = (int)PSC_IDX(s_id[warp][k], pd.n, CHK_PART);
             int rank = 0;
             for (int q = 0; q < m; ++q) rank += (s_id[warp][q] < id);
             write_record<L, T>(blk + head_elems<T>() + (long long)rank * RW, g, pd, id, tx * L::TX, ty * L::TY,
@@ -598,7 +600,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
         const long long sy = g.n[0], sz = (long long)g.n[0] * g.n[1];
 #pragma unroll
         for (int i = 0; i < Q; ++i)
-            df[i] = Store<S>::ld(base, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), ph.sc);
+            df[i] = Store<S>::ld(base, PSC_OFF(cell, (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz), Q * N, CHK_POP), ph.sc);
     } else if (active) {
         if (FACES) {
             pull_all<L, S>(fin, g, x, y, z, cell, ph, df);
@@ -723,7 +725,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
             const T dfeq = w * (drho + rho * ((T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu));
             const T fi = ph.guo * w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
             const T out = df[i] - ph.omega * (df[i] - dfeq) + fi;
-            if (active) Store<S>::st(fout, (long long)i * N + cell, out, ph.sc);
+            if (active) Store<S>::st(fout, PSC_IDX((long long)i * N + cell, Q * N, CHK_POP), out, ph.sc);
         }
     } else {
         const T trM = Mxx + Myy + Mzz;
@@ -745,7 +747,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
             const T sfe = w * (Bn * drho + rho * ((T)3 * em + (T)4.5 * eMe - (T)1.5 * trM));
             const T out = df[i] - omB * ph.omega * (df[i] - dfeq) + Bn * (df[o] - dfeq_o - df[i]) +
                           sfe + omB * fi;
-            if (active) Store<S>::st(fout, (long long)i * N + cell, out, ph.sc);
+            if (active) Store<S>::st(fout, PSC_IDX((long long)i * N + cell, Q * N, CHK_POP), out, ph.sc);
         }
     }
 
@@ -830,7 +832,7 @@ __device__ __forceinline__ void psc_tile(const unsigned tile, const S *__restric
 #pragma unroll
                             for (int q = 0; q < NC; ++q) part[((size_t)warp * cap + kk) * NC + q] = v[q];
                         } else {
-                            const int pid = bits_id(a[R_ID]);
+                            const int pid = (int)PSC_IDX(bits_id(a[R_ID]), pd.n, CHK_PART);
 #pragma unroll
                             for (int q = 0; q < NC; ++q) {
                                 if (v[q] == (T)0) continue;
@@ -962,7 +964,7 @@ __global__ void k_set(const double *__restrict__ f, S *__restrict__ fout, Geom g
         if (wall) v = f[(long long)opp<L>(i) * g.ncell + cell];
         else if (leaves) v = f[(long long)i * g.ncell + cell];     // leaves the lattice: never pulled
         else v = f[(long long)i * g.ncell + d[0] + (long long)g.n[0] * (d[1] + (long long)g.n[1] * d[2])];
-        Store<S>::st(fout, (long long)i * g.ncell + cell, (typename Store<S>::T)(v - weight<L>(i)), ph.sc);
+        Store<S>::st(fout, PSC_IDX((long long)i * g.ncell + cell, L::Q * g.ncell, CHK_POP), (typename Store<S>::T)(v - weight<L>(i)), ph.sc);
     }
 }
 

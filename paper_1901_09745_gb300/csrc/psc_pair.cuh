@@ -98,7 +98,7 @@ __device__ __forceinline__ void pair_flush(const int cnt, const T *recs, const T
             if ((mask[w] >> k) & 1u) { sum += part[(w * kPairCap + k) * NC + q]; any = true; }
         }
         if (any && sum != (T)0) {
-            const int pid = bits_id(recs[k * RW + R_ID]);
+            const int pid = (int)PSC_IDX(bits_id(recs[k * RW + R_ID]), pd.n, CHK_PART);
             double *dst;
             if (L::D == 2) dst = (q < 2) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + 2];
             else dst = (q < 3) ? &pd.F[3 * pid + q] : &pd.T[3 * pid + q - 3];
@@ -134,8 +134,9 @@ __device__ __forceinline__ void pull_pair(const S *__restrict__ fin, const Geom 
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const long long o = (long long)i * N - (L::ex(i) + L::ey(i) * sy + L::ez(i) * sz);
-            da[i] = SC ? Store<S>::ldr(ba, o) : Store<S>::ld(ba, o, ph.sc);
-            db[i] = SC ? Store<S>::ldr(bb, o) : Store<S>::ld(bb, o, ph.sc);
+            const long long oa = PSC_OFF(cellA, o, L::Q * N, CHK_POP), ob = PSC_OFF(cellB, o, L::Q * N, CHK_POP);
+            da[i] = SC ? Store<S>::ldr(ba, oa) : Store<S>::ld(ba, oa, ph.sc);
+            db[i] = SC ? Store<S>::ldr(bb, ob) : Store<S>::ld(bb, ob, ph.sc);
         }
         return;
     }
@@ -147,9 +148,10 @@ __device__ __forceinline__ void pull_pair(const S *__restrict__ fin, const Geom 
 template <typename S>
 __device__ __forceinline__ void store_pair(S *__restrict__ fout, const long long iA, const long long iB,
                                            const typename Store<S>::T a, const typename Store<S>::T b,
-                                           const bool actA, const bool actB) {
-    if (actA) Store<S>::str(fout, iA, a);
-    if (actB) Store<S>::str(fout, iB, b);
+                                           const bool actA, const bool actB, const long long lim) {
+    (void)lim;   // the extent the bounds-checked build tests the indices of active cells against
+    if (actA) Store<S>::str(fout, PSC_IDX(iA, lim, CHK_POP), a);
+    if (actB) Store<S>::str(fout, PSC_IDX(iB, lim, CHK_POP), b);
 }
 
 template <class L> constexpr int pair_nslot() { return 4; }
@@ -178,7 +180,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
     constexpr int NSLOT = pair_nslot<L>();
     const int cap = tl.cap;
 
-    const unsigned tile = ent.x, ty = ent.y & 0xffffu, tz = ent.y >> 16;
+    const unsigned tile = (unsigned)PSC_IDX(ent.x, (long long)g.nt[0] * g.nt[1] * g.nt[2], CHK_TILE);
+    const unsigned ty = ent.y & 0xffffu, tz = ent.y >> 16;
     const int x0 = (int)(tile - (unsigned)g.nt[0] * (ty + (unsigned)g.nt[1] * tz)) * L::TX;
     const int y0 = (int)ty * L::TY;
     const int z0 = (int)tz * L::TZ;
@@ -398,7 +401,8 @@ __device__ __forceinline__ void psc_tile_pair(const uint2 ent, const int cnt, co
                 X = P::add(X, t);
             }
             const V out = P::fma(a1, df[i], P::fma(Bn, df[o], P::mul(P::sp(w * ssc), X)));
-            store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
+            store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB,
+                          L::Q * N);
         }
     }
 
@@ -508,7 +512,8 @@ __device__ __forceinline__ void fluid_tile_pair(const S *__restrict__ fin, S *__
             const T eF = edot<L, T>(i, ph.F[0], ph.F[1], ph.F[2]);
             out = P::add(out, P::mul(P::sp(w), P::sub(P::fma(P::sp((T)9 * ph.guo * eF), eu, P::sp((T)3 * ph.guo * eF)), guo3uF)));
         }
-        store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB);
+        store_pair<S>(fout, (long long)i * N + cellA, (long long)i * N + cellB, out.x, out.y, actA, actB,
+                          L::Q * N);
     }
 }
 

@@ -68,3 +68,12 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(P, "_lib", None)
     with pytest.raises(ImportError):
         P.lib()
+
+
+def test_unchecked_build_reports_no_checks(P):
+    """The default library is the unchecked build: it says so, and the check word call
+    answers LBM_ERR_UNSUPPORTED rather than a misleading zero."""
+    assert not P.lbm_checked_build()
+    with pytest.raises(P.LbmError) as ei:
+        P.lbm_check_violations()
+    assert ei.value.status == P.LBM_ERR_UNSUPPORTED
