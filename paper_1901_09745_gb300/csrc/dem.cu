@@ -441,7 +441,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
             im = b.minv[2 * i];
             iI = b.minv[2 * i + 1];
         }
-        int jn = (sub < nn) ? nbr[i * kNB + sub] : 0;     // the lane's next neighbour, loaded ahead
+        int jn = nbr[i * kNB + sub];      // the lane's next neighbour, loaded ahead (without waiting for nn)
         for (int s = sub; s < nn; s += kLPP) {
             const int j = (int)PSC_IDX(jn, b.n, CHK_PART);
             if (s + kLPP < nn) jn = nbr[i * kNB + s + kLPP];
@@ -550,6 +550,14 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         const double dist = lower ? __dadd_rn(xi[a], 0.5) : __dsub_rn((double)g.n[a] - 0.5, xi[a]);
         const double dn = __dsub_rn(ri, dist);
         float4 *wp4 = reinterpret_cast<float4 *>(b.whist + ((size_t)i * 3 + a) * kH);
+        if (dn < -2.0 * g.skin) {
+            // far from this wall: no contact now, and none in the previous sub-step either
+            // (the skin exceeds the largest pull-off separation and a call's displacement),
+            // so the history is zero -- written, not read, to spare the round trip
+            wp4[0] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            wp4[1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            continue;
+        }
         const float4 w0 = wp4[0], w1 = wp4[1];
         const bool was = w1.w != 0.0f;
         bool contact;
@@ -601,7 +609,11 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         if (a < dim) {
             un[a] = ui[a] + ph.dt * ((fi[a] + acc[a]) * im + ph.g[a]);
             xn[a] = xi[a] + ph.dt * un[a];
-            if (g.periodic[a]) xn[a] -= g.n[a] * floor(xn[a] * g.inv_n[a]);
+            // back into [0, n) on a periodic axis (a sub-step moves far less than a period)
+            if (g.periodic[a]) {
+                if (xn[a] < 0.0) xn[a] += (double)g.n[a];
+                else if (xn[a] >= (double)g.n[a]) xn[a] -= (double)g.n[a];
+            }
         } else {
             un[a] = ui[a];
             xn[a] = xi[a];
