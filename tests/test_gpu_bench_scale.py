@@ -117,6 +117,24 @@ def test_c3_full_size_one_step(P):
     _check(compare(g, o, 3), TOL32)
 
 
+@pytest.mark.parametrize("name,storage,tol", [("c3dense", "f32", TOL32),
+                                               ("c3", "f16", dict(u=1e-3, rho=1e-5, F=1e-3, T=1e-2))])
+def test_full_size_one_step_dense_and_16bit(P, name, storage, tol):
+    """The 256^3 workload at solid fraction 0.3 (5563 spheres: rows with three or four
+    candidates, the brackets beyond the kept slots evaluated again) in FP32, and the
+    2000-sphere workload in FP16 deviation storage (the configuration the storage comparison
+    times): one step from a seeded perturbed state, every cell and particle."""
+    w = synth.workload(name)
+    case = dict(lattice=19, n=w["n"], bc=w["bc"], tau=w["tau"], body_force=w["body_force"],
+                X=w["X"], U=w["U"], Om=w["Om"], r=w["r"])
+    f0 = perturbed_state(case, 15)
+    o = run_oracle(case, f0, 1)
+    g = run_gpu(P, case, f0, 1, storage=storage)
+    del f0
+    assert g["info"]["overflow_tiles"] == 0
+    _check(compare(g, o, 3), tol)
+
+
 def test_c5_coupled_subbox_with_dem_20_steps(P):
     """The coupled loop on a 64^3 channel sub-box of the 512^3 workload (walls in z,
     polydisperse spheres r ~ U(3, 8), tau 0.55, JKR DEM with 10 sub-steps per LBM step),
