@@ -32,7 +32,7 @@
 namespace psc {
 
 template <class L, typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2)
 k_adjoint(const T *__restrict__ gt, const T *__restrict__ lam_in, T *__restrict__ lam_out, Geom g,
           PhysT<T> ph, Tiles tl, Parts pd, T invT, double *dJdX, double *dFpart) {
     constexpr int Q = L::Q;
