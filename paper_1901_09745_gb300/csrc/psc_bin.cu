@@ -13,6 +13,7 @@ namespace psc {
 constexpr int kBinBatch = 8;   // tiles whose slot atomics one thread has in flight at once
 
 __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
+    pdl_launch();     // the packing kernel may start; it waits for this one to finish
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     int mx = 0;   // largest slot taken by this thread
     if (p < pd.n) {
@@ -103,8 +104,7 @@ cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl, 
                        cudaStream_t s) {
     if (pd.n <= 0) return cudaSuccess;
     const int threads = 128;
-    k_bin<<<(pd.n + threads - 1) / threads, threads, 0, s>>>(dim, g, ph.shell_h, tl, pd);
-    return cudaGetLastError();
+    return launch_pdl(k_bin, dim3((pd.n + threads - 1) / threads), dim3(threads), 0, s, dim, g, ph.shell_h, tl, pd);
 }
 
 long long pack_block_bytes(int rec_double, int cap) {
@@ -116,13 +116,11 @@ cudaError_t launch_pack(int lattice, int rec_double, const Geom &g, const Tiles 
                         long long ntiles, cudaStream_t s) {
     const dim3 blocks((unsigned)((g.nt[0] + kWarps - 1) / kWarps), (unsigned)g.nt[1], (unsigned)g.nt[2]);
     if (lattice == 9) {
-        if (rec_double) k_pack_tiles<D2Q9, double><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
-        else k_pack_tiles<D2Q9, float><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
-    } else {
-        if (rec_double) k_pack_tiles<D3Q19, double><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
-        else k_pack_tiles<D3Q19, float><<<blocks, kThreads, 0, s>>>(g, tl, pd, ntiles);
+        return rec_double ? launch_pdl(k_pack_tiles<D2Q9, double>, blocks, dim3(kThreads), 0, s, g, tl, pd, ntiles)
+                          : launch_pdl(k_pack_tiles<D2Q9, float>, blocks, dim3(kThreads), 0, s, g, tl, pd, ntiles);
     }
-    return cudaGetLastError();
+    return rec_double ? launch_pdl(k_pack_tiles<D3Q19, double>, blocks, dim3(kThreads), 0, s, g, tl, pd, ntiles)
+                      : launch_pdl(k_pack_tiles<D3Q19, float>, blocks, dim3(kThreads), 0, s, g, tl, pd, ntiles);
 }
 
 cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s) {

@@ -123,6 +123,27 @@ __device__ __forceinline__ void outlet_nebb(T *df, const PhysT<T> &ph, const flo
     (void)sc;
 }
 
+// Programmatic dependent launch within the step: a kernel launched with launch_pdl may start
+// while its predecessor in the stream finishes; it calls pdl_wait() before it reads anything
+// the predecessor wrote, and pdl_launch() lets its own successor start early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Is cell (x, y, z) one this context updates (inside the lattice and, in a slab of a
 // decomposed lattice, outside its ghost layers along the slowest axis; act1 <= n there)?
 template <class L>
@@ -412,6 +433,8 @@ __global__ void k_pack_tiles(Geom g, Tiles tl, Parts pd, long long ntiles) {
     __shared__ int s_id[kWarps][64];
     __shared__ int s_cnt[kWarps];
     __shared__ uint2 s_ent[kWarps];
+    pdl_wait();       // the binning kernel's counts and lists
+    pdl_launch();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // grid (nt0 / 8, nt1, nt2): the block's 8 warps take 8 tiles along x, no division
     const int tx = (int)blockIdx.x * kWarps + warp, ty = (int)blockIdx.y, tz = (int)blockIdx.z;
