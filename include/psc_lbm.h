@@ -103,8 +103,16 @@ lbm_status lbm_destroy(lbm_ctx *ctx);
  * n x 3) and radii (n), used by Eq. 10 (u_s = U + Omega x (x_n - X), Eq. 12) and by the
  * solid fractions of Table 1. Radii must satisfy r^2 > 1/2 in 3D (Eq. 17 is defined) and
  * r^2 > 1/4 in 2D (Eq. 19), and
- * a periodic axis must be longer than 2 (r + h) + 1. The data is copied. n = 0 removes all
- * particles. */
+ * a periodic axis must be longer than 2 (r + h) + 1; host values must be finite. Nothing
+ * changes when a check fails (LBM_ERR_ARG with a message). on_device = 0: host arrays,
+ * copied before the call returns (page-locked ones are read by the upload kernel directly,
+ * pageable ones go through cudaMemcpyAsync); on_device = 1: device arrays, copied in stream
+ * order. F and T are cleared. n = 0 removes all particles. A particle's index is its
+ * identity: with an attached DEM context (dem_create), an upload of the same count and the
+ * same radii keeps the DEM's neighbour list and contact history, and the list is rebuilt at
+ * the next dem_step only when some particle now lies more than a quarter of the skin from
+ * its position at the list's build (the criterion of the sub-steps); any other upload
+ * rebuilds it (history carried over by index). */
 lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
                              const double *Omega, const double *radius, int on_device);
 
@@ -115,8 +123,11 @@ lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double 
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* Force F and torque T (n x 3 each) on every particle from the last step's collision
- * (Eq. 14; Eq. 11 in original mode). Zero before the first step. Synchronises when the
- * destination is host memory. */
+ * (Eq. 14; Eq. 11 in original mode). Zero before the first step. Either may be NULL (not
+ * both). on_device = 1: device arrays, copied in stream order. on_device = 0: host arrays;
+ * the call synchronises and returns the status of the device's flag words (LBM_ERR_UNSTABLE,
+ * DEM_ERR_NO_CONVERGENCE, LBM_ERR_OVERFLOW); page-locked arrays are written by one kernel
+ * together with those words, pageable ones through cudaMemcpyAsync. */
 lbm_status lbm_get_forces(lbm_ctx *ctx, double *F, double *T, int on_device);
 
 /* Density rho (ncell) and force-shifted velocity u (ncell x 3) of Eq. 5 at the current
@@ -243,8 +254,9 @@ lbm_status dem_get_contacts(dem_ctx *dem, int *pairs, double *hist, int cap, int
  * doubles each, as for pairs; hist may be NULL). LBM_ERR_OVERFLOW beyond cap. */
 lbm_status dem_get_wall_contacts(dem_ctx *dem, int *pw, double *hist, int cap, int *n);
 
-/* Counters: out[0] DEM kernels launched, out[1] contact solves that did not converge,
- * out[2] bin/neighbour-list overflows, out[3] skin violations, out[4] particles. */
+/* Counters (the first n of them): out[0] DEM kernels launched, out[1] contact solves that
+ * did not converge, out[2] bin/neighbour-list overflows, out[3] skin violations, out[4]
+ * particles, out[5] neighbour-list rebuilds. */
 lbm_status dem_get_info(dem_ctx *dem, long long *out, int n);
 
 /* ------------------------------------------------------------- slab decomposition --- */

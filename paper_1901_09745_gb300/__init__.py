@@ -412,8 +412,6 @@ def dem_get_particles(dem, X=None, U=None, Om=None):
 def dem_get_contacts(dem, cap=None):
     """Sorted canonical pairs (k, 2) and their history seen from i (k, 7)."""
     n = C.c_int()
-    _check(dem.fluid, lib().dem_get_contacts(dem.handle, None, None, 0, C.byref(n))
-           if False else LBM_OK)
     cap = cap or max(16, 16 * dem.fluid.np)
     pairs = np.zeros((cap, 2), dtype=np.int32)
     hist = np.zeros((cap, 7))
@@ -436,10 +434,10 @@ def dem_get_wall_contacts(dem, cap=None):
 
 
 def dem_get_info(dem):
-    out = (C.c_longlong * 5)()
-    _check(dem.fluid, lib().dem_get_info(dem.handle, out, 5))
+    out = (C.c_longlong * 6)()
+    _check(dem.fluid, lib().dem_get_info(dem.handle, out, 6))
     return dict(launches=out[0], solve_failures=out[1], overflows=out[2], skin_violations=out[3],
-                particles=out[4])
+                particles=out[4], rebuilds=out[5])
 
 
 # ------------------------------------------------------------ step without device allocation

@@ -3,6 +3,7 @@
 // fused PSC collide-stream). Every entry point returns an lbm_status and never aborts.
 #include <math.h>
 #include <stdarg.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -181,6 +182,7 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (st != LBM_OK) return st;
     lbm_ctx *ctx = (lbm_ctx *)calloc(1, sizeof(lbm_ctx));
     if (!ctx) { ctx_error(NULL, "host allocation failed"); return LBM_ERR_OOM; }
+    ctx->hR_n = -1;
     ctx->p = *p;
     if (ctx->p.shell_h <= 0.0) ctx->p.shell_h = 1.0;
     if (ctx->p.tile_cap <= 0) ctx->p.tile_cap = 64;
@@ -236,6 +238,8 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[1], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->flags, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&ctx->hflags, 4 * sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&ctx->hflags_dev, ctx->hflags, 0);
     // rest state f_i = w_i: every stored deviation is zero (all-zero bits in every format)
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f[0], 0, bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f[1], 0, bytes, ctx->stream);
@@ -257,6 +261,8 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (ctx->dem) dem_release(ctx->dem);
     free_dev(&ctx->f[0]); free_dev(&ctx->f[1]);
     free_dev((void **)&ctx->flags);
+    if (ctx->hflags) cudaFreeHost(ctx->hflags);
+    free(ctx->hR);
     free_particles(ctx);
     free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
     free_dev((void **)&ctx->tile_order);
@@ -303,15 +309,37 @@ void ctx_update_wrap(lbm_ctx *ctx) {
     }
 }
 
+static const uint64_t kExpBits = 0x7ff0000000000000ull;
+
+// 1 when the m values are all finite: a branch-free pass over the bit patterns (all exponent
+// bits set is an infinity or a NaN), which the compiler vectorizes.
+static int all_finite(const double *a, size_t m) {
+    uint64_t bad = 0;
+    for (size_t i = 0; i < m; ++i) {
+        uint64_t b;
+        memcpy(&b, a + i, sizeof(b));
+        bad |= (uint64_t)((b & kExpBits) == kExpBits);
+    }
+    return bad == 0;
+}
+
 lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n) {
-    double rmax = 0.0;
     const double rmin2 = (ctx->dim == 2) ? 0.25 : 0.5;
+    // one branch-free pass (smallest r^2, largest r); the per-particle search only for the
+    // message when it finds a radius out of range
+    double s2min = INFINITY, rmax = 0.0;
     for (int i = 0; i < n; ++i) {
-        if (!(R[i] * R[i] > rmin2) || !isfinite(R[i])) {
-            ctx_error(ctx, "radius %d = %g: the linear approximation (Eq. 17/19) needs r^2 > %g", i, R[i], rmin2);
-            return LBM_ERR_ARG;
+        const double r = R[i], r2 = r * r;
+        s2min = r2 < s2min ? r2 : s2min;
+        rmax = r > rmax ? r : rmax;
+    }
+    if (n > 0 && (!(s2min > rmin2) || !all_finite(R, (size_t)n))) {
+        for (int i = 0; i < n; ++i) {
+            if (!(R[i] * R[i] > rmin2) || !isfinite(R[i])) {
+                ctx_error(ctx, "radius %d = %g: the linear approximation (Eq. 17/19) needs r^2 > %g", i, R[i], rmin2);
+                return LBM_ERR_ARG;
+            }
         }
-        if (R[i] > rmax) rmax = R[i];
     }
     for (int a = 0; a < ctx->dim; ++a) {
         if (ctx->g.periodic[a] && n > 0 && ctx->g.n[a] <= (int)floor(2.0 * (rmax + ctx->p.shell_h)) + 1) {
@@ -356,15 +384,37 @@ static lbm_status ctx_reserve_tiles(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+// The address at which this context's kernels can read or write the caller's array: device
+// memory of this device, managed memory, or page-locked host memory mapped into the
+// device's address space. NULL for pageable host memory and for another device's memory
+// (cudaMemcpyAsync moves those).
+static void *device_view(const lbm_ctx *ctx, const void *p) {
+    if (!p) return NULL;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return NULL;
+    }
+    switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == ctx->device ? at.devicePointer : NULL;
+    case cudaMemoryTypeHost:
+    case cudaMemoryTypeManaged: return at.devicePointer;
+    default: return NULL;
+    }
+}
+
 extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
                                         const double *Omega, const double *radius, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
+    NvtxRange nvtx_("lbm_set_particles");
     ctx->mods += 1;
     if (n < 0 || n > (1 << 24)) { ctx_error(ctx, "particle count must be in [0, 2^24], got %d", n); return LBM_ERR_ARG; }
     if (n > 0 && (!X || !U || !Omega || !radius)) { ctx_error(ctx, "particle arrays must not be NULL"); return LBM_ERR_ARG; }
     cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // validate radii on the host (device radii are copied back once)
+    // validate on the host (device radii are copied back once); nothing on the device
+    // changes before the arguments pass
     double *hr = NULL;
+    const double *Rh = radius;
     if (n > 0) {
         if (on_device) {
             hr = (double *)malloc((size_t)n * sizeof(double));
@@ -372,11 +422,12 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
             cudaError_t e = cudaMemcpyAsync(hr, radius, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
             if (e != cudaSuccess) { free(hr); return ctx_cuda(ctx, e, "copy radii"); }
+            Rh = hr;
         }
-        lbm_status st = ctx_check_radii(ctx, on_device ? hr : radius, n);
-        free(hr);
-        if (st != LBM_OK) return st;
-        if (!on_device) {
+        lbm_status st = ctx_check_radii(ctx, Rh, n);
+        if (st != LBM_OK) { free(hr); return st; }
+        if (!on_device && !(all_finite(X, 3 * (size_t)n) && all_finite(U, 3 * (size_t)n) &&
+                            all_finite(Omega, 3 * (size_t)n))) {
             for (int i = 0; i < 3 * n; ++i)
                 if (!isfinite(X[i]) || !isfinite(U[i]) || !isfinite(Omega[i])) {
                     ctx_error(ctx, "particle %d has a non-finite position, velocity or spin", i / 3);
@@ -384,24 +435,58 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
                 }
         }
     }
+    // the radii of the last upload are kept on the host: with the same count and radii the
+    // DEM may keep its neighbour list (the device then tests the displacements)
+    const int same_radii = n > 0 && ctx->hR_n == n && memcmp(ctx->hR, Rh, (size_t)n * sizeof(double)) == 0;
+    if (n > 0 && !same_radii) {
+        if (n > ctx->hR_cap) {
+            double *t = (double *)realloc(ctx->hR, (size_t)n * sizeof(double));
+            if (!t) { free(hr); ctx_error(ctx, "host allocation failed"); return LBM_ERR_OOM; }
+            ctx->hR = t;
+            ctx->hR_cap = n;
+        }
+        memcpy(ctx->hR, Rh, (size_t)n * sizeof(double));
+    }
+    free(hr);
+    ctx->hR_n = -1;     // until the upload below has been queued
     lbm_status st = ctx_reserve_particles(ctx, n);
     if (st != LBM_OK) return st;
+    int keep_list = 0;
     if (n > 0) {
-        size_t v = (size_t)n * 3 * sizeof(double), s = (size_t)n * sizeof(double);
-        CK(cudaMemcpyAsync(ctx->dX, X, v, kind, ctx->stream), "copy X");
-        CK(cudaMemcpyAsync(ctx->dU, U, v, kind, ctx->stream), "copy U");
-        CK(cudaMemcpyAsync(ctx->dOm, Omega, v, kind, ctx->stream), "copy Omega");
-        CK(cudaMemcpyAsync(ctx->dR, radius, s, kind, ctx->stream), "copy radius");
-        CK(cudaMemsetAsync(ctx->dF, 0, v, ctx->stream), "memset F");
-        CK(cudaMemsetAsync(ctx->dT, 0, v, ctx->stream), "memset T");
-        CK(launch_f_of_r(ctx->dim, ctx->dR, ctx->dFr, n, ctx->stream), "f(r) kernel");
+        Upload u;
+        memset(&u, 0, sizeof(u));
+        u.n = n;
+        u.dim = ctx->dim;
+        u.dX = ctx->dX; u.dU = ctx->dU; u.dOm = ctx->dOm; u.dR = ctx->dR; u.dFr = ctx->dFr;
+        u.dF = ctx->dF; u.dT = ctx->dT;
+        for (int a = 0; a < 3; ++a) { u.n_lat[a] = ctx->g.n[a]; u.periodic[a] = ctx->g.periodic[a]; }
+        if (ctx->dem && same_radii) keep_list = dem_upload_check(ctx->dem, n, &u.ref, &u.req, &u.lim2);
+        // sources the kernel can read directly (device memory, mapped page-locked host
+        // memory) are read by it; others are first copied into the context's arrays and
+        // the kernel then reads those in place
+        const void *v[4] = {device_view(ctx, X), device_view(ctx, U), device_view(ctx, Omega), device_view(ctx, radius)};
+        if (v[0] && v[1] && v[2] && v[3]) {
+            u.X = (const double *)v[0]; u.U = (const double *)v[1]; u.Om = (const double *)v[2];
+            u.R = (const double *)v[3];
+        } else {
+            size_t vb = (size_t)n * 3 * sizeof(double), sb = (size_t)n * sizeof(double);
+            CK(cudaMemcpyAsync(ctx->dX, X, vb, kind, ctx->stream), "copy X");
+            CK(cudaMemcpyAsync(ctx->dU, U, vb, kind, ctx->stream), "copy U");
+            CK(cudaMemcpyAsync(ctx->dOm, Omega, vb, kind, ctx->stream), "copy Omega");
+            CK(cudaMemcpyAsync(ctx->dR, radius, sb, kind, ctx->stream), "copy radius");
+            u.X = ctx->dX; u.U = ctx->dU; u.Om = ctx->dOm; u.R = ctx->dR;
+        }
+        CK(launch_upload(u, ctx->stream), "particle upload kernel");
+        ctx->launches += 1;
         st = ctx_reserve_tiles(ctx);
         if (st != LBM_OK) return st;
+        // the caller may reuse its host arrays once this returns
         if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "set_particles sync");
     }
+    ctx->hR_n = n;
     ctx->np = n;
     ctx->bins_valid = 0;
-    if (ctx->dem) dem_particles_changed(ctx->dem);
+    if (ctx->dem && !keep_list) dem_particles_changed(ctx->dem);
     ctx_update_wrap(ctx);
     return LBM_OK;
 }
@@ -518,10 +603,7 @@ extern "C" lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
 }
 
 // Read the device flag word after a synchronisation and turn it into a status.
-lbm_status ctx_check_flags(lbm_ctx *ctx) {
-    int h[4];
-    CK(cudaMemcpyAsync(h, ctx->flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "read flags");
-    CK(cudaStreamSynchronize(ctx->stream), "sync");
+static lbm_status flags_status(lbm_ctx *ctx, const int *h) {
     if (h[0] & 1) { ctx_error(ctx, "a cell reached a non-positive or NaN density (unstable run)"); return LBM_ERR_UNSTABLE; }
     if (h[1]) { ctx_error(ctx, "JKR contact-radius solve did not converge for %d contacts", h[1]); return DEM_ERR_NO_CONVERGENCE; }
     if (h[2]) { ctx_error(ctx, "%d DEM bin or neighbour-list overflows (more neighbours than slots)", h[2]); return LBM_ERR_OVERFLOW; }
@@ -529,16 +611,35 @@ lbm_status ctx_check_flags(lbm_ctx *ctx) {
     return LBM_OK;
 }
 
+lbm_status ctx_check_flags(lbm_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->hflags, ctx->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read flags");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    return flags_status(ctx, ctx->hflags);
+}
+
 extern "C" lbm_status lbm_get_forces(lbm_ctx *ctx, double *F, double *T, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
     if (ctx->np == 0) return on_device ? LBM_OK : ctx_check_flags(ctx);
     if (!F && !T) { ctx_error(ctx, "F and T are both NULL"); return LBM_ERR_ARG; }
-    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    size_t v = (size_t)ctx->np * 3 * sizeof(double);
-    if (F) CK(cudaMemcpyAsync(F, ctx->dF, v, kind, ctx->stream), "copy F");
-    if (T) CK(cudaMemcpyAsync(T, ctx->dT, v, kind, ctx->stream), "copy T");
-    if (!on_device) return ctx_check_flags(ctx);
-    return LBM_OK;
+    const size_t v = (size_t)ctx->np * 3 * sizeof(double);
+    if (on_device) {
+        if (F) CK(cudaMemcpyAsync(F, ctx->dF, v, cudaMemcpyDeviceToDevice, ctx->stream), "copy F");
+        if (T) CK(cudaMemcpyAsync(T, ctx->dT, v, cudaMemcpyDeviceToDevice, ctx->stream), "copy T");
+        return LBM_OK;
+    }
+    // host arrays the kernel can write (mapped page-locked memory) take F, T and the flag
+    // words in one launch; pageable ones are copied
+    void *vF = device_view(ctx, F), *vT = device_view(ctx, T);
+    if ((!F || vF) && (!T || vT)) {
+        CK(launch_download(ctx->dF, ctx->dT, (double *)vF, (double *)vT, 3LL * ctx->np, ctx->flags, ctx->hflags_dev,
+                           ctx->stream), "force download kernel");
+        ctx->launches += 1;
+        CK(cudaStreamSynchronize(ctx->stream), "sync");
+        return flags_status(ctx, ctx->hflags);
+    }
+    if (F) CK(cudaMemcpyAsync(F, ctx->dF, v, cudaMemcpyDeviceToHost, ctx->stream), "copy F");
+    if (T) CK(cudaMemcpyAsync(T, ctx->dT, v, cudaMemcpyDeviceToHost, ctx->stream), "copy T");
+    return ctx_check_flags(ctx);
 }
 
 static lbm_status ctx_diag(lbm_ctx *ctx, size_t doubles) {

@@ -21,12 +21,15 @@ struct lbm_ctx {
     int own_stream;
     int device;
     int *flags;                // device flag word: [0] bit 0 unstable density, [1] DEM failures
+    int *hflags, *hflags_dev;  // its page-locked host mirror (host / device address)
 
     // particles (FP64, device)
     int np, np_cap;
     double *dX, *dU, *dOm, *dR, *dFr, *dF, *dT;
     float4 *dPf;               // FP32 record data per particle (binning kernel)
     double rmax;
+    double *hR;                // host copy of the radii of the last upload (hR_n of them,
+    int hR_n, hR_cap;          // -1: unknown), to tell whether an upload changed them
 
     // tile candidate lists
     long long ntiles;
@@ -83,6 +86,12 @@ void dem_state_clear(dem_ctx *dem);
 // The fluid context's particles were replaced by the host: the DEM rebuilds its neighbour
 // list at its next call.
 void dem_particles_changed(dem_ctx *dem);
+// A particle upload of n particles with the radii unchanged may keep the DEM's neighbour
+// list when no particle has moved more than a quarter of the skin from its position at the
+// list's build (the criterion the sub-steps apply): returns 1 and the reference positions,
+// the device word that requests a rebuild and the squared threshold (FP32), or 0 when the
+// list must be rebuilt anyway (no valid list, another count).
+int dem_upload_check(dem_ctx *dem, int n, const double **ref, int **req, float *lim2);
 
 // NVTX range over one call of the C ABI (visible in Nsight timelines; a no-op when no tool
 // is attached). The no-allocation step takes none.

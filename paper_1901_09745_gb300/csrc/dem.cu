@@ -41,6 +41,7 @@ using psc::axis_span;
 using psc::contact_sign;
 using psc::ContactSign;
 using psc::jkr_s;
+using psc::moved2;
 
 constexpr int kNB = 32;        // neighbour slots per particle (one warp lane each)
 constexpr int kH = 8;          // history floats per slot: xi_s[3], xi_t, xi_r[3], contact flag
@@ -90,9 +91,9 @@ struct DemBufs {
 };
 
 // Device words of a DEM context: a rebuild request (nonzero: rebuild the neighbour list at
-// the next call; set by a sub-step or by the host), the index (0/1) of the current list
-// buffer, and this call's decision.
-enum { kRebuildReq = 0, kListIdx = 1, kRebuildNow = 2, kStateWords = 4 };
+// the next call; set by a sub-step, a particle upload or the host), the index (0/1) of the
+// current list buffer, this call's decision, and the number of rebuilds so far.
+enum { kRebuildReq = 0, kListIdx = 1, kRebuildNow = 2, kRebuilds = 3, kStateWords = 4 };
 
 // Programmatic dependent launch: a kernel launched with that attribute may start while the
 // kernel before it in the stream runs; it waits here until that kernel has finished and its
@@ -111,7 +112,7 @@ __global__ void k_dem_decide(int *state, int *count, long long nbins) {
     if (t == 0) {
         const int rb = state[kRebuildReq] != 0;
         state[kRebuildNow] = rb;
-        if (rb) state[kListIdx] ^= 1;
+        if (rb) { state[kListIdx] ^= 1; state[kRebuilds] += 1; }
         state[kRebuildReq] = 0;
     }
 }
@@ -621,18 +622,7 @@ __global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
         const bool spin = (dim == 3) || (a == 2);
         on[a] = spin ? oi[a] + ph.dt * (ti[a] + acc[3 + a]) * iI : oi[a];
     }
-    float disp2 = 0.0f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a >= dim) break;
-        float dd = (float)(xn[a] - xr[a]);
-        if (g.periodic[a]) {
-            const float half = 0.5f * (float)g.n[a];
-            if (dd > half) dd -= (float)g.n[a];
-            else if (dd < -half) dd += (float)g.n[a];
-        }
-        disp2 += dd * dd;
-    }
+    const float disp2 = moved2(xn, xr, g.n, g.periodic, dim);
     if (disp2 > 0.25f * (float)(g.skin * g.skin)) atomicAdd(&b.flags[3], 1);
     // a quarter of the skin used: the next call rebuilds the list
     if (disp2 > 0.0625f * (float)(g.skin * g.skin)) b.state[kRebuildReq] = 1;
@@ -683,6 +673,14 @@ static int dem_list_index(dem_ctx *d, int *idx) {
 
 void dem_particles_changed(dem_ctx *d) {
     if (d) d->force_rebuild = 1;
+}
+
+int dem_upload_check(dem_ctx *d, int n, const double **ref, int **req, float *lim2) {
+    if (!d || !d->lists_valid || d->force_rebuild || d->n != n || n <= 0 || !d->Xref || !d->state) return 0;
+    *ref = d->Xref;
+    *req = d->state + kRebuildReq;
+    *lim2 = 0.0625f * (float)(d->g.skin * d->g.skin);   // the sub-step's own threshold
+    return 1;
 }
 
 static void dfree(void **p) { if (*p) cudaFree(*p); *p = NULL; }
@@ -1142,11 +1140,12 @@ extern "C" lbm_status dem_get_wall_contacts(dem_ctx *d, int *pw, double *hist, i
 extern "C" lbm_status dem_get_info(dem_ctx *d, long long *out, int n) {
     if (!d || !out || n < 1) return LBM_ERR_ARG;
     lbm_ctx *fl = d->fl;
-    int h[4] = {0, 0, 0, 0};
+    int h[4] = {0, 0, 0, 0}, st[kStateWords] = {0, 0, 0, 0};
     DCK(cudaMemcpyAsync(h, fl->flags, sizeof(h), cudaMemcpyDeviceToHost, fl->stream), "read flags");
+    if (d->state) DCK(cudaMemcpyAsync(st, d->state, sizeof(st), cudaMemcpyDeviceToHost, fl->stream), "read state");
     DCK(cudaStreamSynchronize(fl->stream), "sync");
-    long long vals[5] = {d->launches, h[1], h[2], h[3], d->n};
-    for (int i = 0; i < n && i < 5; ++i) out[i] = vals[i];
+    long long vals[6] = {d->launches, h[1], h[2], h[3], d->n, st[kRebuilds]};
+    for (int i = 0; i < n && i < 6; ++i) out[i] = vals[i];
     return LBM_OK;
 }
 

@@ -92,6 +92,27 @@ __host__ __device__ __forceinline__ int axis_at(int k, int start, int nb, int pe
     return periodic ? (start + k) % nb : start + k;
 }
 
+// Squared displacement (FP32) of a particle at x from its position xr at the last
+// neighbour-list build: one image shift on a periodic axis, so the result is never below the
+// minimum-image displacement. The DEM rebuilds its list once a particle passes a quarter of
+// the skin; both the sub-step and a particle upload test this value.
+__host__ __device__ __forceinline__ float moved2(const double *x, const double *xr, const int *n, const int *periodic,
+                                                 int dim) {
+    float d2 = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dim) break;
+        float dd = (float)(x[a] - xr[a]);
+        if (periodic[a]) {
+            const float half = 0.5f * (float)n[a];
+            if (dd > half) dd -= (float)n[a];
+            else if (dd < -half) dd += (float)n[a];
+        }
+        d2 += dd * dd;
+    }
+    return d2;
+}
+
 // IEEE-rounded FP64 operations, no contraction on either side (the device intrinsics; on the
 // host plain operations, the library being compiled with FP contraction off).
 __host__ __device__ __forceinline__ double dadd_rn(double a, double b) {

@@ -84,10 +84,8 @@ __global__ void k_bin(int dim, Geom g, double h, Tiles tl, Parts pd) {
 
 // Eq. 18 with V_a of Eq. 17 (3D) or Eq. 19 (2D), the integrand read as the sphere (disc)
 // height sqrt(r^2 - x^2 - y^2) over the unit square (segment); principal arctangents.
-__global__ void k_f_of_r(int dim, const double *R, double *Fr, int n) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const double r = R[p], r2 = r * r;
+__device__ __forceinline__ double f_of_r(int dim, double r) {
+    const double r2 = r * r;
     double va;
     if (dim == 2) {
         const double s = sqrt(r2 - 0.25);
@@ -97,7 +95,51 @@ __global__ void k_f_of_r(int dim, const double *R, double *Fr, int n) {
         va = (1.0 / 12.0 - r2) * atan(0.5 * s / (0.5 - r2)) + s / 3.0 +
              (r2 - 1.0 / 12.0) * atan(0.5 / s) - (4.0 / 3.0) * r2 * r * atan(0.25 / (r * s));
     }
-    Fr[p] = va - r + 0.5;
+    return va - r + 0.5;
+}
+
+__global__ void k_f_of_r(int dim, const double *R, double *Fr, int n) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    Fr[p] = f_of_r(dim, R[p]);
+}
+
+// One thread per particle. Sources and destinations may be the same arrays (each thread
+// reads its elements before writing them), so no pointer is declared restrict.
+__global__ void k_upload(Upload u) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= u.n) return;
+    double x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long k = 3LL * p + a;
+        x[a] = u.X[k];
+        const double v = u.U[k], o = u.Om[k];
+        u.dX[k] = x[a];
+        u.dU[k] = v;
+        u.dOm[k] = o;
+        u.dF[k] = 0.0;
+        u.dT[k] = 0.0;
+    }
+    const double r = u.R[p];
+    u.dR[p] = r;
+    u.dFr[p] = f_of_r(u.dim, r);
+    if (u.ref) {
+        const double xr[3] = {u.ref[3LL * p], u.ref[3LL * p + 1], u.ref[3LL * p + 2]};
+        if (psc::moved2(x, xr, u.n_lat, u.periodic, u.dim) > u.lim2) *u.req = 1;
+    }
+}
+
+// F, T and the flag words to the caller's memory (device memory or mapped page-locked host
+// memory), one thread per element.
+__global__ void k_download(const double *F, const double *T, double *Fo, double *To, long long m, const int *flags,
+                           int *flags_out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < m) {
+        if (Fo) Fo[k] = F[k];
+        if (To) To[k] = T[k];
+    }
+    if (k < 4) flags_out[k] = flags[k];
 }
 
 cudaError_t launch_bin(int dim, const Geom &g, const Phys &ph, const Tiles &tl, const Parts &pd,
@@ -127,6 +169,21 @@ cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStrea
     if (n <= 0) return cudaSuccess;
     const int threads = 128;
     k_f_of_r<<<(n + threads - 1) / threads, threads, 0, s>>>(dim, R, Fr, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_upload(const Upload &u, cudaStream_t s) {
+    if (u.n <= 0) return cudaSuccess;
+    const int threads = 128;
+    k_upload<<<(u.n + threads - 1) / threads, threads, 0, s>>>(u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_download(const double *F, const double *T, double *Fo, double *To, long long m,
+                            const int *flags, int *flags_out, cudaStream_t s) {
+    const int threads = 256;
+    const long long work = m > 4 ? m : 4;
+    k_download<<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(F, T, Fo, To, m, flags, flags_out);
     return cudaGetLastError();
 }
 

@@ -152,5 +152,24 @@ cudaError_t launch_adjoint(int storage, int lattice, const void *gt, const void 
                            double *dJdX, double *dFpart, cudaStream_t s);
 // f(r) of Eq. 18 (Eq. 17 in 3D, Eq. 19 in 2D) for every particle.
 cudaError_t launch_f_of_r(int dim, const double *R, double *Fr, int n, cudaStream_t s);
+// A particle upload in one launch: X, U, Omega (n x 3) and the radii copied from the
+// sources (device memory, or page-locked host memory mapped into the device's address
+// space; a source may be its own destination) into the context's arrays, F and T cleared,
+// f(r) evaluated; when `ref` is set, *req = 1 if some particle lies more than sqrt(lim2)
+// (FP32, one image shift on periodic axes) from its reference position.
+struct Upload {
+    const double *X, *U, *Om, *R;
+    double *dX, *dU, *dOm, *dR, *dFr, *dF, *dT;
+    int n, dim;
+    const double *ref;
+    int *req;
+    float lim2;
+    int n_lat[3], periodic[3];
+};
+cudaError_t launch_upload(const Upload &u, cudaStream_t s);
+// m = 3 n doubles of F and T (either output may be NULL) and the four flag words copied to
+// the caller's memory (device memory or mapped page-locked host memory).
+cudaError_t launch_download(const double *F, const double *T, double *Fo, double *To, long long m,
+                            const int *flags, int *flags_out, cudaStream_t s);
 
 }  // namespace psc

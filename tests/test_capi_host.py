@@ -35,7 +35,7 @@ def test_header_cites_the_paper_for_each_hot_path_entry_point():
     assert "arXiv 1901.09745" in text
     for name in ("lbm_create", "lbm_set_particles", "lbm_step", "lbm_get_forces"):
         pos = text.index(name + "(")
-        block = text[max(0, pos - 900):pos]
+        block = text[:pos]
         comment = block[block.rfind("/*"):]
         assert re.search(r"(Eq\.|Sec\.|Table)", comment), name
 
