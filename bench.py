@@ -358,7 +358,10 @@ def run_ours(args, rank, local_rank, world):
                      "dram_frac": round(traffic / k_avg_s / 1e9 / peak, 4) if traffic else None},
         "e2e": {"value": round(ncell * e2e_steps * world / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(n * 10 * 8), "d2h_bytes_per_step": int(n * 6 * 8),
-                "steps": e2e_steps},
+                "steps": e2e_steps,
+                "path": "per step: lbm_set_particles from page-locked host tensors (read by the upload "
+                        "kernel), lbm_step, dem_step, lbm_get_forces into page-locked host tensors "
+                        "(written by the download kernel, with the status words)"},
         "gpu_launches": int(launches1 - launches0),
         "storage_compare": {"note": "collide-stream kernels only (fluid + PSC tiles), static particles, "
                                     "same grid; error against FP64 reported by the test suite",

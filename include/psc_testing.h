@@ -2,7 +2,8 @@
  *
  * The binning, the packed records and the DEM sub-step use a few __host__ __device__
  * helpers (tile ranges and culling, record positions, neighbour-bin walk, contact decision,
- * JKR contact-radius solve). These calls run the same source on the host, so tests can check
+ * JKR contact-radius solve, displacement since the neighbour list's build) and the host
+ * checks of a particle upload. These calls run the same source on the host, so tests can check
  * the compiled arithmetic against brute force without a GPU. They allocate nothing, touch no
  * device and never fail; arguments are plain values and caller-owned arrays. Not part of the
  * simulation interface of psc_lbm.h. */
@@ -38,6 +39,13 @@ int psc_test_contact_sign(double d2, double S, int *ge0, int *gt0);
 /* The JKR contact-radius solve (reading R14): s = sqrt(a / a0) for t = delta_N R / a0^2,
  * started from s_prev; *fail = 1 when it did not converge, *iters the converging iteration. */
 float psc_test_jkr_s(float t, float s_prev, int *fail, int *iters);
+/* The DEM's squared displacement test (FP32, one image shift on periodic axes) of a
+ * particle at x[3] from its position xr[3] at the last neighbour-list build. */
+float psc_test_moved2(const double *x, const double *xr, const int *n, const int *periodic, int dim);
+/* The host-side checks of a particle upload: 1 when the m values are all finite; the
+ * smallest r^2 and the largest r over n radii. */
+int psc_test_all_finite(const double *a, long long m);
+void psc_test_radii_range(const double *R, int n, double *s2min, double *rmax);
 
 #ifdef __cplusplus
 }

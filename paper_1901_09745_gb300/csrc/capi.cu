@@ -12,6 +12,7 @@
 
 #include "../../include/psc_lbm.h"
 #include "capi_internal.h"
+#include "hostcheck.h"
 #include "lattice.cuh"
 #include "psc_internal.h"
 
@@ -309,31 +310,13 @@ void ctx_update_wrap(lbm_ctx *ctx) {
     }
 }
 
-static const uint64_t kExpBits = 0x7ff0000000000000ull;
-
-// 1 when the m values are all finite: a branch-free pass over the bit patterns (all exponent
-// bits set is an infinity or a NaN), which the compiler vectorizes.
-static int all_finite(const double *a, size_t m) {
-    uint64_t bad = 0;
-    for (size_t i = 0; i < m; ++i) {
-        uint64_t b;
-        memcpy(&b, a + i, sizeof(b));
-        bad |= (uint64_t)((b & kExpBits) == kExpBits);
-    }
-    return bad == 0;
-}
-
 lbm_status ctx_check_radii(lbm_ctx *ctx, const double *R, int n) {
     const double rmin2 = (ctx->dim == 2) ? 0.25 : 0.5;
     // one branch-free pass (smallest r^2, largest r); the per-particle search only for the
     // message when it finds a radius out of range
-    double s2min = INFINITY, rmax = 0.0;
-    for (int i = 0; i < n; ++i) {
-        const double r = R[i], r2 = r * r;
-        s2min = r2 < s2min ? r2 : s2min;
-        rmax = r > rmax ? r : rmax;
-    }
-    if (n > 0 && (!(s2min > rmin2) || !all_finite(R, (size_t)n))) {
+    double s2min, rmax;
+    psc::radii_range(R, n, &s2min, &rmax);
+    if (n > 0 && (!(s2min > rmin2) || !psc::all_finite(R, (size_t)n))) {
         for (int i = 0; i < n; ++i) {
             if (!(R[i] * R[i] > rmin2) || !isfinite(R[i])) {
                 ctx_error(ctx, "radius %d = %g: the linear approximation (Eq. 17/19) needs r^2 > %g", i, R[i], rmin2);
@@ -426,8 +409,8 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
         }
         lbm_status st = ctx_check_radii(ctx, Rh, n);
         if (st != LBM_OK) { free(hr); return st; }
-        if (!on_device && !(all_finite(X, 3 * (size_t)n) && all_finite(U, 3 * (size_t)n) &&
-                            all_finite(Omega, 3 * (size_t)n))) {
+        if (!on_device && !(psc::all_finite(X, 3 * (size_t)n) && psc::all_finite(U, 3 * (size_t)n) &&
+                            psc::all_finite(Omega, 3 * (size_t)n))) {
             for (int i = 0; i < 3 * n; ++i)
                 if (!isfinite(X[i]) || !isfinite(U[i]) || !isfinite(Omega[i])) {
                     ctx_error(ctx, "particle %d has a non-finite position, velocity or spin", i / 3);

@@ -2,6 +2,7 @@
 // that the CPU tests check the arithmetic the kernels compile rather than a copy of it (see
 // include/psc_testing.h). Nothing here touches a GPU.
 #include "../../include/psc_testing.h"
+#include "hostcheck.h"
 #include "hostdev.cuh"
 
 using namespace psc;
@@ -45,3 +46,14 @@ extern "C" float psc_test_jkr_s(float t, float s_prev, int *fail, int *iters) {
     *fail = 0;
     return jkr_s(t, fail, s_prev, iters);
 }
+
+extern "C" int psc_test_all_finite(const double *a, long long m) { return all_finite(a, (size_t)m); }
+
+extern "C" void psc_test_radii_range(const double *R, int n, double *s2min, double *rmax) {
+    radii_range(R, n, s2min, rmax);
+}
+
+extern "C" float psc_test_moved2(const double *x, const double *xr, const int *n, const int *periodic, int dim) {
+    return moved2(x, xr, n, periodic, dim);
+}
+

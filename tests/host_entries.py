@@ -24,6 +24,9 @@ def lib():
             "psc_test_axis_at": ([C.c_int] * 4, C.c_int),
             "psc_test_contact_sign": ([C.c_double, C.c_double, ip, ip], C.c_int),
             "psc_test_jkr_s": ([C.c_float, C.c_float, ip, ip], C.c_float),
+            "psc_test_moved2": ([dp, dp, ip, ip, C.c_int], C.c_float),
+            "psc_test_all_finite": ([C.c_void_p, C.c_longlong], C.c_int),
+            "psc_test_radii_range": ([C.c_void_p, C.c_int, dp, dp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
