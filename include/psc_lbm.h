@@ -239,6 +239,15 @@ lbm_status dem_destroy(dem_ctx *dem);
  * positions, velocities and spins replace the fluid context's particle state. */
 lbm_status dem_step(dem_ctx *dem, int substeps);
 
+/* nsteps coupled steps (Sec. 2.5): each is lbm_step(fluid, 1) followed by
+ * dem_step(dem, substeps), with the same results (up to the order of the FP64 force sums,
+ * as between any two runs). dem must be attached to fluid (LBM_ERR_ARG otherwise). In 2D
+ * with FP32 or 16-bit storage and an even sub-step count a step is one CUDA graph in which
+ * the tiles without particle candidates, which the DEM does not read, are computed on a
+ * second stream while the DEM call runs; the step ends with both streams joined, so the
+ * context's stream orders everything, as for the two calls. Asynchronous. */
+lbm_status lbm_coupled_step(lbm_ctx *fluid, dem_ctx *dem, int nsteps, int substeps);
+
 /* Particle state after the last DEM sub-step (n x 3 each; NULL pointers are skipped). */
 lbm_status dem_get_particles(dem_ctx *dem, double *X, double *U, double *Omega, int on_device);
 

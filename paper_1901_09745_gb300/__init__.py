@@ -119,6 +119,7 @@ def lib():
         "dem_get_contacts": ([vp, vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "dem_get_particles": ([vp, vp, vp, vp, C.c_int], C.c_int),
         "dem_get_info": ([vp, C.POINTER(C.c_longlong), C.c_int], C.c_int),
+        "lbm_coupled_step": ([vp, vp, C.c_int, C.c_int], C.c_int),
         "dem_get_wall_contacts": ([vp, vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "lbm_psc_step_noalloc": ([C.POINTER(LbmParams), vp, vp, C.c_int, vp, vp, vp, vp, vp, vp], C.c_int),
         "lbm_decomp_layout": ([C.c_int, C.c_int, C.c_int, C.c_int, ip, ip, ip], C.c_int),
@@ -395,6 +396,11 @@ def dem_destroy(dem):
 
 def dem_step(dem, substeps=1):
     _check(dem.fluid, lib().dem_step(dem.handle, int(substeps)))
+
+
+def lbm_coupled_step(ctx, dem, nsteps=1, substeps=1):
+    """nsteps of lbm_step(ctx, 1) + dem_step(dem, substeps), fused where the library can."""
+    _check(ctx, lib().lbm_coupled_step(ctx.handle, dem.handle, int(nsteps), int(substeps)))
 
 
 def dem_get_particles(dem, X=None, U=None, Om=None):

@@ -18,13 +18,13 @@
 
 namespace psc {
 cudaError_t launch_collide_stream_f64(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *);
+                                     Overlap *);
 cudaError_t launch_collide_stream_f32(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *);
+                                     Overlap *);
 cudaError_t launch_collide_stream_f16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *);
+                                     Overlap *);
 cudaError_t launch_collide_stream_bf16(int, const void *, void *, const Geom &, const Phys &, const Tiles &, const Parts &, int *, cudaStream_t,
-                                     const Overlap *);
+                                     Overlap *);
 cudaError_t launch_gather_f64(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f32(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
 cudaError_t launch_gather_f16(int, const void *, double *, double *, double *, const Geom &, const Phys &, cudaStream_t);
@@ -36,7 +36,7 @@ cudaError_t launch_set_bf16(int, const double *, void *, const Geom &, const Phy
 
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout, const Geom &g,
                                   const Phys &ph, const Tiles &tl, const Parts &pd, int *flags,
-                                  cudaStream_t s, const Overlap *ov) {
+                                  cudaStream_t s, Overlap *ov) {
     switch (storage) {
     case ST_F64: return launch_collide_stream_f64(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
     case ST_F32: return launch_collide_stream_f32(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
@@ -273,8 +273,10 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     for (int i = 0; i < ctx->ev_cap; ++i) cudaEventDestroy(ctx->ev[i]);
     free(ctx->ev);
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < 2; ++b) {
             if (ctx->sgraph[a][b]) cudaGraphExecDestroy(ctx->sgraph[a][b]);
+            if (ctx->cgraph[a][b]) cudaGraphExecDestroy(ctx->cgraph[a][b]);
+        }
     if (ctx->ov.aux) cudaStreamDestroy(ctx->ov.aux);
     if (ctx->ov.fork) cudaEventDestroy(ctx->ov.fork);
     if (ctx->ov.join) cudaEventDestroy(ctx->ov.join);
@@ -571,6 +573,91 @@ lbm_status ctx_step_once(lbm_ctx *ctx) {
     ctx->cs_launches += 1;
     ctx->cur ^= 1;
     ctx->steps += 1;
+    return LBM_OK;
+}
+
+// One coupled step: the fluid step and then the DEM call, as lbm_step(ctx, 1) and
+// dem_step(dem, substeps) would queue them, but replayed from one CUDA graph in which the
+// particle tiles run first and the plain-fluid tiles (which the DEM call does not read)
+// follow on the second stream beside the DEM's kernels; the graph joins the two streams at
+// its end. Steps the graph cannot take (a timed step, an odd sub-step count, no particles,
+// 3D or FP64, a stream the caller is capturing) are queued as the two calls.
+static lbm_status ctx_coupled_once(lbm_ctx *ctx, dem_ctx *dem, int substeps) {
+    const bool timed = ctx->timing > 0 && ctx->steps % ctx->timing == 0;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cs), "cudaStreamIsCapturing");
+    const bool fused = ctx->np > 0 && substeps > 0 && substeps % 2 == 0 && !timed &&
+                       cs == cudaStreamCaptureStatusNone && ctx->dim == 2 && ctx->p.storage != LBM_F64 &&
+                       ctx->ov.aux != NULL;
+    if (!fused) {
+        lbm_status st = ctx_step_once(ctx);
+        if (st != LBM_OK) return st;
+        return dem_step(dem, substeps);
+    }
+    // the DEM call's host side first: it touches no buffer of the fluid step
+    int run = 0;
+    lbm_status st = dem_prepare(dem, substeps, &run);
+    if (st != LBM_OK) return st;
+    if (!run) return ctx_step_once(ctx);
+    const bool bin = !ctx->bins_valid;
+    const void *key[28];
+    const void *lk[10] = {(const void *)(size_t)ctx->gen, ctx->dX, ctx->dU, ctx->dOm, ctx->dR, ctx->dF,
+                          ctx->dT, ctx->dFr, ctx->dPf, (const void *)(size_t)ctx->np};
+    for (int k = 0; k < 10; ++k) key[k] = lk[k];
+    dem_graph_key(dem, key + 10);
+    key[10 + kDemKey] = (const void *)(size_t)substeps;
+    const int a = ctx->cur, b = bin ? 1 : 0;
+    bool same = ctx->cgraph[a][b] != NULL;
+    for (int k = 0; same && k < 28; ++k) same = (ctx->cgkey[a][b][k] == key[k]);
+    if (!same) {
+        if (ctx->cgraph[a][b]) { cudaGraphExecDestroy(ctx->cgraph[a][b]); ctx->cgraph[a][b] = NULL; }
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        ctx->ov.defer = 1;
+        ctx->ov.deferred = 0;
+        lbm_status sl = ctx_enqueue_step(ctx, bin, NULL);
+        ctx->ov.defer = 0;
+        cudaError_t ed = sl == LBM_OK ? dem_enqueue_call(dem, substeps) : cudaSuccess;
+        cudaError_t ew = (sl == LBM_OK && ed == cudaSuccess && ctx->ov.deferred)
+                             ? cudaStreamWaitEvent(ctx->stream, ctx->ov.join, 0) : cudaSuccess;
+        cudaGraph_t graph = NULL;
+        cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        if (sl != LBM_OK) { if (graph) cudaGraphDestroy(graph); return sl; }
+        if (ed != cudaSuccess || ew != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return ctx_cuda(ctx, ed != cudaSuccess ? ed : ew, "coupled step (capture)");
+        }
+        CK(ec, "cudaStreamEndCapture");
+        cudaError_t ei = cudaGraphInstantiate(&ctx->cgraph[a][b], graph, 0);
+        cudaGraphDestroy(graph);
+        CK(ei, "cudaGraphInstantiate");
+        for (int k = 0; k < 28; ++k) ctx->cgkey[a][b][k] = key[k];
+    }
+    CK(cudaGraphLaunch(ctx->cgraph[a][b], ctx->stream), "cudaGraphLaunch");
+    // the two calls' bookkeeping
+    if (bin) {
+        ctx->launches += 2;
+        ctx->bins_valid = 1;
+    }
+    ctx->launches += 3;
+    ctx->cs_launches += 1;
+    ctx->cur ^= 1;
+    ctx->steps += 1;
+    dem_after_call(dem, substeps, 0);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_coupled_step(lbm_ctx *ctx, dem_ctx *dem, int nsteps, int substeps) {
+    NvtxRange nvtx_("lbm_coupled_step");
+    if (!ctx || !dem) return LBM_ERR_ARG;
+    if (dem_fluid(dem) != ctx) { ctx_error(ctx, "the DEM context is attached to another fluid context"); return LBM_ERR_ARG; }
+    if (nsteps < 0 || substeps < 0) {
+        ctx_error(ctx, "nsteps and substeps must be >= 0, got %d and %d", nsteps, substeps);
+        return LBM_ERR_ARG;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        lbm_status st = ctx_coupled_once(ctx, dem, substeps);
+        if (st != LBM_OK) return st;
+    }
     return LBM_OK;
 }
 

@@ -57,6 +57,10 @@ struct lbm_ctx {
     cudaGraphExec_t sgraph[2][2];
     const void *sgkey[2][2][10];
     long long gen;
+    // one coupled step (fluid step + DEM call) replayed from a CUDA graph, by parity and
+    // whether it bins, keyed on the fluid step's key, the DEM call's and the sub-step count
+    cudaGraphExec_t cgraph[2][2];
+    const void *cgkey[2][2][28];
 
     // optional CUDA-event timing of the collide-stream kernel (bench / profiling)
     int timing;
@@ -92,6 +96,15 @@ void dem_particles_changed(dem_ctx *dem);
 // the device word that requests a rebuild and the squared threshold (FP32), or 0 when the
 // list must be rebuilt anyway (no valid list, another count).
 int dem_upload_check(dem_ctx *dem, int n, const double **ref, int **req, float *lim2);
+// The pieces of dem_step, for a coupled step that captures a DEM call with the fluid step:
+// the host side before the kernels (*run = 0: nothing to do), the graph key of the call,
+// its kernels, and the bookkeeping after them.
+constexpr int kDemKey = 17;
+lbm_status dem_prepare(dem_ctx *dem, int substeps, int *run);
+void dem_graph_key(const dem_ctx *dem, const void *key[kDemKey]);
+cudaError_t dem_enqueue_call(dem_ctx *dem, int substeps);
+void dem_after_call(dem_ctx *dem, int substeps, int swap);
+lbm_ctx *dem_fluid(const dem_ctx *dem);
 
 // NVTX range over one call of the C ABI (visible in Nsight timelines; a no-op when no tool
 // is attached). The no-allocation step takes none.

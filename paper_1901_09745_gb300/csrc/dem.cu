@@ -648,7 +648,7 @@ struct dem_ctx {
     float reject;
     // CUDA graph of one dem_step call (even sub-step counts), keyed on what it captures
     cudaGraphExec_t gexec;
-    const void *gkey[17];
+    const void *gkey[kDemKey];
     int gsub;
     int *bin_count, *bin_list;
     long long nbins;
@@ -670,6 +670,8 @@ static int dem_list_index(dem_ctx *d, int *idx) {
     *idx = h[kListIdx] & 1;
     return e == cudaSuccess;
 }
+
+lbm_ctx *dem_fluid(const dem_ctx *d) { return d ? d->fl : NULL; }
 
 void dem_particles_changed(dem_ctx *d) {
     if (d) d->force_rebuild = 1;
@@ -888,10 +890,12 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
     return cudaGetLastError();
 }
 
-extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
-    NvtxRange nvtx_("dem_step");
-    if (!d) return LBM_ERR_ARG;
+// The host side of a call before its kernels: buffers, bins, the list's state (memsets on
+// the stream when the list starts again or a rebuild is forced) and the rejection margin.
+// *run = 0 when the call has nothing to do.
+lbm_status dem_prepare(dem_ctx *d, int substeps, int *run) {
     lbm_ctx *fl = d->fl;
+    *run = 0;
     if (substeps < 0) { ctx_error(fl, "substeps must be >= 0"); return LBM_ERR_ARG; }
     if (fl->np == 0 || substeps == 0) return LBM_OK;
     if (fl->np != d->n) d->lists_valid = 0;
@@ -914,37 +918,71 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
     }
     // largest delta_C of any pair (R <= r_max / 2) plus a margin far above the FP32 error of
     // the position copies
-    {
-        int nmax = 1;
-        for (int a = 0; a < d->g.dim; ++a) nmax = fl->g.n[a] > nmax ? fl->g.n[a] : nmax;
-        d->g.margin = (float)(1e-3 + 8.0 * nmax / 16777216.0);
-        const double Es = d->p.E / (2.0 * (1.0 - d->p.poisson * d->p.poisson));
-        const double Rm = 0.5 * fl->rmax;
-        const double a0 = cbrt(9.0 * kPi * d->p.gamma * Rm * Rm / Es);
-        const double dC = d->p.adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * Rm) : 0.0;
-        d->reject = (float)(dC + d->g.margin);
-        if (dC >= d->g.skin) {
-            ctx_error(fl, "the neighbour-list skin %g must exceed the largest JKR pull-off separation %g "
-                          "(dem_params.skin)", d->g.skin, dC);
-            return LBM_ERR_ARG;
-        }
+    int nmax = 1;
+    for (int a = 0; a < d->g.dim; ++a) nmax = fl->g.n[a] > nmax ? fl->g.n[a] : nmax;
+    d->g.margin = (float)(1e-3 + 8.0 * nmax / 16777216.0);
+    const double Es = d->p.E / (2.0 * (1.0 - d->p.poisson * d->p.poisson));
+    const double Rm = 0.5 * fl->rmax;
+    const double a0 = cbrt(9.0 * kPi * d->p.gamma * Rm * Rm / Es);
+    const double dC = d->p.adhesive ? a0 * a0 / (2.0 * cbrt(6.0) * Rm) : 0.0;
+    d->reject = (float)(dC + d->g.margin);
+    if (dC >= d->g.skin) {
+        ctx_error(fl, "the neighbour-list skin %g must exceed the largest JKR pull-off separation %g "
+                      "(dem_params.skin)", d->g.skin, dC);
+        return LBM_ERR_ARG;
+    }
+    *run = 1;
+    return LBM_OK;
+}
+
+// Everything a call's kernels capture (a CUDA graph of the call is valid while this is unchanged).
+void dem_graph_key(const dem_ctx *d, const void *key[kDemKey]) {
+    const lbm_ctx *fl = d->fl;
+    unsigned rbits;
+    memcpy(&rbits, &d->reject, sizeof(rbits));
+    const void *k[kDemKey] = {d->Vf[0], fl->dX, fl->dU, fl->dOm, fl->dR, fl->dF, fl->dT, d->X2, d->U2, d->Om2,
+                              d->Xf[0], d->minv, d->bin_count, (const void *)(size_t)d->n, (const void *)(size_t)rbits,
+                              (const void *)(size_t)(d->g.nb[0] + 4096LL * (d->g.nb[1] + 4096LL * d->g.nb[2])),
+                              (const void *)(size_t)d->g.bin_cap};
+    for (int i = 0; i < kDemKey; ++i) key[i] = k[i];
+}
+
+cudaError_t dem_enqueue_call(dem_ctx *d, int substeps) { return dem_enqueue(d, substeps); }
+
+// The host bookkeeping after a call's kernels were queued (an even sub-step count leaves
+// every buffer where it started; an odd one, queued directly, swaps them).
+void dem_after_call(dem_ctx *d, int substeps, int swap) {
+    lbm_ctx *fl = d->fl;
+    if (swap && (substeps & 1)) {
+        double *t;
+        t = fl->dX; fl->dX = d->X2; d->X2 = t;
+        t = fl->dU; fl->dU = d->U2; d->U2 = t;
+        t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
     }
     const int kernels = 3 + substeps;
+    d->lists_valid = 1;
+    d->launches += kernels;
+    fl->launches += kernels;
+    fl->bins_valid = 0;   // particles moved: the fluid re-bins before its next step
+}
+
+extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
+    NvtxRange nvtx_("dem_step");
+    if (!d) return LBM_ERR_ARG;
+    lbm_ctx *fl = d->fl;
+    int run = 0;
+    lbm_status st = dem_prepare(d, substeps, &run);
+    if (st != LBM_OK || !run) return st;
     // even sub-step counts leave every buffer where it started, so the whole call can be
     // replayed from one CUDA graph, keyed on every pointer and size it was captured with
     // (the list buffers in use are chosen on the device)
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     DCK(cudaStreamIsCapturing(fl->stream, &cs), "cudaStreamIsCapturing");
-    unsigned rbits;
-    memcpy(&rbits, &d->reject, sizeof(rbits));
-    const void *key[17] = {d->Vf[0], fl->dX, fl->dU, fl->dOm, fl->dR, fl->dF, fl->dT, d->X2, d->U2, d->Om2, d->Xf[0],
-                           d->minv, d->bin_count, (const void *)(size_t)d->n, (const void *)(size_t)rbits,
-                           (const void *)(size_t)(d->g.nb[0] + 4096LL * (d->g.nb[1] + 4096LL * d->g.nb[2])),
-                           (const void *)(size_t)d->g.bin_cap};
-    bool replayed = false;
+    const void *key[kDemKey];
+    dem_graph_key(d, key);
     if (substeps % 2 == 0 && cs == cudaStreamCaptureStatusNone) {
         bool same = d->gexec && d->gsub == substeps;
-        for (int k = 0; same && k < 17; ++k) same = (d->gkey[k] == key[k]);
+        for (int k = 0; same && k < kDemKey; ++k) same = (d->gkey[k] == key[k]);
         if (!same) {
             if (d->gexec) { cudaGraphExecDestroy(d->gexec); d->gexec = NULL; }
             cudaGraph_t graph = NULL;
@@ -957,24 +995,14 @@ extern "C" lbm_status dem_step(dem_ctx *d, int substeps) {
             cudaGraphDestroy(graph);
             DCK(ei, "cudaGraphInstantiate");
             d->gsub = substeps;
-            for (int k = 0; k < 17; ++k) d->gkey[k] = key[k];
+            for (int k = 0; k < kDemKey; ++k) d->gkey[k] = key[k];
         }
         DCK(cudaGraphLaunch(d->gexec, fl->stream), "cudaGraphLaunch");
-        replayed = true;
+        dem_after_call(d, substeps, 0);
+        return LBM_OK;
     }
-    if (!replayed) {
-        DCK(dem_enqueue(d, substeps), "DEM kernels");
-        if (substeps & 1) {
-            double *t;
-            t = fl->dX; fl->dX = d->X2; d->X2 = t;
-            t = fl->dU; fl->dU = d->U2; d->U2 = t;
-            t = fl->dOm; fl->dOm = d->Om2; d->Om2 = t;
-        }
-    }
-    d->lists_valid = 1;
-    d->launches += kernels;
-    fl->launches += kernels;
-    fl->bins_valid = 0;   // particles moved: the fluid re-bins before its next step
+    DCK(dem_enqueue(d, substeps), "DEM kernels");
+    dem_after_call(d, substeps, 1);
     return LBM_OK;
 }
 

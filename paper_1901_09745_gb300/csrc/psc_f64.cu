@@ -6,7 +6,7 @@ namespace psc {
 
 cudaError_t launch_collide_stream_f64(int lattice, const void *fin, void *fout, const Geom &g,
                                     const Phys &ph, const Tiles &tl, const Parts &pd, int *flags,
-                                    cudaStream_t s, const Overlap *ov) {
+                                    cudaStream_t s, Overlap *ov) {
     return launch_collide_stream_storage<double>(lattice, fin, fout, g, ph, tl, pd, flags, s, ov);
 }
 

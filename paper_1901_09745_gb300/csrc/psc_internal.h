@@ -123,12 +123,18 @@ enum StorageKind { ST_F64 = 0, ST_F32 = 1, ST_F16 = 2, ST_BF16 = 3 };
 struct Overlap {
     cudaStream_t aux;
     cudaEvent_t fork, join;
+    // defer = 1 (a coupled step, whose DEM call follows on the main stream): where the
+    // particle and plain-fluid tiles run on two streams, the particle tiles (and the overflow
+    // tiles) run first at full occupancy, the fluid tiles follow on aux with room left on
+    // every SM for the main stream's next kernels, and the join is left to the caller, who
+    // waits on `join` when the launcher sets deferred = 1
+    int defer, deferred;
 };
 
 // Fused solid-fraction + PSC collision + pull streaming + force reduction (one step).
 cudaError_t launch_collide_stream(int storage, int lattice, const void *fin, void *fout,
                                   const Geom &g, const Phys &ph, const Tiles &tl,
-                                  const Parts &pd, int *flags, cudaStream_t s, const Overlap *ov);
+                                  const Parts &pd, int *flags, cudaStream_t s, Overlap *ov);
 // Pre-collision populations (full f, FP64) and/or Eq. 5 moments of the current state.
 cudaError_t launch_gather(int storage, int lattice, const void *fin, double *f_out,
                           double *rho, double *u, const Geom &g, const Phys &ph,

@@ -1027,6 +1027,27 @@ inline cudaError_t block_registers(K kern, int threads, int &regs) {
 }
 
 // One collide-stream step. Without particles: the fluid kernel over every tile. With
+// The overflow-tile kernel (tiles with more candidates than the pair kernels keep), which also
+// clears the particle-tile kernel's work counters for the next launch.
+template <class L, typename S, int PSC>
+cudaError_t launch_overflow(const void *fin, void *fout, const Geom &g, const PhysT<typename Store<S>::T> &pt,
+                            const Tiles &tl, const Parts &pd, int *flags, size_t osmem, dim3 block, cudaStream_t s) {
+    auto okern = k_collide_overflow<L, S, PSC>;
+    if (osmem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
+        if (e != cudaSuccess) return e;
+    }
+    okern<<<32, block, osmem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+    return cudaGetLastError();
+}
+
+// Fluid-tile blocks per SM when they follow the particle tiles beside the caller's next
+// kernels (a deferred join). On the 2048^2 channel with 5000 discs and its DEM call the
+// coupled step took 167.8 / 140.8 / 142.0 / 146.0 / 147.2 / 159.4 us with 1 / 2 / 3 / 4 / 5
+// / 6 blocks per SM (156 us as two calls): fewer leave the fluid tiles unfinished when the
+// DEM call ends, more slow the latency-bound DEM kernels down.
+constexpr int kDeferF = 2;
+
 // particles in 2D (FP32 and 16-bit storage): the particle-tile kernel (4 blocks per SM) and
 // the fluid-tile kernel (3 blocks per SM) side by side on two streams, which together fill
 // each SM's register file, so the issue-bound particle tiles and the DRAM-bound fluid tiles
@@ -1036,7 +1057,7 @@ inline cudaError_t block_registers(K kern, int threads, int &regs) {
 template <class L, typename S, int PSC>
 cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, const Phys &ph,
                                     const Tiles &tl, const Parts &pd, int *flags, cudaStream_t s,
-                                    const Overlap *ov) {
+                                    Overlap *ov) {
     using T = typename Store<S>::T;
     constexpr int NC = (L::D == 2) ? 3 : 6;
     constexpr bool kSteal = (L::D == 3) || sizeof(T) == 8;
@@ -1088,6 +1109,20 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
         if (e != cudaSuccess) return e;
         side = per >= kSideP && kSideP * rp + kSideF * rf <= rf_sm;
     }
+    if (side && ov->defer) {
+        e = persistent_blocks(kern, smem, ntiles, nb, kPThreads);
+        if (e != cudaSuccess) return e;
+        kern<<<nb, pblock, smem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
+        e = launch_overflow<L, S, PSC>(fin, fout, g, pt, tl, pd, flags, osmem, block, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ov->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->fork, 0);
+        if (e != cudaSuccess) return e;
+        fkern<<<nsm * kDeferF, pblock, 0, ov->aux>>>((const S *)fin, (S *)fout, g, pt, tl, pd.n, flags);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ov->join, ov->aux);
+        if (e == cudaSuccess) ov->deferred = 1;
+        return e;
+    }
     if (side) {
         e = cudaEventRecord(ov->fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->fork, 0);
@@ -1110,19 +1145,13 @@ cudaError_t launch_collide_stream_t(const void *fin, void *fout, const Geom &g, 
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    auto okern = k_collide_overflow<L, S, PSC>;
-    if (osmem > 48 * 1024) {
-        e = cudaFuncSetAttribute(okern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)osmem);
-        if (e != cudaSuccess) return e;
-    }
-    okern<<<32, block, osmem, s>>>((const S *)fin, (S *)fout, g, pt, tl, pd, flags);
-    return cudaGetLastError();
+    return launch_overflow<L, S, PSC>(fin, fout, g, pt, tl, pd, flags, osmem, block, s);
 }
 
 template <typename S>
 cudaError_t launch_collide_stream_storage(int lattice, const void *fin, void *fout, const Geom &g,
                                           const Phys &ph, const Tiles &tl, const Parts &pd,
-                                          int *flags, cudaStream_t s, const Overlap *ov) {
+                                          int *flags, cudaStream_t s, Overlap *ov) {
     if (lattice == 9) {
         return ph.psc == 0 ? launch_collide_stream_t<D2Q9, S, 0>(fin, fout, g, ph, tl, pd, flags, s, ov)
                            : launch_collide_stream_t<D2Q9, S, 1>(fin, fout, g, ph, tl, pd, flags, s, ov);
