@@ -235,6 +235,7 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->ov.aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.prep, cudaEventDisableTiming);
     size_t bytes = (size_t)g.ncell * ctx->q * ctx->elem;
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[1], bytes);
@@ -280,6 +281,7 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     if (ctx->ov.aux) cudaStreamDestroy(ctx->ov.aux);
     if (ctx->ov.fork) cudaEventDestroy(ctx->ov.fork);
     if (ctx->ov.join) cudaEventDestroy(ctx->ov.join);
+    if (ctx->ov.prep) cudaEventDestroy(ctx->ov.prep);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     free(ctx);
     return LBM_OK;
@@ -612,13 +614,23 @@ static lbm_status ctx_coupled_once(lbm_ctx *ctx, dem_ctx *dem, int substeps) {
     if (!same) {
         if (ctx->cgraph[a][b]) { cudaGraphExecDestroy(ctx->cgraph[a][b]); ctx->cgraph[a][b] = NULL; }
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        // the DEM call's preparation (rebuild decision, FP32 copies, list rebuild when due)
+        // reads only the particle state, which the fluid step leaves alone: it runs on the
+        // second stream beside the binning and the particle tiles
+        cudaError_t ep = cudaEventRecord(ctx->ov.prep, ctx->stream);
+        if (ep == cudaSuccess) ep = cudaStreamWaitEvent(ctx->ov.aux, ctx->ov.prep, 0);
+        if (ep == cudaSuccess) ep = dem_enqueue_prep(dem, ctx->ov.aux);
+        if (ep == cudaSuccess) ep = cudaEventRecord(ctx->ov.prep, ctx->ov.aux);
         ctx->ov.defer = 1;
         ctx->ov.deferred = 0;
-        lbm_status sl = ctx_enqueue_step(ctx, bin, NULL);
+        lbm_status sl = ep == cudaSuccess ? ctx_enqueue_step(ctx, bin, NULL) : LBM_OK;
         ctx->ov.defer = 0;
-        cudaError_t ed = sl == LBM_OK ? dem_enqueue_call(dem, substeps) : cudaSuccess;
-        cudaError_t ew = (sl == LBM_OK && ed == cudaSuccess && ctx->ov.deferred)
-                             ? cudaStreamWaitEvent(ctx->stream, ctx->ov.join, 0) : cudaSuccess;
+        cudaError_t ed = ep;
+        if (ed == cudaSuccess && sl == LBM_OK) ed = cudaStreamWaitEvent(ctx->stream, ctx->ov.prep, 0);
+        if (ed == cudaSuccess && sl == LBM_OK) ed = dem_enqueue_substeps(dem, substeps, ctx->stream);
+        cudaError_t ew = cudaSuccess;
+        if (ed == cudaSuccess && sl == LBM_OK)
+            ew = cudaStreamWaitEvent(ctx->stream, ctx->ov.deferred ? ctx->ov.join : ctx->ov.prep, 0);
         cudaGraph_t graph = NULL;
         cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
         if (sl != LBM_OK) { if (graph) cudaGraphDestroy(graph); return sl; }

@@ -103,6 +103,10 @@ constexpr int kDemKey = 17;
 lbm_status dem_prepare(dem_ctx *dem, int substeps, int *run);
 void dem_graph_key(const dem_ctx *dem, const void *key[kDemKey]);
 cudaError_t dem_enqueue_call(dem_ctx *dem, int substeps);
+// The same kernels in two parts on given streams: the preparation (rebuild decision, FP32
+// copies, list rebuild when due) and the sub-steps (which read the fluid's F and T).
+cudaError_t dem_enqueue_prep(dem_ctx *dem, cudaStream_t s);
+cudaError_t dem_enqueue_substeps(dem_ctx *dem, int substeps, cudaStream_t s);
 void dem_after_call(dem_ctx *dem, int substeps, int swap);
 lbm_ctx *dem_fluid(const dem_ctx *dem);
 

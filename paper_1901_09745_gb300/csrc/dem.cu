@@ -843,13 +843,13 @@ static cudaError_t launch_dep(void (*kern)(KArgs...), unsigned blocks, unsigned 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// Queue one dem_step call (rebuild decision, FP32 copies, list rebuild when due, sub-steps)
-// without touching host-side state: the particle buffers alternate between the fluid
-// context's and the DEM's own each sub-step, and `flip` (an odd count) tells the caller to
-// swap them afterwards.
-static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
+// Queue one dem_step call without touching host-side state, in two parts: the preparation
+// (rebuild decision, FP32 copies, list rebuild when due), which reads only the particle
+// state, and the sub-steps, which also read the fluid's F and T. The particle buffers
+// alternate between the fluid context's and the DEM's own each sub-step (an odd count
+// leaves them swapped; the caller swaps the pointers).
+cudaError_t dem_enqueue_prep(dem_ctx *d, cudaStream_t s) {
     lbm_ctx *fl = d->fl;
-    cudaStream_t s = fl->stream;
     const int n = d->n;
     cudaError_t e = launch_dep(k_dem_decide, (unsigned)((d->nbins + 255) / 256 < 64 ? (d->nbins + 255) / 256 : 64),
                                256u, s, d->state, d->bin_count, d->nbins);
@@ -863,7 +863,13 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
                        (const int *)d->bin_list, (int *const *)d->lists_dev, (int *const *)(d->lists_dev + 2),
                        (float *const *)(d->lists_dev + 4), d->Xref, d->minv, d->ph.density, fl->flags,
                        (const int *)d->state);
-    if (e != cudaSuccess) return e;
+    return e;
+}
+
+cudaError_t dem_enqueue_substeps(dem_ctx *d, int substeps, cudaStream_t s) {
+    lbm_ctx *fl = d->fl;
+    const int n = d->n;
+    cudaError_t e = cudaSuccess;
     DemBufs b;
     b.n = n;
     b.R = fl->dR;
@@ -888,6 +894,12 @@ static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+static cudaError_t dem_enqueue(dem_ctx *d, int substeps) {
+    cudaError_t e = dem_enqueue_prep(d, d->fl->stream);
+    if (e == cudaSuccess) e = dem_enqueue_substeps(d, substeps, d->fl->stream);
+    return e;
 }
 
 // The host side of a call before its kernels: buffers, bins, the list's state (memsets on

@@ -129,6 +129,9 @@ struct Overlap {
     // every SM for the main stream's next kernels, and the join is left to the caller, who
     // waits on `join` when the launcher sets deferred = 1
     int defer, deferred;
+    // recorded on aux by a coupled step once the DEM call's preparation kernels (which read
+    // only the particle state the fluid step leaves alone) have run there
+    cudaEvent_t prep;
 };
 
 // Fused solid-fraction + PSC collision + pull streaming + force reduction (one step).
