@@ -408,41 +408,57 @@ constexpr int kLPP = 2;   // lanes per particle in the sub-step kernel (c2 coupl
 
 // One DEM sub-step. kLPP lanes share a particle and split its neighbour slots; their FP64
 // sums are combined with shuffles in a fixed order, then the first lane integrates.
+// early = 1 when the kernel before it in the stream is the previous sub-step of the same call.
 template <int DIM>
-__global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b) {
-    dep_wait();
-    dep_launch();
+__global__ void k_dem_substep(DemGeom g, DemPhys ph, DemBufs b, int early) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / kLPP, sub = t % kLPP;
     const bool valid = i < b.n;
-    const int li = b.state[kListIdx];
-    const int *const nbr_n = b.nbr_n[li], *const nbr = b.nbr[li];
-    float *const hist = b.hist[li];
     constexpr int dim = DIM;
-    // force and torque components a 2D disc has: F_x, F_y and T_z
-    auto used = [](int q) { return DIM == 3 || q == 0 || q == 1 || q == 5; };
-    double acc[6] = {0, 0, 0, 0, 0, 0};
-    double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0}, ri = 1.0;
-    double fi[3] = {0, 0, 0}, ti[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, im = 0.0, iI = 0.0;
-    int fail = 0;
-    if (valid) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) { xi[a] = b.X[3 * i + a]; ui[a] = b.U[3 * i + a]; oi[a] = b.Om[3 * i + a]; }
+    // Values fixed over a call's sub-steps: the list in use, the particle's neighbour count
+    // and first neighbour, its radius and masses, the fluid's F and T (read by the
+    // integrating lane before the contact loop's stores) and the position at the list's
+    // build. After a sub-step of the same call they are loaded before waiting for it, so
+    // the wait leads straight to the loads of the state that sub-step wrote.
+    int li = 0, nn = 0, jn = 0;
+    double ri = 1.0, fi[3] = {0, 0, 0}, ti[3] = {0, 0, 0}, xr[3] = {0, 0, 0}, im = 0.0, iI = 0.0;
+    float imi = 0.0f;
+    auto fixed = [&]() {
+        li = b.state[kListIdx];
+        if (!valid) return;
+        nn = (int)PSC_IDX(b.nbr_n[li][i], kNB + 1, CHK_NBR);
+        jn = b.nbr[li][i * kNB + sub];      // the lane's first neighbour (read without waiting for nn)
         ri = b.R[i];
-        const float4 pif = b.Xf[i];
-        const float imi = (float)b.minv[2 * i];
-        const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
-        const float uif[3] = {vi0.x, vi0.y, vi0.z};
-        const float oif[3] = {vi0.w, vi1.x, vi1.y};
-        const int nn = (int)PSC_IDX(nbr_n[i], kNB + 1, CHK_NBR);
+        imi = (float)b.minv[2 * i];
         if (sub == 0) {
-            // the integration's inputs, loaded before the contact loop's stores
 #pragma unroll
             for (int a = 0; a < 3; ++a) { fi[a] = b.Ff[3 * i + a]; ti[a] = b.Tf[3 * i + a]; xr[a] = b.Xref[3 * i + a]; }
             im = b.minv[2 * i];
             iI = b.minv[2 * i + 1];
         }
-        int jn = nbr[i * kNB + sub];      // the lane's next neighbour, loaded ahead (without waiting for nn)
+    };
+    if (early) {
+        fixed();
+        dep_wait();
+    } else {
+        dep_wait();
+        fixed();
+    }
+    dep_launch();
+    const int *const nbr = b.nbr[li];
+    float *const hist = b.hist[li];
+    // force and torque components a 2D disc has: F_x, F_y and T_z
+    auto used = [](int q) { return DIM == 3 || q == 0 || q == 1 || q == 5; };
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double xi[3] = {0, 0, 0}, ui[3] = {0, 0, 0}, oi[3] = {0, 0, 0};
+    int fail = 0;
+    if (valid) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { xi[a] = b.X[3 * i + a]; ui[a] = b.U[3 * i + a]; oi[a] = b.Om[3 * i + a]; }
+        const float4 pif = b.Xf[i];
+        const float4 vi0 = b.Vf[2 * i], vi1 = b.Vf[2 * i + 1];
+        const float uif[3] = {vi0.x, vi0.y, vi0.z};
+        const float oif[3] = {vi0.w, vi1.x, vi1.y};
         for (int s = sub; s < nn; s += kLPP) {
             const int j = (int)PSC_IDX(jn, b.n, CHK_PART);
             if (s + kLPP < nn) jn = nbr[i * kNB + s + kLPP];
@@ -889,8 +905,9 @@ cudaError_t dem_enqueue_substeps(dem_ctx *d, int substeps, cudaStream_t s) {
         const int src = k & 1, dst = src ^ 1;
         b.X = X[src]; b.U = U[src]; b.Om = Om[src]; b.Xf = d->Xf[src]; b.Vf = d->Vf[src];
         b.Xo = X[dst]; b.Uo = U[dst]; b.Omo = Om[dst]; b.Xfo = d->Xf[dst]; b.Vfo = d->Vf[dst];
-        if (d->g.dim == 2) e = launch_dep(k_dem_substep<2>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b);
-        else e = launch_dep(k_dem_substep<3>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b);
+        const int early = k > 0 ? 1 : 0;
+        if (d->g.dim == 2) e = launch_dep(k_dem_substep<2>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b, early);
+        else e = launch_dep(k_dem_substep<3>, (unsigned)blocks, (unsigned)threads, s, d->g, d->ph, b, early);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
