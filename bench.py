@@ -196,7 +196,7 @@ WORKLOAD_TEXT = {
 DEFAULT_STORAGE = {"c2": "f32", "c3": "f32", "c3dense": "f32", "c5": "f16", "c5dense": "f16", "c4": "f32",
                    "c1": "f64"}
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
-TIMING_EVERY = 8
+TIMING_EVERY = 16
 
 
 def dem_defaults(w):
