@@ -98,13 +98,12 @@ void dem_particles_changed(dem_ctx *dem);
 int dem_upload_check(dem_ctx *dem, int n, const double **ref, int **req, float *lim2);
 // The pieces of dem_step, for a coupled step that captures a DEM call with the fluid step:
 // the host side before the kernels (*run = 0: nothing to do), the graph key of the call,
-// its kernels, and the bookkeeping after them.
+// its kernels in two parts on given streams -- the preparation (rebuild decision, FP32
+// copies, list rebuild when due) and the sub-steps (which read the fluid's F and T) -- and
+// the bookkeeping after them.
 constexpr int kDemKey = 17;
 lbm_status dem_prepare(dem_ctx *dem, int substeps, int *run);
 void dem_graph_key(const dem_ctx *dem, const void *key[kDemKey]);
-cudaError_t dem_enqueue_call(dem_ctx *dem, int substeps);
-// The same kernels in two parts on given streams: the preparation (rebuild decision, FP32
-// copies, list rebuild when due) and the sub-steps (which read the fluid's F and T).
 cudaError_t dem_enqueue_prep(dem_ctx *dem, cudaStream_t s);
 cudaError_t dem_enqueue_substeps(dem_ctx *dem, int substeps, cudaStream_t s);
 void dem_after_call(dem_ctx *dem, int substeps, int swap);

@@ -976,8 +976,6 @@ void dem_graph_key(const dem_ctx *d, const void *key[kDemKey]) {
     for (int i = 0; i < kDemKey; ++i) key[i] = k[i];
 }
 
-cudaError_t dem_enqueue_call(dem_ctx *d, int substeps) { return dem_enqueue(d, substeps); }
-
 // The host bookkeeping after a call's kernels were queued (an even sub-step count leaves
 // every buffer where it started; an odd one, queued directly, swaps them).
 void dem_after_call(dem_ctx *d, int substeps, int swap) {
