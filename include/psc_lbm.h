@@ -105,9 +105,10 @@ lbm_status lbm_destroy(lbm_ctx *ctx);
  * r^2 > 1/4 in 2D (Eq. 19), and
  * a periodic axis must be longer than 2 (r + h) + 1; host values must be finite. Nothing
  * changes when a check fails (LBM_ERR_ARG with a message). on_device = 0: host arrays,
- * copied before the call returns (page-locked ones are read by the upload kernel directly,
- * pageable ones go through cudaMemcpyAsync); on_device = 1: device arrays, copied in stream
- * order. F and T are cleared. n = 0 removes all particles. A particle's index is its
+ * copied into the library's page-locked staging buffers before the call returns (the
+ * caller may reuse them at once; the call does not wait for the device, whose upload
+ * kernel reads the staging buffer in stream order); on_device = 1: device arrays, read by
+ * the upload kernel in stream order. F and T are cleared. n = 0 removes all particles. A particle's index is its
  * identity: with an attached DEM context (dem_create), an upload of the same count and the
  * same radii keeps the DEM's neighbour list and contact history, and the list is rebuilt at
  * the next dem_step only when some particle now lies more than a quarter of the skin from

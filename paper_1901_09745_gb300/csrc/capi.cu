@@ -236,6 +236,7 @@ extern "C" lbm_status lbm_create(const lbm_params *p, lbm_ctx **out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ov.prep, cudaEventDisableTiming);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ctx->stage_ev[k], cudaEventDisableTiming);
     size_t bytes = (size_t)g.ncell * ctx->q * ctx->elem;
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[0], bytes);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->f[1], bytes);
@@ -265,6 +266,10 @@ extern "C" lbm_status lbm_destroy(lbm_ctx *ctx) {
     free_dev((void **)&ctx->flags);
     if (ctx->hflags) cudaFreeHost(ctx->hflags);
     free(ctx->hR);
+    for (int k = 0; k < 2; ++k) {
+        if (ctx->stage[k]) cudaFreeHost(ctx->stage[k]);
+        if (ctx->stage_ev[k]) cudaEventDestroy(ctx->stage_ev[k]);
+    }
     free_particles(ctx);
     free_dev((void **)&ctx->tile_count); free_dev((void **)&ctx->tile_list); free_dev((void **)&ctx->tile_stats);
     free_dev((void **)&ctx->tile_order);
@@ -390,6 +395,47 @@ static void *device_view(const lbm_ctx *ctx, const void *p) {
     }
 }
 
+// The staging buffer for a host upload of n particles (10 n doubles: X, U, Omega, radii):
+// its host address, *dev its device address and *k its index; NULL when page-locked memory
+// for it cannot be had (the caller then copies and synchronises instead). Waits for the
+// upload that read the buffer last (normally long finished: the other buffer served the
+// upload in between).
+static double *ctx_stage(lbm_ctx *ctx, int n, const double **dev, int *k) {
+    const size_t need = (size_t)n * 10;
+    if (need > ctx->stage_cap) {
+        for (int b = 0; b < 2; ++b) {
+            if (ctx->stage_busy[b]) cudaEventSynchronize(ctx->stage_ev[b]);
+            ctx->stage_busy[b] = 0;
+            if (ctx->stage[b]) cudaFreeHost(ctx->stage[b]);
+            ctx->stage[b] = ctx->stage_dev[b] = NULL;
+        }
+        ctx->stage_cap = 0;
+        for (int b = 0; b < 2; ++b) {
+            if (cudaHostAlloc((void **)&ctx->stage[b], need * sizeof(double), cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostGetDevicePointer((void **)&ctx->stage_dev[b], ctx->stage[b], 0) != cudaSuccess) {
+                cudaGetLastError();
+                for (int c = 0; c < 2; ++c) {
+                    if (ctx->stage[c]) cudaFreeHost(ctx->stage[c]);
+                    ctx->stage[c] = ctx->stage_dev[c] = NULL;
+                }
+                return NULL;
+            }
+        }
+        ctx->stage_cap = need;
+    }
+    const int b = ctx->stage_k;
+    if (ctx->stage_busy[b]) {
+        if (cudaEventSynchronize(ctx->stage_ev[b]) != cudaSuccess) {
+            cudaGetLastError();
+            return NULL;
+        }
+        ctx->stage_busy[b] = 0;
+    }
+    *dev = ctx->stage_dev[b];
+    *k = b;
+    return ctx->stage[b];
+}
+
 extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, const double *U,
                                         const double *Omega, const double *radius, int on_device) {
     if (!ctx) return LBM_ERR_ARG;
@@ -448,11 +494,26 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
         u.dF = ctx->dF; u.dT = ctx->dT;
         for (int a = 0; a < 3; ++a) { u.n_lat[a] = ctx->g.n[a]; u.periodic[a] = ctx->g.periodic[a]; }
         if (ctx->dem && same_radii) keep_list = dem_upload_check(ctx->dem, n, &u.ref, &u.req, &u.lim2);
-        // sources the kernel can read directly (device memory, mapped page-locked host
-        // memory) are read by it; others are first copied into the context's arrays and
-        // the kernel then reads those in place
-        const void *v[4] = {device_view(ctx, X), device_view(ctx, U), device_view(ctx, Omega), device_view(ctx, radius)};
-        if (v[0] && v[1] && v[2] && v[3]) {
+        // host arrays are copied into a page-locked staging buffer that the kernel reads,
+        // so the call need not wait for the device; device arrays (or, without a staging
+        // buffer, mapped page-locked ones) are read by the kernel directly; others are
+        // first copied into the context's arrays and the kernel then reads those in place
+        const double *sdev = NULL;
+        int sk = 0;
+        double *sh = on_device ? NULL : ctx_stage(ctx, n, &sdev, &sk);
+        const size_t n3 = (size_t)n * 3;
+        const void *v[4] = {NULL, NULL, NULL, NULL};
+        if (!sh) {
+            v[0] = device_view(ctx, X); v[1] = device_view(ctx, U);
+            v[2] = device_view(ctx, Omega); v[3] = device_view(ctx, radius);
+        }
+        if (sh) {
+            memcpy(sh, X, n3 * sizeof(double));
+            memcpy(sh + n3, U, n3 * sizeof(double));
+            memcpy(sh + 2 * n3, Omega, n3 * sizeof(double));
+            memcpy(sh + 3 * n3, radius, (size_t)n * sizeof(double));
+            u.X = sdev; u.U = sdev + n3; u.Om = sdev + 2 * n3; u.R = sdev + 3 * n3;
+        } else if (v[0] && v[1] && v[2] && v[3]) {
             u.X = (const double *)v[0]; u.U = (const double *)v[1]; u.Om = (const double *)v[2];
             u.R = (const double *)v[3];
         } else {
@@ -465,10 +526,15 @@ extern "C" lbm_status lbm_set_particles(lbm_ctx *ctx, int n, const double *X, co
         }
         CK(launch_upload(u, ctx->stream), "particle upload kernel");
         ctx->launches += 1;
+        if (sh) {
+            CK(cudaEventRecord(ctx->stage_ev[sk], ctx->stream), "cudaEventRecord");
+            ctx->stage_busy[sk] = 1;
+            ctx->stage_k = sk ^ 1;
+        }
         st = ctx_reserve_tiles(ctx);
         if (st != LBM_OK) return st;
-        // the caller may reuse its host arrays once this returns
-        if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "set_particles sync");
+        // the caller may reuse its host arrays once this returns (staged: already copied)
+        if (!on_device && !sh) CK(cudaStreamSynchronize(ctx->stream), "set_particles sync");
     }
     ctx->hR_n = n;
     ctx->np = n;

@@ -30,6 +30,13 @@ struct lbm_ctx {
     double rmax;
     double *hR;                // host copy of the radii of the last upload (hR_n of them,
     int hR_n, hR_cap;          // -1: unknown), to tell whether an upload changed them
+    // page-locked staging of host uploads: two buffers of 10 n doubles, mapped so that the
+    // upload kernel reads them; lbm_set_particles copies the caller's arrays there and
+    // returns without waiting for the device, and an event per buffer guards its reuse
+    double *stage[2], *stage_dev[2];
+    size_t stage_cap;
+    int stage_k, stage_busy[2];
+    cudaEvent_t stage_ev[2];
 
     // tile candidate lists
     long long ntiles;

@@ -181,3 +181,35 @@ def test_upload_between_dem_calls_keeps_or_rebuilds_the_list(P, case):
     assert rel_l2((Og - Om1)[:, 2], (st.Om - Om1)[:, 2]) <= 1e-4
     assert rel_l2(Xg - X1, st.X - X1) <= 1e-4
     assert rel_l2(hg, ho) <= 1e-3
+
+
+@pytest.mark.parametrize("src", ["numpy", "pinned"])
+def test_host_arrays_may_change_as_soon_as_the_upload_returns(P, src):
+    """Host arrays are copied before lbm_set_particles returns (into the library's staging
+    buffers, without waiting for the device): the caller may overwrite them at once, and
+    uploads in a row each keep their own values."""
+    import torch
+    L = 96
+    X, U, Om, r = _discs(40, L, 3)
+    ref = P.lbm_create(9, L, L, 1, tau=0.8, storage="f32")
+    P.lbm_set_particles(ref, X, U, Om, r)
+    P.lbm_step(ref, 3)
+    F0, T0 = P.lbm_get_forces(ref)
+    P.lbm_destroy(ref)
+
+    ctx = P.lbm_create(9, L, L, 1, tau=0.8, storage="f32")
+    # three uploads in a row (the staging buffers are reused), the last one with the right
+    # values; each source is overwritten as soon as its call returns
+    for shift in (7.0, 13.0, 0.0):
+        args = [_as(torch, a.copy(), src) for a in (X + shift, U, Om, r)]
+        P.lbm_set_particles(ctx, *args)
+        for a in args[:3]:
+            if src == "numpy":
+                a[...] = 1.0e9
+            else:
+                a.fill_(1.0e9)
+    P.lbm_step(ctx, 3)
+    F1, T1 = P.lbm_get_forces(ctx)
+    P.lbm_destroy(ctx)
+    for a, b in ((F1, F0), (T1, T0)):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
