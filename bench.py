@@ -364,9 +364,10 @@ def run_ours(args, rank, local_rank, world):
         "e2e": {"value": round(ncell * e2e_steps * world / e2e_s / 1e6, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(n * 10 * 8), "d2h_bytes_per_step": int(n * 6 * 8),
                 "steps": e2e_steps,
-                "path": "per step: lbm_set_particles from page-locked host tensors (read by the upload "
-                        "kernel), lbm_coupled_step (lbm_step + dem_step), lbm_get_forces into page-locked "
-                        "host tensors (written by the download kernel, with the status words)"},
+                "path": "per step: lbm_set_particles from page-locked host tensors (copied into the "
+                        "library's page-locked staging buffer, read by the upload kernel), lbm_coupled_step "
+                        "(lbm_step + dem_step), lbm_get_forces into page-locked host tensors (written by "
+                        "the download kernel, with the status words)"},
         "gpu_launches": int(launches1 - launches0),
         "storage_compare": {"note": "collide-stream kernels only (fluid + PSC tiles), static particles, "
                                     "same grid; error against FP64 reported by the test suite",
