@@ -37,6 +37,22 @@ def test_finiteness_check_finds_every_nonfinite_value(H):
                 assert _finite(H, b) == 0, (m, pos, bad)
 
 
+def test_finiteness_check_reads_arrays_at_any_8_byte_offset(H):
+    """Caller arrays need only the alignment of a double: starts at every offset of 8 bytes
+    modulo 64 give the same answers."""
+    base = np.random.default_rng(8).normal(0, 1.0, 200)
+    for off in range(8):
+        for m in (0, 1, 7, 8, 9, 31, 64, 100):
+            a = base[off:off + m]
+            assert _finite(H, a) == 1
+            if m:
+                b = a.copy()
+                view = base.copy()[off:off + m]
+                view[m - 1] = np.inf
+                assert H.psc_test_all_finite(view.ctypes.data_as(C.c_void_p), view.size) == 0
+                assert _finite(H, b) == 1
+
+
 def test_radii_range_matches_numpy(H):
     rng = np.random.default_rng(6)
     lo, hi = C.c_double(), C.c_double()
